@@ -1,0 +1,246 @@
+"""Seeded synthetic workloads shaped like the paper's pressurised-crack examples.
+
+This module holds only input generation: mesh sizes, material constants, crack layouts and
+the initial phase field they imply, random vectors.  It contains none of the solver's
+arithmetic, so both the CUDA library's tests and the oracle's tests may use it.
+
+Recipes (seed 12345 unless stated):
+  * 2D single crack: [-10,10]^2, 64^2 Q1, E=1, nu=0.2, Gc=1, kappa=1e-10, eps=2h, p=1e-3,
+    phi=0 on every cell meeting |x|<=1, |y|<=h, else 1; phi_old=phi, u=0.
+  * 3D penny crack: [-10,10]^3, 128^3 Q1 or 64^3 Q2, same material, crack disk of radius 1 in
+    the plane z=0 (cells meeting |z|<=h, x^2+y^2<=1 get phi=0).
+  * 3D multi-crack: 8 penny cracks, centres U[-6,6]^3, normals N(0,I) normalised, radii U[1,2].
+  * batch instances: N^3 Q1 with N in {16,24,32,48,64}, 1-6 cracks of radius U[0.5,2],
+    p ~ U[5e-4, 2e-3].
+h is the cell diameter (sqrt(dim) times the edge length); the paper calls h the element
+diameter in its first example.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+SEED = 12345
+ALL_FACES = 0x3F
+
+
+@dataclass
+class Crack:
+    center: tuple
+    normal: tuple
+    radius: float          # half length in 2D, disk radius in 3D
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    deg: int
+    n_cells: tuple
+    n_levels: int
+    lo: tuple
+    hi: tuple
+    E: float = 1.0
+    nu: float = 0.2
+    Gc: float = 1.0
+    kappa: float = 1e-10
+    eps: float = 0.0
+    pressure: float = 1e-3
+    eps_factor: float = 2.0
+    dirichlet_faces: int = ALL_FACES
+    cracks: list = field(default_factory=list)
+    seed: int = SEED
+
+    @property
+    def edge(self) -> float:
+        return (self.hi[0] - self.lo[0]) / self.n_cells[0]
+
+    @property
+    def h(self) -> float:
+        """Cell diameter."""
+        return math.sqrt(sum(((self.hi[a] - self.lo[a]) / self.n_cells[a]) ** 2 for a in range(self.dim)))
+
+    def nodes_per_axis(self):
+        return tuple(self.deg * self.n_cells[a] + 1 for a in range(self.dim))
+
+    @property
+    def n_nodes(self) -> int:
+        return int(np.prod(self.nodes_per_axis()))
+
+    @property
+    def n_dofs(self) -> int:
+        return (self.dim + 1) * self.n_nodes
+
+    @property
+    def n_cells_total(self) -> int:
+        return int(np.prod(self.n_cells))
+
+    def finalize(self) -> "Workload":
+        if self.eps == 0.0:
+            self.eps = self.eps_factor * self.h
+        return self
+
+
+def config_2d_single_crack(n: int = 64, n_levels: int = 3, deg: int = 1) -> Workload:
+    w = Workload("2d_single_crack", 2, deg, (n, n), n_levels, (-10.0, -10.0), (10.0, 10.0))
+    w.cracks = [Crack((0.0, 0.0), (0.0, 1.0), 1.0)]
+    return w.finalize()
+
+
+def config_3d_penny(n: int = 128, deg: int = 1, n_levels: int = 5) -> Workload:
+    w = Workload("3d_penny", 3, deg, (n, n, n), n_levels, (-10.0,) * 3, (10.0,) * 3)
+    w.cracks = [Crack((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), 1.0)]
+    return w.finalize()
+
+
+def config_3d_multi(n: int = 256, deg: int = 1, n_levels: int = 6, eps_factor: float = 2.0,
+                    seed: int = SEED) -> Workload:
+    rng = np.random.default_rng(seed)
+    cracks = []
+    for _ in range(8):
+        c = rng.uniform(-6.0, 6.0, 3)
+        nv = rng.normal(size=3)
+        nv /= np.linalg.norm(nv)
+        cracks.append(Crack(tuple(c), tuple(nv), float(rng.uniform(1.0, 2.0))))
+    w = Workload("3d_multi", 3, deg, (n, n, n), n_levels, (-10.0,) * 3, (10.0,) * 3,
+                 eps_factor=eps_factor, cracks=cracks, seed=seed)
+    return w.finalize()
+
+
+def batch_instances(count: int = 256, sizes=(16, 24, 32, 48, 64), seed: int = SEED,
+                    coarsest: int = 4) -> list:
+    """Independent 3D instances for the batching pattern; levels go down to a coarsest grid of
+    at most 'coarsest' cells per edge (N=24 and N=48 stop at 3^3... 6^3 accordingly)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        levels = 1
+        m = n
+        while m % 2 == 0 and m // 2 >= 2 and m > coarsest:
+            m //= 2
+            levels += 1
+        ncr = int(rng.integers(1, 7))
+        cracks = []
+        for _ in range(ncr):
+            c = rng.uniform(-6.0, 6.0, 3)
+            nv = rng.normal(size=3)
+            nv /= np.linalg.norm(nv)
+            cracks.append(Crack(tuple(c), tuple(nv), float(rng.uniform(0.5, 2.0))))
+        w = Workload(f"batch_{i}", 3, 1, (n, n, n), levels, (-10.0,) * 3, (10.0,) * 3,
+                     pressure=float(rng.uniform(5e-4, 2e-3)), cracks=cracks, seed=seed + i)
+        out.append(w.finalize())
+    return out
+
+
+def small(w: Workload, n: int, n_levels: int | None = None) -> Workload:
+    """Same recipe on an n^dim mesh (eps follows the new h)."""
+    v = replace(w, n_cells=(n,) * w.dim, n_levels=n_levels or w.n_levels, eps=0.0)
+    return v.finalize()
+
+
+# ---------------------------------------------------------------- crack -> initial phase field
+
+def _cell_meets_crack(lo: np.ndarray, hi: np.ndarray, crack: Crack, h: float, dim: int) -> np.ndarray:
+    """Vectorised test whether axis-aligned cells [lo, hi] meet the closed crack region
+    {|n.(x-c)| <= h, |x - c - (n.(x-c)) n| <= r}.  Exact for axis-aligned normals (interval
+    overlap plus nearest-point distance); otherwise sampled on a 5^dim lattice per cell."""
+    c = np.asarray(crack.center[:dim], dtype=np.float64)
+    nv = np.asarray(crack.normal[:dim], dtype=np.float64)
+    nv = nv / np.linalg.norm(nv)
+    axis = int(np.argmax(np.abs(nv)))
+    if abs(abs(nv[axis]) - 1.0) < 1e-14:
+        ok = (lo[:, axis] <= c[axis] + h) & (hi[:, axis] >= c[axis] - h)
+        dist2 = np.zeros(lo.shape[0])
+        for a in range(dim):
+            if a == axis:
+                continue
+            nearest = np.clip(c[a], lo[:, a], hi[:, a])
+            dist2 += (nearest - c[a]) ** 2
+        return ok & (dist2 <= crack.radius ** 2 * (1 + 1e-12))
+    t = np.linspace(0.0, 1.0, 5)
+    grids = np.meshgrid(*([t] * dim), indexing="ij")
+    offs = np.stack([g.ravel() for g in grids], axis=1)
+    hit = np.zeros(lo.shape[0], dtype=bool)
+    for o in offs:
+        x = lo + (hi - lo) * o
+        s = (x - c) @ nv
+        tang = x - c - s[:, None] * nv
+        hit |= (np.abs(s) <= h) & (np.einsum("ij,ij->i", tang, tang) <= crack.radius ** 2)
+    return hit
+
+
+def initial_phase_field(w: Workload) -> np.ndarray:
+    """phi per node: 0 on all nodes of cells meeting a crack region, 1 elsewhere."""
+    dim = w.dim
+    n = np.array(w.n_cells)
+    edge = (np.array(w.hi) - np.array(w.lo)) / n
+    cidx = np.indices(tuple(n[::-1])).reshape(dim, -1)[::-1].T     # (ncell, dim), x fastest
+    lo = np.array(w.lo)[None, :] + cidx * edge[None, :]
+    hi = lo + edge[None, :]
+    hit = np.zeros(cidx.shape[0], dtype=bool)
+    for cr in w.cracks:
+        hit |= _cell_meets_crack(lo, hi, cr, w.h, dim)
+    phi = np.ones(w.n_nodes)
+    npa = np.array(w.nodes_per_axis())
+    hc = cidx[hit]
+    strides = np.cumprod(np.concatenate([[1], npa[:-1]]))
+    for off in np.ndindex(*([w.deg + 1] * dim)):
+        node = ((hc * w.deg + np.array(off)[None, :]) * strides[None, :]).sum(axis=1)
+        phi[node] = 0.0
+    return phi
+
+
+def smooth_displacement(w: Workload, amplitude: float = 1e-3, modes: int = 3,
+                        seed: int | None = None) -> np.ndarray:
+    """A smooth seeded displacement field (a few low Fourier modes per component), zero on
+    the box boundary, used as a synthetic linearisation point."""
+    rng = np.random.default_rng(w.seed if seed is None else seed)
+    npa = w.nodes_per_axis()
+    axes = [np.linspace(0.0, 1.0, npa[a]) for a in range(w.dim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+    X = [g.ravel() for g in grids]
+    out = []
+    for _ in range(w.dim):
+        f = np.zeros(w.n_nodes)
+        for _m in range(modes):
+            k = rng.integers(1, 4, size=w.dim)
+            a = rng.normal()
+            term = np.full(w.n_nodes, a)
+            for ax in range(w.dim):
+                term = term * np.sin(math.pi * k[ax] * X[ax])
+            f += term
+        out.append(amplitude * f)
+    return np.concatenate(out)
+
+
+def initial_state(w: Workload, displacement: str = "zero"):
+    """(U, phi_old, phi_tilde) with U = [u | phi]; displacement 'zero' or 'smooth'."""
+    phi = initial_phase_field(w)
+    if displacement == "smooth":
+        u = smooth_displacement(w)
+    else:
+        u = np.zeros(w.dim * w.n_nodes)
+    U = np.concatenate([u, phi])
+    return U, phi.copy(), phi.copy()
+
+
+def random_state(w: Workload, seed: int | None = None):
+    """Random smooth-ish state with phi in (0,1) everywhere, for operator parity tests."""
+    rng = np.random.default_rng(w.seed if seed is None else seed)
+    u = smooth_displacement(w, amplitude=1e-2, seed=int(rng.integers(1 << 30)))
+    u = u + 1e-3 * rng.standard_normal(u.shape)
+    phi = rng.uniform(0.05, 1.0, w.n_nodes)
+    ptil = np.clip(phi + 0.05 * rng.standard_normal(w.n_nodes), 0.0, 1.0)
+    return np.concatenate([u, phi]), phi.copy(), ptil
+
+
+def random_vector(n: int, seed: int = SEED) -> np.ndarray:
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def random_active(w: Workload, fraction: float = 0.1, seed: int = SEED) -> np.ndarray:
+    """Random 0/1 indicator per node (a synthetic active set for masking tests)."""
+    return (np.random.default_rng(seed).uniform(size=w.n_nodes) < fraction).astype(np.uint8)

@@ -1,0 +1,199 @@
+"""Pins of the oracle's FE layer against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms (patch test,
+tractions of affine fields, energies of constant states), finite differences of an
+independently written energy, the paper's Lame table, and structural facts of the method
+(G_uphi = 0, symmetry of G_uu, elimination pattern).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fem
+from paper_1902_08112_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _mesh(dim, deg, n, lo=-1.0, hi=1.0):
+    return fem.Mesh(dim, deg, (n,) * dim, (lo,) * dim, (hi,) * dim)
+
+
+def _affine_u(mesh, A, b=None):
+    X = mesh.node_coords()
+    u = X @ np.asarray(A).T
+    if b is not None:
+        u = u + np.asarray(b)[None, :]
+    return np.concatenate([u[:, c] for c in range(mesh.dim)])
+
+
+def test_lame_matches_paper_table():
+    """Sec. 5.1 parameter table: mu, lambda derived from E and nu (3D formulas)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "lame_table.txt")) if not l.startswith("#")]
+    for E, nu, mu_t, lam_t in (map(float, r) for r in rows):
+        mu, lam = fem.lame(E, nu)
+        assert math.floor(mu * 10) / 10 == pytest.approx(mu_t)
+        assert math.floor(lam * 10) / 10 == pytest.approx(lam_t)
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_lumped_mass_sums_to_volume(dim, deg):
+    m = fem.Mesh(dim, deg, (3,) * dim, (0.0,) * dim, tuple(1.0 + 0.5 * a for a in range(dim)))
+    M = fem.lumped_mass(m)
+    vol = np.prod([1.0 + 0.5 * a for a in range(dim)])
+    assert M.sum() == pytest.approx(vol, rel=1e-14)
+    assert (M > 0).all()
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_patch_test_affine_displacement(dim, deg):
+    """phi = phi~ = 1 and an affine u: sigma is constant, so the u-rows of A vanish at every
+    interior node (Q1 and Q2 reproduce affine fields exactly)."""
+    m = _mesh(dim, deg, 3)
+    rng = np.random.default_rng(1)
+    u = _affine_u(m, rng.normal(size=(dim, dim)), rng.normal(size=dim))
+    U = np.concatenate([u, np.ones(m.n_nodes)])
+    ph = fem.Phys(E=3.0, nu=0.3, p=0.7, eps=0.5)
+    A = fem.residual_A(m, ph, U, np.ones(m.n_nodes))
+    interior = fem.dirichlet_face_mask(m, 0x3F) == 0
+    for c in range(dim):
+        Ac = A[c * m.n_nodes:(c + 1) * m.n_nodes]
+        assert np.abs(Ac[interior]).max() < 1e-12
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_face_tractions_of_affine_fields(dim, deg):
+    """Sum of the u-residual over the nodes of a face equals the traction sigma.n integrated over
+    the face (sigma constant): uniaxial u=(g x,0,..) gives sigma_xx=(lambda+2mu) g,
+    sigma_yy = lambda g; shear u=(g y,0,..) gives sigma_xy = mu g."""
+    m = fem.Mesh(dim, deg, (2,) * dim, (0.0,) * dim, tuple(1.0 + 0.25 * a for a in range(dim)))
+    E, nu, g = 2.0, 0.25, 1e-2
+    ph = fem.Phys(E=E, nu=nu, p=0.0, eps=1.0)
+    mu, lam = fem.lame(E, nu)
+    L = [1.0 + 0.25 * a for a in range(dim)]
+    X = m.node_coords()
+    nn = m.n_nodes
+
+    def face_area(axis):
+        return np.prod([L[a] for a in range(dim) if a != axis])
+
+    def face_nodes(axis):
+        return np.isclose(X[:, axis], L[axis])
+
+    ones = np.ones(nn)
+    A1 = np.zeros((dim, dim)); A1[0, 0] = g
+    U = np.concatenate([_affine_u(m, A1), ones])
+    R = fem.residual_A(m, ph, U, ones)
+    assert R[0 * nn:1 * nn][face_nodes(0)].sum() == pytest.approx((lam + 2 * mu) * g * face_area(0), rel=1e-12)
+    assert R[1 * nn:2 * nn][face_nodes(1)].sum() == pytest.approx(lam * g * face_area(1), rel=1e-12)
+    A2 = np.zeros((dim, dim)); A2[0, 1] = g
+    U = np.concatenate([_affine_u(m, A2), ones])
+    R = fem.residual_A(m, ph, U, ones)
+    assert R[0 * nn:1 * nn][face_nodes(1)].sum() == pytest.approx(mu * g * face_area(1), rel=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_energy_of_constant_states(dim):
+    """Energy closed forms: affine u with phi=1 gives (E_s + p tr e)|D|; u=0 with constant phi=c
+    gives (g(c)*0 + Gc/2 (1-c)^2/eps)|D|."""
+    m = _mesh(dim, 1, 2, 0.0, 2.0)
+    vol = 2.0 ** dim
+    ph = fem.Phys(E=1.5, nu=0.2, p=0.3, eps=0.4, Gc=2.0)
+    mu, lam = fem.lame(1.5, 0.2)
+    A = np.zeros((dim, dim)); A[0, 0] = 0.01; A[0, 1] = 0.02
+    U = np.concatenate([_affine_u(m, A), np.ones(m.n_nodes)])
+    e = 0.5 * (A + A.T)
+    Es = 0.5 * lam * np.trace(e) ** 2 + mu * np.sum(e * e)
+    assert fem.energy(m, ph, U) == pytest.approx((Es + ph.p * np.trace(A)) * vol, rel=1e-13)
+    c = 0.3
+    U = np.concatenate([np.zeros(dim * m.n_nodes), np.full(m.n_nodes, c)])
+    assert fem.energy(m, ph, U) == pytest.approx(0.5 * ph.Gc * (1 - c) ** 2 / ph.eps * vol, rel=1e-13)
+
+
+def _rand_state(m, seed):
+    rng = np.random.default_rng(seed)
+    u = 0.05 * rng.standard_normal(m.dim * m.n_nodes)
+    phi = rng.uniform(0.1, 1.0, m.n_nodes)
+    return np.concatenate([u, phi])
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_residual_is_energy_gradient(dim, deg):
+    """A(U) = dE/dU when phi~ = phi and f = 1 (central differences of the energy, O(delta^2))."""
+    m = _mesh(dim, deg, 2)
+    ph = fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, Gc=1.0, kappa=1e-3)
+    U = _rand_state(m, 3)
+    phi = U[dim * m.n_nodes:]
+    A = fem.residual_A(m, ph, U, phi)
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        v = rng.standard_normal(U.size)
+        dlt = 1e-5
+        fd = (fem.energy(m, ph, U + dlt * v) - fem.energy(m, ph, U - dlt * v)) / (2 * dlt)
+        assert fd == pytest.approx(A @ v, rel=1e-7)
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+@pytest.mark.parametrize("f", [1.0, 0.5])
+def test_jacobian_is_residual_derivative(dim, deg, f):
+    """G v = d/dt A(U + t v) at t=0 with phi~ frozen (central differences), all blocks."""
+    m = _mesh(dim, deg, 2)
+    ph = fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, Gc=1.0, kappa=1e-3, f=f)
+    U = _rand_state(m, 5)
+    ptil = np.random.default_rng(6).uniform(0, 1, m.n_nodes)
+    G = fem.assemble(m, ph, U, ptil, np.zeros(m.n_nodes, np.uint8))
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        v = rng.standard_normal(U.size)
+        dlt = 1e-6
+        fd = (fem.residual_A(m, ph, U + dlt * v, ptil) - fem.residual_A(m, ph, U - dlt * v, ptil)) / (2 * dlt)
+        Gv = G @ v
+        assert np.linalg.norm(fd - Gv) <= 1e-7 * np.linalg.norm(Gv)
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (3, 1), (3, 2)])
+def test_block_structure(dim, deg):
+    """G_uphi = 0 exactly (phi~ frozen in the u-equation, Sec. 3.3) and G_uu symmetric."""
+    m = _mesh(dim, deg, 2)
+    ph = fem.Phys(E=1.0, nu=0.3, p=0.1, eps=0.3, kappa=1e-4)
+    U = _rand_state(m, 8)
+    ptil = np.random.default_rng(9).uniform(0, 1, m.n_nodes)
+    mask = fem.dirichlet_face_mask(m, 0x3F)
+    G = fem.assemble(m, ph, U, ptil, mask).toarray()
+    nu_ = dim * m.n_nodes
+    assert np.count_nonzero(G[:nu_, nu_:]) == 0
+    Guu = G[:nu_, :nu_]
+    assert np.abs(Guu - Guu.T).max() <= 1e-14 * np.abs(Guu).max()
+
+
+def test_elimination_pattern():
+    """Constrained rows are identity rows, constrained columns are zero (Algorithm 1, step 4)."""
+    w = W.small(W.config_2d_single_crack(), 4, 1)
+    m = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(eps=w.eps, p=w.pressure)
+    U, _, pt = W.random_state(w)
+    mask = fem.dirichlet_face_mask(m, 0x3F) | (W.random_active(w, 0.3) * fem.BIT_ACTIVE).astype(np.uint8)
+    G = fem.assemble(m, ph, U, pt, mask).toarray()
+    Gfull = fem.assemble(m, ph, U, pt, np.zeros_like(mask)).toarray()
+    cons = fem.constrained_dofs(m, mask)
+    assert cons.sum() > 0
+    np.testing.assert_array_equal(G[cons], np.eye(G.shape[0])[cons])
+    assert np.count_nonzero(G[np.ix_(~cons, cons)]) == 0
+    np.testing.assert_array_equal(G[np.ix_(~cons, ~cons)], Gfull[np.ix_(~cons, ~cons)])
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 2), (3, 1)])
+def test_row_sampler_matches_assembly(dim, deg):
+    m = _mesh(dim, deg, 3)
+    ph = fem.Phys(E=1.0, nu=0.2, p=0.02, eps=0.5, kappa=1e-6)
+    U = _rand_state(m, 10)
+    ptil = U[dim * m.n_nodes:]
+    mask = fem.dirichlet_face_mask(m, 0x3F)
+    mask[::7] |= fem.BIT_ACTIVE
+    G = fem.assemble(m, ph, U, ptil, mask)
+    x = np.random.default_rng(11).standard_normal(m.n_dofs)
+    rows = np.arange(0, m.n_dofs, 5)
+    np.testing.assert_allclose(fem.apply_rows(m, ph, U, ptil, mask, x, rows), (G @ x)[rows],
+                               rtol=1e-13, atol=1e-13 * np.abs(G @ x).max())

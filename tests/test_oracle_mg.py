@@ -1,0 +1,249 @@
+"""Pins of the oracle's multigrid, Krylov and active-set layers.
+
+Pinned against: exact polynomial reproduction of nested interpolation, the closed-form error
+polynomial of Chebyshev iteration on a diagonal matrix, dense eigenvalues (Ritz values of 10
+CG steps lie inside the spectrum), dense solves on tiny meshes (numpy.linalg.solve), published
+SplitMix64 outputs, Sneddon's closed-form crack volume, and the complementarity conditions of
+the active-set method at convergence.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fem, multigrid as mg, krylov, pdas
+from oracle.rng import splitmix64
+from paper_1902_08112_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_published_outputs():
+    G = 0x9E3779B97F4A7C15
+    for line in open(os.path.join(GOLDEN, "splitmix64.txt")):
+        if line.startswith("#"):
+            continue
+        k, hx = line.split()
+        z = splitmix64(np.array([(int(k) * G) % (1 << 64)], dtype=np.uint64))[0]
+        assert int(z) == int(hx, 16)
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_prolongation_reproduces_polynomials(dim, deg):
+    """Nested Q_deg spaces: interpolating a coarse Q_deg function onto the fine grid is exact
+    for every polynomial of degree <= deg per axis."""
+    mf = fem.Mesh(dim, deg, (4,) * dim, (-1.0,) * dim, (2.0,) * dim)
+    mc = mf.coarsen()
+    P = mg.prolongation(mc, mf)
+    Xc, Xf = mc.node_coords(), mf.node_coords()
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        coef = rng.normal(size=(deg + 1,) * dim)
+
+        def f(X):
+            out = np.zeros(X.shape[0])
+            for idx in np.ndindex(*coef.shape):
+                term = np.full(X.shape[0], coef[idx])
+                for a in range(dim):
+                    term = term * X[:, a] ** idx[a]
+                out += term
+            return out
+
+        np.testing.assert_allclose(P @ f(Xc), f(Xf), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(np.asarray(P.sum(axis=1)).ravel(), 1.0, rtol=1e-14)
+
+
+def test_injection_and_binary_coarse_active_set():
+    """Coarse nodes coincide with fine nodes, so restricting the active indicator by coincident
+    nodes keeps it in {0,1} and equal to the fine value there (Sec. 4.2)."""
+    w = W.small(W.config_3d_penny(), 8, 3)
+    mf = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+    mc = mf.coarsen()
+    inj = mg.injection_index(mc, mf)
+    np.testing.assert_allclose(mc.node_coords(), mf.node_coords()[inj], atol=1e-14)
+    act = W.random_active(w, 0.4)
+    mask = fem.dirichlet_face_mask(mf, 0x3F) | (act * fem.BIT_ACTIVE).astype(np.uint8)
+    U, _, pt = W.random_state(w)
+    levels = mg.build_levels(mf, 3, fem.Phys(eps=w.eps), U, pt, mask)
+    for l in range(2):
+        a = (levels[l].mask & fem.BIT_ACTIVE) // fem.BIT_ACTIVE
+        assert set(np.unique(a)) <= {0, 1}
+        inj = mg.injection_index(levels[l].mesh, levels[l + 1].mesh)
+        np.testing.assert_array_equal(levels[l].mask, levels[l + 1].mask[inj])
+
+
+def _cheb_T(k, t):
+    """Chebyshev polynomial of the first kind, T_k(t), for any real t."""
+    t = np.asarray(t, dtype=np.float64)
+    inside = np.cos(k * np.arccos(np.clip(t, -1.0, 1.0)))
+    outside = np.cosh(k * np.arccosh(np.maximum(np.abs(t), 1.0))) * np.where(t < 0, (-1.0) ** k, 1.0)
+    return np.where(np.abs(t) <= 1.0, inside, outside)
+
+
+def test_chebyshev_matches_closed_form_polynomial():
+    """On A = diag(lam), D = I, x0 = 0: the error after k steps is
+    e_k = T_k((theta - lam)/delta) / T_k(theta/delta) * x*, componentwise."""
+    lam = np.linspace(0.3, 2.0, 40)
+    A = np.diag(lam)
+    xs = np.random.default_rng(1).standard_normal(40)
+    b = lam * xs
+    a, c = 0.5, 2.2
+    theta, delta = 0.5 * (a + c), 0.5 * (c - a)
+    for k in (1, 2, 4, 7):
+        x = mg.chebyshev_zero(A, np.ones(40), b, a, c, k)
+        expected = _cheb_T(k, (theta - lam) / delta) / _cheb_T(k, theta / delta) * xs
+        np.testing.assert_allclose(xs - x, expected, rtol=1e-10, atol=1e-12)
+
+
+def _small_levels(dim=2, n=8, n_levels=2, deg=1, seed=3):
+    w = W.small(W.config_2d_single_crack() if dim == 2 else W.config_3d_penny(deg=deg), n, n_levels)
+    w.deg = deg
+    m = fem.Mesh(w.dim, deg, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(eps=w.eps, p=w.pressure, kappa=w.kappa)
+    U, po, pt = W.initial_state(w)
+    U[: w.dim * m.n_nodes] = W.smooth_displacement(w)
+    mask = fem.dirichlet_face_mask(m, 0x3F)
+    return w, m, ph, U, po, pt, mask
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cg_eigen_estimate_inside_spectrum(dim):
+    """Ritz values of 10 Jacobi-PCG steps lie inside [lambda_min, lambda_max] of D^-1 A_block
+    (dense eigenvalues of the symmetric D^-1/2 A D^-1/2) and lambda_max is close after 10 steps."""
+    w, m, ph, U, po, pt, mask = _small_levels(dim, 8 if dim == 2 else 4, 1)
+    levels = mg.build_levels(m, 1, ph, U, pt, mask)
+    mg.estimate_levels(levels, 12345, 10)
+    lev = levels[0]
+    for bi, blk in enumerate((lev.ublock, lev.pblock)):
+        free = lev.free[blk]
+        A = lev.G[blk][:, blk].toarray()[np.ix_(free, free)]
+        s = 1.0 / np.sqrt(np.diag(A))
+        ev = np.linalg.eigvalsh(s[:, None] * A * s[None, :])
+        assert lev.lam_max[bi] <= ev[-1] * (1 + 1e-10)
+        assert lev.lam_min[bi] >= ev[0] * (1 - 1e-10)
+        assert lev.lam_max[bi] >= 0.9 * ev[-1]
+
+
+def test_coarse_solver_converges_to_dense_solution():
+    """Chebyshev-as-solver on [0.9 l_min, 1.2 l_max] with many steps solves the block lower
+    triangular coarse system (compare with numpy.linalg.solve)."""
+    w, m, ph, U, po, pt, mask = _small_levels(2, 4, 1)
+    ph.kappa = 1e-2        # well-conditioned coarse problem so that the bound is reachable
+    levels = mg.build_levels(m, 1, ph, U, pt, mask)
+    mg.estimate_levels(levels, 12345, 10)
+    lev = levels[0]
+    b = np.where(lev.free, np.random.default_rng(2).standard_normal(m.n_dofs), 0.0)
+    # widen the bounds to the true spectrum so the a-priori step count is a valid bound
+    for bi, blk in enumerate((lev.ublock, lev.pblock)):
+        free = lev.free[blk]
+        A = lev.G[blk][:, blk].toarray()[np.ix_(free, free)]
+        s = 1.0 / np.sqrt(np.diag(A))
+        ev = np.linalg.eigvalsh(s[:, None] * A * s[None, :])
+        lev.lam_min = tuple(ev[0] / 0.9 if i == bi else lev.lam_min[i] for i in range(2))
+        lev.lam_max = tuple(ev[-1] / 1.2 if i == bi else lev.lam_max[i] for i in range(2))
+    prm = mg.MGParams(coarse_rtol=1e-10, coarse_maxit=5000)
+    x = mg.coarse_solve(lev, b, prm)
+    xd = np.linalg.solve(lev.G.toarray(), b)
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("dim,n,levels,deg", [(2, 8, 2, 1), (3, 4, 2, 1), (2, 8, 2, 2)])
+def test_fgmres_mg_matches_dense_solve(dim, n, levels, deg):
+    """FGMRES + V-cycle on tiny meshes reaches the dense solution (numpy.linalg.solve)."""
+    w, m, ph, U, po, pt, mask = _small_levels(dim, n, levels, deg)
+    lv = mg.build_levels(m, levels, ph, U, pt, mask)
+    mg.estimate_levels(lv, 12345, 10)
+    G = lv[-1].G
+    b = np.random.default_rng(4).standard_normal(m.n_dofs)
+    x, its, res, res0, _ = krylov.fgmres(lambda v: G @ v, b, lambda v: mg.precondition(lv, v, mg.MGParams()),
+                                         rtol=1e-13, restart=40, maxit=400)
+    xd = np.linalg.solve(G.toarray(), b)
+    assert np.linalg.norm(x - xd) <= 1e-10 * np.linalg.norm(xd)
+    assert res <= 1e-12 * res0
+
+
+def test_mg_iterations_bounded_under_refinement():
+    """h-robustness of the monolithic MG preconditioner (Sec. 5: iteration counts insensitive
+    to refinement); 2D single crack, FGMRES to 1e-8."""
+    counts = []
+    for n, L in ((16, 2), (32, 3), (64, 4)):
+        w = W.small(W.config_2d_single_crack(), n, L)
+        m = fem.Mesh(2, 1, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(eps=w.eps, p=w.pressure, kappa=w.kappa)
+        U, po, pt = W.initial_state(w)
+        R = -fem.residual_A(m, ph, U, pt)
+        act = pdas.active_set(m, R, fem.lumped_mass(m), U, po, 100.0)
+        dmask = fem.dirichlet_face_mask(m, 0x3F)
+        Rt, mask = pdas.eliminated_rhs(m, ph, U, pt, po, dmask, act, R)
+        lv = mg.build_levels(m, L, ph, U, pt, mask)
+        mg.estimate_levels(lv, 12345, 10)
+        G = lv[-1].G
+        _, its, res, res0, _ = krylov.fgmres(lambda v: G @ v, Rt,
+                                             lambda v: mg.precondition(lv, v, mg.MGParams()), rtol=1e-8)
+        assert res <= 1e-8 * res0 * 1.0001
+        counts.append(its)
+    assert max(counts) <= 25
+    assert counts[-1] <= 2 * counts[0] + 2
+
+
+def test_sneddon_crack_volume_2d():
+    """Loose physics pin: pressurised crack of half length l0 in plane strain; Sneddon's crack
+    volume V = 2 pi (1 - nu^2) p l0^2 / E.  Phase-field volume = int u . grad(phi^2).  The
+    half length is taken from the discrete phase field; O(eps) and finite-domain bias remain, so
+    only ~8% agreement is asked."""
+    n = 160
+    w = W.small(W.config_2d_single_crack(), n, 1)
+    m = fem.Mesh(2, 1, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(eps=w.eps, p=w.pressure, kappa=w.kappa)
+    U, po, pt = W.initial_state(w)
+    mask = fem.dirichlet_face_mask(m, 0x3F) | np.uint8(fem.BIT_PHI_DIR)
+    G = fem.assemble(m, ph, U, pt, mask)
+    R = -fem.residual_A(m, ph, U, pt)
+    cons = fem.constrained_dofs(m, mask)
+    R[cons] = 0.0
+    import scipy.sparse.linalg as spla
+    dU = spla.spsolve(G.tocsc(), R)
+    U1 = U + dU
+    # opening volume V_pf = int u . grad(phi^2) = -int phi^2 div u (u = 0 on the boundary):
+    # the u-rows of A at u = 0, p = 1, phi~ = phi are (phi^2, div Phi_i), so V_pf = -sum_i u_i A_i
+    ph1 = fem.Phys(eps=w.eps, p=1.0, kappa=w.kappa)
+    Ub = U.copy(); Ub[: 2 * m.n_nodes] = 0.0
+    Au = fem.residual_A(m, ph1, Ub, U[2 * m.n_nodes:])[: 2 * m.n_nodes]
+    vol_pf = -float(Au @ U1[: 2 * m.n_nodes])
+    # effective half length: the phi = 1/2 level along the crack line (the initial crack covers
+    # every cell meeting |x| <= 1, so phi = 0 nodes reach past x = 1 and phi ramps over one cell)
+    X = m.node_coords()
+    phi = U[2 * m.n_nodes:]
+    on_line = np.abs(X[:, 1]) < 1e-12
+    l_eff = np.abs(X[on_line & (phi == 0.0), 0]).max() + 0.5 * w.edge
+    E, nu, p = w.E, w.nu, w.pressure
+    vol = 2 * math.pi * (1 - nu ** 2) * p * l_eff ** 2 / E
+    assert vol_pf == pytest.approx(vol, rel=0.08)
+    assert vol_pf > 0
+
+
+def test_active_set_complementarity_at_convergence():
+    """At PDAS convergence: phi <= phi_old, phi = phi_old on the active set, the multiplier
+    lambda = M^-1 R is >= 0 on the active set and ~0 on the inactive set (Algorithm 1)."""
+    w = W.small(W.config_2d_single_crack(), 16, 2)
+    m = fem.Mesh(2, 1, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(eps=w.eps, p=w.pressure * 50, kappa=w.kappa)
+    U, po, pt = W.initial_state(w)
+    dmask = fem.dirichlet_face_mask(m, 0x3F)
+    prev = None
+    for k in range(12):
+        U, info = pdas.newton_step(m, ph, 2, U, po, pt, dmask, prev, rtol=1e-12)
+        if info.converged:
+            break
+        prev = info.active
+    assert info.converged
+    nn = m.n_nodes
+    phi = U[2 * nn:]
+    R = -fem.residual_A(m, ph, U, pt)
+    lam = R[2 * nn:] / fem.lumped_mass(m)
+    act = info.active
+    assert (phi <= po + 1e-9).all()
+    np.testing.assert_allclose(phi[act], po[act], atol=1e-9)
+    assert (lam[act] >= -1e-8).all()
+    assert np.abs(lam[~act]).max() <= 1e-6
