@@ -1,0 +1,339 @@
+"""Benchmark of the matrix-free phase-field fracture solver on one GB300 (or N replicas).
+
+Workload (default): 3D pressurised penny crack, [-10,10]^3, 128^3 Q1 hexahedra (8.6M DoFs),
+5-level geometric multigrid, E=1, nu=0.2, Gc=1, kappa=1e-10, eps=2h, p=1e-3; synthetic seeded
+state (initial crack phase field, smooth displacement), active set from Algorithm 1 step 3.
+
+One timed step = one primal-dual active-set step (Algorithm 1) on that system: residual,
+active set, restriction of state and active set to all levels, diagonals and CG eigenvalue
+estimates, FGMRES to 1e-8 with the FP32 V-cycle, update.  The reported metric is the
+Jacobian-apply throughput in GDoF/s: fine DoFs / mean device time of the FP64 fine-level
+Jacobian applies launched inside the timed steps (CUDA events on the library's stream).
+Secondary keys give the V-cycle time and the time to a 1e-8 solve with FP32-MG and FP64-MG.
+
+--impl reference times the CPU oracle (assembled CSR Jacobian, scipy SpMV, 1 thread) on a
+bounded sample of the same recipe.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian-apply GDoF/s; time-to-1e-8 solve FP32-MG vs FP64-MG; solves/s, p99"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(n: int = 24, seconds: float = 3.0):
+    """Oracle Jacobian apply (assembled CSR, scipy SpMV, 1 thread) on an n^3 sample of the recipe."""
+    from oracle import fem
+    from paper_1902_08112_gb300 import workloads as W
+    w = W.small(W.config_3d_penny(), n, 1)
+    U, po, pt = W.initial_state(w, displacement="smooth")
+    m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+    mask = fem.dirichlet_face_mask(m, 0x3F)
+    t0 = time.perf_counter()
+    G = fem.assemble(m, ph, U, pt, mask)
+    t_asm = time.perf_counter() - t0
+    x = W.random_vector(m.n_dofs, 7)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        y = G @ x
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    gdofs = m.n_dofs * reps / el / 1e9
+    return {"value": gdofs, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"3D penny recipe at {n}^3 Q1 ({m.n_dofs} DoFs): scipy CSR SpMV of the oracle's "
+                      f"assembled Jacobian, {reps} applies in {el:.2f} s; assembly {t_asm:.1f} s excluded"}, float(y[0])
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    from oracle import fem
+    from paper_1902_08112_gb300 import workloads as W
+    n = 24
+    w = W.small(W.config_3d_penny(), n, 1)
+    U, po, pt = W.initial_state(w, displacement="smooth")
+    m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+    G = fem.assemble(m, ph, U, pt, fem.dirichlet_face_mask(m, 0x3F))
+    x = W.random_vector(m.n_dofs, 7)
+    for _ in range(args.warmup):
+        G @ x
+    reps_per_step = 20
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(reps_per_step):
+            G @ x
+    el = time.perf_counter() - t0
+    val = m.n_dofs * reps_per_step * args.steps / el / 1e9
+    sample = f"3D penny recipe at {n}^3 Q1 ({m.n_dofs} DoFs): oracle CSR SpMV, {reps_per_step} applies per step"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "3d_penny_q1_128 (oracle sample 24^3)"},
+            "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pff", choices=["pff", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="cells per edge of the 3D penny workload")
+    ap.add_argument("--levels", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1902_08112_gb300 import pff, workloads as W
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    w = W.config_3d_penny(n=args.n, n_levels=args.levels)
+    U0, po, pt = W.initial_state(w, displacement="smooth")
+    stream = torch.cuda.Stream(device=dev)
+    prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
+                             mg_precision=32)
+    h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm, stream)
+    nd, nn = w.n_dofs, w.n_nodes
+    with torch.cuda.stream(stream):
+        U0_d = torch.from_numpy(U0).to(dev)
+        po_d = torch.from_numpy(po).to(dev)
+        pt_d = torch.from_numpy(pt).to(dev)
+        U = U0_d.clone()
+    stream.synchronize()
+    pff.set_state(h, U0_d, po_d, pt_d)
+    n_act, _ = pff.update_active_set(h)
+
+    def step():
+        with torch.cuda.stream(stream):
+            U.copy_(U0_d)
+        return pff.newton_step(h, U, allow_noconv=True)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    barrier()
+    pff.profile(h, True)
+    launches0 = pff.launch_count()
+    infos = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    launches = pff.launch_count() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    cnt64, ms64 = pff.profile_read(h, pff.PROF_APPLY64_FINE)
+    cnt64c, ms64c = pff.profile_read(h, pff.PROF_APPLY64_COARSE)
+    cnt32, ms32 = pff.profile_read(h, pff.PROF_APPLY32)
+    pff.profile(h, False)
+    if ws > 1:
+        t = torch.tensor([ms_total, ms64 / max(cnt64, 1)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total, apply_ms = float(t[0]), float(t[1])
+    else:
+        apply_ms = ms64 / max(cnt64, 1)
+    ms_step = ms_total / args.steps
+    value = ws * nd / (apply_ms * 1e-3) / 1e9
+
+    # ---- secondary measurements (outside the timed region)
+    def timed(fn, reps=3):
+        fn()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rng = np.random.default_rng(3)
+    with torch.cuda.stream(stream):
+        r = torch.from_numpy(rng.standard_normal(nd)).to(dev)
+        z = torch.empty_like(r)
+        xs = torch.zeros_like(r)
+    stream.synchronize()
+    # Newton right-hand side of the benchmark state for the two solve variants
+    res = {}
+    for mgp in (32, 64):
+        pff.set_params(h, pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps,
+                                             pressure=w.pressure, mg_precision=mgp))
+        pff.set_state(h, U0_d, po_d, pt_d)
+        pff.update_active_set(h)
+        pff.setup(h)
+        vc_ms = timed(lambda: pff.vcycle(h, r, z))
+        R = torch.empty(nd, dtype=torch.float64, device=dev)
+        pff.residual(h, R)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            xs.zero_()
+        info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=200, allow_noconv=True)
+        stream.synchronize()
+        solve_ms = (time.perf_counter() - t0) * 1e3
+        res[f"fp{mgp}_mg"] = {"vcycle_ms": vc_ms, "solve_ms": solve_ms, "iterations": info.iterations,
+                              "rel_res": info.res_final / max(info.res0, 1e-300)}
+
+    # ---- end to end through the C ABI with host buffers (H2D of x, apply, D2H of y)
+    xh = torch.from_numpy(rng.standard_normal(nd)).pin_memory()
+    yh = torch.empty(nd, dtype=torch.float64).pin_memory()
+    xd = torch.empty(nd, dtype=torch.float64, device=dev)
+    yd = torch.empty(nd, dtype=torch.float64, device=dev)
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            xd.copy_(xh, non_blocking=True)
+        pff.apply_jacobian(h, -1, xd, yd)
+        with torch.cuda.stream(stream):
+            yh.copy_(yd, non_blocking=True)
+    e2e_ms = timed(e2e_step, reps=max(3, args.steps))
+
+    # ---- roofline of the dominant kernel class inside the timed steps
+    classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32)}
+    dom = max(classes, key=lambda k: classes[k][1])
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if dom == "apply64_fine":
+        bytes_per = 105.0 * nn
+        achieved = bytes_per / (apply_ms * 1e-3) / 1e9
+    else:
+        c, ms = classes[dom]
+        bytes_per = None
+        achieved = None
+    roof = {"kernel": "level_apply FP64 fine (k_cell OP_APPLY)" if dom == "apply64_fine" else dom,
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+            "algorithmic_bytes_per_launch": bytes_per,
+            "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"3d_penny_q1_{args.n}", "n_dofs": nd, "levels": w.n_levels,
+                   "step": "one active-set Newton step (FP32 V-cycle in FP64 FGMRES to 1e-8)",
+                   "l2": "inputs larger than L2 (one FP64 apply touches ~%.0f MB)" % (105.0 * nn / 1e6),
+                   "parallelism": f"replicas{ws}"},
+        "clocks": clk.summary(),
+        "e2e": {"value": nd / (e2e_ms * 1e-3) / 1e9 * ws, "unit": "GDoF/s", "h2d_bytes_per_step": nd * 8,
+                "d2h_bytes_per_step": nd * 8},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in classes.items()},
+        "newton": {"gmres_iterations": [i.solve.iterations for i in infos], "n_active": n_act},
+        "solve": res,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline()
+        line["cpu_baseline"] = cb
+    pff.destroy_hierarchy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

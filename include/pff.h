@@ -1,0 +1,250 @@
+/*
+ * pff.h -- C ABI of the GB300 matrix-free multigrid solver for pressurised phase-field
+ * fracture (Jodlbauer, Langer, Wick: "Matrix-free multigrid solvers for phase-field fracture
+ * problems", arXiv 1902.08112).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Vectors are DEVICE pointers on the GPU the hierarchy was created on, caller-owned,
+ *    contiguous, in the component-blocked layout [u_x | u_y | (u_z) | phi]: entry
+ *    (comp, node) sits at comp * n_nodes + node, nodes lexicographic with x fastest.  The
+ *    number of components is dim + 1.  FP64 vectors are double*, FP32 vectors float*.
+ *  - Levels are numbered 0 (coarsest) .. n_levels-1 (finest); level -1 means the finest.
+ *  - Every call is stream-ordered on the stream given at creation and asynchronous, except
+ *    the calls that fill a host-side info/out struct, which synchronise that stream.
+ *  - Errors are returned as pff_status; no exception, abort or device trap crosses the ABI.
+ *    pff_last_error() gives a one-line description of the last failure of a hierarchy.
+ *  - Node mask bits (uint8 per node): PFF_MASK_UX/UY/UZ = displacement component clamped
+ *    (Dirichlet), PFF_MASK_ACTIVE = phase field in the active set, PFF_MASK_PHI_DIR = phase
+ *    field clamped.  A masked (eliminated) DoF has an identity row and a zero column in every
+ *    operator (Algorithm 1, step 4).
+ *  - The library owns its level data, masks, preconditioner data and Krylov workspace; they
+ *    are allocated once in pff_create_hierarchy and freed by pff_destroy_hierarchy.
+ */
+#ifndef PFF_H
+#define PFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pff_hierarchy pff_hierarchy;
+
+typedef enum {
+    PFF_OK = 0,
+    PFF_EINVAL = 1,      /* bad argument (sizes, level, null pointer, unsupported option) */
+    PFF_ENOMEM = 2,      /* device or host allocation failed */
+    PFF_ECUDA = 3,       /* a CUDA runtime call failed */
+    PFF_ENOCONV = 4,     /* iteration cap reached before the tolerance */
+    PFF_ENONFINITE = 5,  /* NaN/Inf found in a residual norm or Arnoldi norm */
+    PFF_ETIMEOUT = 6,    /* a bounded device-side wait ran out */
+    PFF_ESTATE = 7       /* call out of order (e.g. apply before pff_set_state) */
+} pff_status;
+
+enum {
+    PFF_MASK_UX = 1,
+    PFF_MASK_UY = 2,
+    PFF_MASK_UZ = 4,
+    PFF_MASK_ACTIVE = 8,
+    PFF_MASK_PHI_DIR = 16
+};
+
+/* Mesh: a uniform box [lo, hi] with n_cells[a] hexahedra (dim 3) or quadrilaterals (dim 2)
+ * per axis, Q1 or Q2 Lagrange elements for u and phi (Sec. 2.4; Q2 is an extension), and a
+ * nested hierarchy of n_levels uniform grids (each coarsening halves every axis, so
+ * n_cells[a] must be divisible by 2^(n_levels-1)).
+ * dirichlet_faces: bit 2a clamps all displacement components on the lower face of axis a,
+ * bit 2a+1 on the upper face (0x3F = every face, the pressurised-crack setting of Sec. 2.1).
+ * dirichlet_mask: optional HOST array of fine-level node masks (PFF_MASK_U* bits) OR-ed into
+ * the face mask; NULL for none.  Coarse levels inherit masks from the coincident fine nodes. */
+typedef struct {
+    int dim;
+    int degree;
+    int n_cells[3];
+    int n_levels;
+    double lo[3];
+    double hi[3];
+    unsigned dirichlet_faces;
+    const uint8_t* dirichlet_mask;
+} pff_mesh;
+
+/* Problem and solver parameters.
+ *  E, nu          Young's modulus and Poisson ratio; Lame coefficients by the 3D formulas
+ *                 (plane strain in 2D), as in the parameter table of Sec. 5.1.
+ *  Gc, kappa, eps critical energy release rate, residual stiffness of g_kappa, phase-field
+ *                 width (Problem 2.1, Sec. 2.1).
+ *  pressure       constant crack pressure p (Problem 2.1).
+ *  c_as, tol_as   active-set constant c and tolerance eps_as (remark after Algorithm 1:
+ *                 100 and 1e-10).  tol_as also decides ties of the active-set test.
+ *  phi_elastic_factor  factor f on the phi-equation elastic term f (g'(phi) E_s, psi).
+ *                 1 = derivative of the bulk energy of Sec. 5 (default); 0.5 = the literal
+ *                 factor printed in Eq. (semilinear).
+ *  mg_precision   32: whole V-cycle in FP32 with FP32 accumulation (inside FP64 FGMRES);
+ *                 64: all-FP64 V-cycle.  The coarse solve is always FP64.
+ *  cheb_degree    Chebyshev degree of the smoother (Sec. 3.2.1: 4).
+ *  cg_steps       CG steps of the eigenvalue estimate (Sec. 3.2.1: 10).
+ *  cheb_safety, cheb_ratio  smoothing range [ratio*safety*l, safety*l] (1.2 and 1/5).
+ *  coarse_rtol, coarse_maxit  Chebyshev coarse solver: steps from the Chebyshev error bound
+ *                 for this reduction, capped (Sec. 3.2.2 gives neither).
+ *  seed           seed of the SplitMix64 start vector of the CG eigenvalue estimate. */
+typedef struct {
+    double E, nu, Gc, kappa, eps, pressure;
+    double c_as, tol_as;
+    double phi_elastic_factor;
+    int mg_precision;
+    int cheb_degree;
+    int cg_steps;
+    double cheb_safety;
+    double cheb_ratio;
+    double coarse_rtol;
+    int coarse_maxit;
+    uint64_t seed;
+} pff_params;
+
+typedef struct {
+    int iterations;        /* FGMRES iterations (Arnoldi steps) */
+    int converged;         /* 1 if ||b - G x|| <= rtol ||b - G x0|| */
+    double res0;           /* ||b - G x0|| */
+    double res_final;      /* true residual norm at exit */
+} pff_solve_info;
+
+typedef struct {
+    int n_active;          /* size of the active set A_k */
+    int n_changed;         /* |A_k xor A_{k-1}| */
+    double res_norm;       /* ||R~_k||_2 (right-hand side of the eliminated system) */
+    int converged;         /* A_k == A_{k-1} and res_norm <= tol_as (Algorithm 1) */
+    pff_solve_info solve;  /* the linear solve of step 5 */
+} pff_newton_info;
+
+/* Fill *p with the defaults quoted above (E=1, nu=0.2, Gc=1, kappa=1e-10, eps=1, p=1e-3,
+ * c=100, eps_as=1e-10, f=1, FP32 V-cycle, degree 4, 10 CG steps, 1.2, 0.2, 1e-6, 200, 12345). */
+void pff_default_params(pff_params* p);
+
+/* Create the level hierarchy (Sec. 3.2 and 4.2) on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  Allocates all device memory the solver needs.
+ * Errors: PFF_EINVAL (sizes, degree, levels), PFF_ENOMEM, PFF_ECUDA.  *out is NULL on error. */
+pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_params* params, void* cuda_stream,
+                                pff_hierarchy** out);
+
+/* Free every allocation of the hierarchy (synchronises its stream).  NULL is a no-op. */
+pff_status pff_destroy_hierarchy(pff_hierarchy* h);
+
+/* Sizes of a level: nodes, cells and nodes per axis (host outputs, any may be NULL). */
+pff_status pff_level_info(const pff_hierarchy* h, int level, int64_t* n_nodes, int64_t* n_cells,
+                          int nodes_per_axis[3]);
+
+/* Replace the parameters used by later calls (same mesh).  Marks the preconditioner stale. */
+pff_status pff_set_params(pff_hierarchy* h, const pff_params* params);
+
+/* Set the linearisation point.  U: FP64 [u | phi] (n_dofs), phi_old: FP64 (n_nodes) = the
+ * irreversibility bound, phi_tilde: FP64 (n_nodes) = the extrapolation used in the
+ * displacement equation (Eq. (semilinear)).  The library copies them, restricts U and
+ * phi_tilde to every coarser level by coincident nodes (Sec. 4.2), and keeps FP32 copies.
+ * The current active set is kept.  Errors: PFF_EINVAL (NULL). */
+pff_status pff_set_state(pff_hierarchy* h, const double* U, const double* phi_old,
+                         const double* phi_tilde);
+
+/* Set the active set from a device array of n_nodes bytes (nonzero = active) and carry it to
+ * every coarser level by coincident nodes (Sec. 4.2).  Marks the preconditioner stale. */
+pff_status pff_set_active_set(pff_hierarchy* h, const uint8_t* active);
+
+/* Copy the fine-level active indicator (0/1 bytes, n_nodes) to a device array. */
+pff_status pff_get_active_set(const pff_hierarchy* h, uint8_t* active);
+
+/* Steps 1 and 3 of Algorithm 1 at the current state: R = -A(U), lambda = M^-1 R on the phi
+ * DoFs with the lumped Gauss-Lobatto mass, active iff lambda + c (phi - phi_old) > tol_as.
+ * Installs the new active set on all levels.  Host outputs (may be NULL): the set size and
+ * the number of nodes that changed.  Synchronises. */
+pff_status pff_update_active_set(pff_hierarchy* h, int* n_active, int* n_changed);
+
+/* Residual R = -A(U) of Eq. (semilinear) at the current fine state, all DoFs, no elimination
+ * (FP64, device output of n_dofs). */
+pff_status pff_residual(pff_hierarchy* h, double* R);
+
+/* Matrix-free Jacobian apply y = G~_l(U_l) x on a level (Sec. 4.1, 4.2), FP64: the level's
+ * operator at its restricted state, eliminated rows give y = x, eliminated columns are
+ * ignored.  x and y must not overlap.  The finest level is the Newton Jacobian G~_k. */
+pff_status pff_apply_jacobian(pff_hierarchy* h, int level, const double* x, double* y);
+
+/* The same operator evaluated in FP32 arithmetic with FP32 accumulation (V-cycle operator). */
+pff_status pff_apply_jacobian_f32(pff_hierarchy* h, int level, const float* x, float* y);
+
+/* Diagonal of G~_l (1 on eliminated rows), computed matrix-free (remark in Sec. 4.1).
+ * precision 64 -> double* d, 32 -> float* d. */
+pff_status pff_diagonal(pff_hierarchy* h, int level, int precision, void* d);
+
+/* Restricted state of a level (device outputs, any may be NULL): U_l (FP64, n_dofs_l),
+ * phi_tilde_l (FP64, n_nodes_l), mask_l (uint8, n_nodes_l). */
+pff_status pff_level_state(const pff_hierarchy* h, int level, double* U, double* phi_tilde,
+                           uint8_t* mask);
+
+/* Transfers between level l-1 (coarse) and l (fine), canonical for nested Q1/Q2 (Sec. 3.2):
+ * restrict: r_c = P^T r_f with eliminated coarse entries set to 0;
+ * prolongate_add: x_f += P e_c on the free fine entries.  precision 32 or 64. */
+pff_status pff_restrict(pff_hierarchy* h, int fine_level, int precision, const void* r_fine,
+                        void* r_coarse);
+pff_status pff_prolongate_add(pff_hierarchy* h, int fine_level, int precision,
+                              const void* e_coarse, void* x_fine);
+
+/* Build the preconditioner at the current state and active set: level diagonals and the
+ * eigenvalue bounds of 10 Jacobi-preconditioned CG steps per diagonal block (Sec. 3.2.1).
+ * Called implicitly by the smoother, V-cycle and solver when stale. */
+pff_status pff_setup(pff_hierarchy* h);
+
+/* Eigenvalue estimates of D^-1 G_bb on a level (host out[4]: lmin_u, lmax_u, lmin_phi,
+ * lmax_phi; synchronises). */
+pff_status pff_eigen_estimates(pff_hierarchy* h, int level, double out[4]);
+
+/* Block-diagonal Chebyshev-Jacobi smoother S_full (Sec. 3.2.1, 3.3) on level l, degree
+ * cheb_degree, range [ratio*safety*l, safety*l] per block:  x <- x + S(b - G~_l x)
+ * (zero_guess != 0: x <- S(b), x is output only).  Entries of b on eliminated DoFs must be
+ * 0.  precision 32 or 64. */
+pff_status pff_smooth(pff_hierarchy* h, int level, int precision, const void* b, void* x,
+                      int zero_guess);
+
+/* Coarse solve on level 0 (Sec. 3.2.2): Chebyshev on [0.9 lmin, 1.2 lmax] of each block, in
+ * block forward-substitution order (u first, then phi with the coupling on the right), FP64. */
+pff_status pff_coarse_solve(pff_hierarchy* h, const double* b, double* x);
+
+/* One V-cycle of P_full^-1 = MG(G~) (Sec. 3.3): z ~ G~^-1 r; eliminated entries z_i = r_i.
+ * Runs in params.mg_precision (FP64 in/out either way). */
+pff_status pff_vcycle(pff_hierarchy* h, const double* r, double* z);
+
+/* Right-preconditioned flexible GMRES(restart) in FP64 with the V-cycle as preconditioner:
+ * solve G~ x = b from the given x (initial guess, overwritten), until
+ * ||b - G~ x|| <= rtol ||b - G~ x0|| or maxit iterations.  info (host, may be NULL) is
+ * filled and the call synchronises.  Returns PFF_ENOCONV at the cap, PFF_ENONFINITE on
+ * NaN/Inf. */
+pff_status pff_gmres_solve(pff_hierarchy* h, const double* b, double* x, double rtol, int restart,
+                           int maxit, pff_solve_info* info);
+
+/* One primal-dual active-set step (Algorithm 1) at state U (device FP64 in/out, n_dofs) with
+ * the phi_old and phi_tilde of the last pff_set_state: residual, active set, elimination
+ * (active rows carry phi_old - phi), FGMRES + V-cycle solve to rtol 1e-8 (restart 30,
+ * maxit 200), U += dU.  The new U becomes the hierarchy's state. */
+pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_info* info);
+
+/* Kernel timing (tracing).  pff_profile(h, 1) clears the counters and starts recording CUDA
+ * events on the hierarchy's stream around every level-operator launch (the preset of eliminated
+ * rows plus the cell kernel); pff_profile(h, 0) stops.  pff_profile_read synchronises and
+ * returns, for one class, the number of launches and their summed device time in ms.
+ * Classes: PFF_PROF_APPLY64_FINE (FP64 operator on the finest level), PFF_PROF_APPLY64_COARSE
+ * (FP64 operators on coarser levels), PFF_PROF_APPLY32 (FP32 operators, all levels). */
+enum { PFF_PROF_APPLY64_FINE = 0, PFF_PROF_APPLY64_COARSE = 1, PFF_PROF_APPLY32 = 2, PFF_PROF_NCLASS = 3 };
+pff_status pff_profile(pff_hierarchy* h, int enable);
+pff_status pff_profile_read(pff_hierarchy* h, int cls, int* count, double* total_ms);
+
+/* Number of kernel launches this library has issued in the process so far (tracing). */
+long long pff_launch_count(void);
+
+/* Last error message of a hierarchy (never NULL; "" when none). */
+const char* pff_last_error(const pff_hierarchy* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFF_H */

@@ -1,0 +1,594 @@
+// C ABI of the pff library (declarations and contracts in include/pff.h).
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "pff_solver.cuh"
+
+using namespace pff;
+
+static pff_status fail(pff_hierarchy* h, pff_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+#define CUDA_OR_FAIL(h, expr)                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) return fail(h, PFF_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define REQUIRE(h, cond, st, msg) \
+    do {                          \
+        if (!(cond)) return fail(h, st, msg); \
+    } while (0)
+
+extern "C" void pff_default_params(pff_params* p) {
+    if (!p) return;
+    p->E = 1.0;
+    p->nu = 0.2;
+    p->Gc = 1.0;
+    p->kappa = 1e-10;
+    p->eps = 1.0;
+    p->pressure = 1e-3;
+    p->c_as = 100.0;
+    p->tol_as = 1e-10;
+    p->phi_elastic_factor = 1.0;
+    p->mg_precision = 32;
+    p->cheb_degree = 4;
+    p->cg_steps = 10;
+    p->cheb_safety = 1.2;
+    p->cheb_ratio = 0.2;
+    p->coarse_rtol = 1e-6;
+    p->coarse_maxit = 200;
+    p->seed = 12345;
+}
+
+// Gauss-Legendre rule with deg+1 points mapped to [0,1] and the Lagrange basis on the
+// equispaced nodes a/deg evaluated there (value and derivative).
+static void make_tables(int deg, Tables& tb) {
+    memset(&tb, 0, sizeof(tb));
+    const int np = deg + 1;
+    double xq[3], wq[3];
+    if (np == 2) {
+        const double r = 1.0 / sqrt(3.0);
+        xq[0] = 0.5 * (1.0 - r);
+        xq[1] = 0.5 * (1.0 + r);
+        wq[0] = wq[1] = 0.5;
+    } else {
+        const double r = sqrt(3.0 / 5.0);
+        xq[0] = 0.5 * (1.0 - r);
+        xq[1] = 0.5;
+        xq[2] = 0.5 * (1.0 + r);
+        wq[0] = wq[2] = 5.0 / 18.0;
+        wq[1] = 8.0 / 18.0;
+    }
+    for (int q = 0; q < np; ++q) {
+        tb.w1[q] = wq[q];
+        const double t = xq[q];
+        if (deg == 1) {
+            tb.N1[0][q] = 1.0 - t;
+            tb.N1[1][q] = t;
+            tb.D1[0][q] = -1.0;
+            tb.D1[1][q] = 1.0;
+        } else {
+            tb.N1[0][q] = 2.0 * t * t - 3.0 * t + 1.0;
+            tb.N1[1][q] = 4.0 * t - 4.0 * t * t;
+            tb.N1[2][q] = 2.0 * t * t - t;
+            tb.D1[0][q] = 4.0 * t - 3.0;
+            tb.D1[1][q] = 4.0 - 8.0 * t;
+            tb.D1[2][q] = 4.0 * t - 1.0;
+        }
+    }
+}
+
+static Phys make_phys(const pff_params& p) {
+    Phys ph;
+    ph.mu = p.E / (2.0 * (1.0 + p.nu));
+    ph.lam = p.E * p.nu / ((1.0 + p.nu) * (1.0 - 2.0 * p.nu));
+    ph.Gc = p.Gc;
+    ph.kappa = p.kappa;
+    ph.eps = p.eps;
+    ph.p = p.pressure;
+    ph.f = p.phi_elastic_factor;
+    return ph;
+}
+
+static const char* check_params(const pff_params* p) {
+    if (!p) return "params is NULL";
+    if (!(p->E > 0) || !(p->nu > -1.0 && p->nu < 0.5)) return "need E > 0 and -1 < nu < 0.5";
+    if (!(p->eps > 0) || !(p->Gc >= 0) || !(p->kappa >= 0 && p->kappa < 1)) return "need eps > 0, Gc >= 0, 0 <= kappa < 1";
+    if (p->mg_precision != 32 && p->mg_precision != 64) return "mg_precision must be 32 or 64";
+    if (p->cheb_degree < 1 || p->cheb_degree > 64) return "cheb_degree must be in [1, 64]";
+    if (p->cg_steps < 1 || p->cg_steps > 50) return "cg_steps must be in [1, 50]";
+    if (!(p->cheb_safety > 0) || !(p->cheb_ratio > 0 && p->cheb_ratio < 1)) return "need cheb_safety > 0, 0 < cheb_ratio < 1";
+    if (!(p->coarse_rtol > 0 && p->coarse_rtol < 1) || p->coarse_maxit < 1) return "need 0 < coarse_rtol < 1, coarse_maxit >= 1";
+    return nullptr;
+}
+
+static void free_all(pff_hierarchy* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+template <typename T>
+static cudaError_t dalloc(pff_hierarchy* h, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(q);
+    *p = reinterpret_cast<T*>(q);
+    return cudaMemsetAsync(q, 0, count * sizeof(T) + 16, h->stream);
+}
+
+extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_params* params, void* cuda_stream,
+                                           pff_hierarchy** out) {
+    if (!out) return PFF_EINVAL;
+    *out = nullptr;
+    if (!mesh) return PFF_EINVAL;
+    if (check_params(params)) return PFF_EINVAL;
+    if (mesh->dim != 2 && mesh->dim != 3) return PFF_EINVAL;
+    if (mesh->degree != 1 && mesh->degree != 2) return PFF_EINVAL;
+    if (mesh->n_levels < 1 || mesh->n_levels > 16) return PFF_EINVAL;
+    const int div = 1 << (mesh->n_levels - 1);
+    for (int a = 0; a < mesh->dim; ++a) {
+        if (mesh->n_cells[a] < 1 || mesh->n_cells[a] % div != 0) return PFF_EINVAL;
+        if (!(mesh->hi[a] > mesh->lo[a])) return PFF_EINVAL;
+    }
+    pff_hierarchy* h = new (std::nothrow) pff_hierarchy();
+    if (!h) return PFF_ENOMEM;
+    h->mesh = *mesh;
+    h->mesh.dirichlet_mask = nullptr;
+    h->prm = *params;
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    h->L = mesh->n_levels;
+    h->ph = make_phys(*params);
+    make_tables(mesh->degree, h->tb);
+    h->lv.resize(h->L);
+    pff_status st = PFF_OK;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < h->L && e == cudaSuccess; ++l) {
+        Level& L = h->lv[l];
+        Geom& g = L.g;
+        g.dim = mesh->dim;
+        g.deg = mesh->degree;
+        const int f = 1 << (h->L - 1 - l);
+        g.n_nodes = 1;
+        g.n_cells = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (a < mesh->dim) {
+                g.nc[a] = mesh->n_cells[a] / f;
+                g.nn[a] = g.deg * g.nc[a] + 1;
+                g.h[a] = (mesh->hi[a] - mesh->lo[a]) / g.nc[a];
+            } else {
+                g.nc[a] = 1;
+                g.nn[a] = 1;
+                g.h[a] = 1.0;
+            }
+            g.n_nodes *= g.nn[a];
+            if (a < mesh->dim) g.n_cells *= g.nc[a];
+        }
+        const size_t nn = (size_t)g.n_nodes, nd = (size_t)n_dofs(g);
+        if (e == cudaSuccess) e = dalloc(h, &L.mask, nn);
+        if (e == cudaSuccess) e = dalloc(h, &L.U64, nd);
+        if (e == cudaSuccess) e = dalloc(h, &L.pt64, nn);
+        if (e == cudaSuccess) e = dalloc(h, &L.U32, nd);
+        if (e == cudaSuccess) e = dalloc(h, &L.pt32, nn);
+        if (e == cudaSuccess) e = dalloc(h, &L.dinv64, nd);
+        if (e == cudaSuccess) e = dalloc(h, &L.dinv32, nd);
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+            float* wf = nullptr;
+            double* wd = nullptr;
+            e = dalloc(h, &wf, nd);
+            if (e == cudaSuccess) e = dalloc(h, &wd, nd);
+            L.w[0][k] = wf;
+            L.w[1][k] = wd;
+        }
+    }
+    Level& F = h->lv[h->L - 1];
+    const size_t nnf = (size_t)F.g.n_nodes, ndf = (size_t)n_dofs(F.g);
+    if (e == cudaSuccess) e = dalloc(h, &h->dir_mask, nnf);
+    if (e == cudaSuccess) e = dalloc(h, &h->phi_old, nnf);
+    if (e == cudaSuccess) e = dalloc(h, &h->lumped, nnf);
+    if (e == cudaSuccess) e = dalloc(h, &h->R, ndf);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = dalloc(h, &h->tmp64[k], ndf);
+    if (e == cudaSuccess) e = dalloc(h, &h->prev_active, nnf);
+    if (e == cudaSuccess) e = dalloc(h, &h->d_counts, 16);
+    if (e == cudaSuccess) e = dalloc(h, &h->d_scal, 4096);
+    if (e == cudaSuccess) e = dalloc(h, &h->d_scratch, (size_t)dot_partials() * 64);
+    if (e != cudaSuccess) {
+        st = (e == cudaErrorMemoryAllocation) ? PFF_ENOMEM : PFF_ECUDA;
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return st;
+    }
+    // Dirichlet mask of the finest level (faces + optional host mask), copied to every level
+    uint8_t* extra = nullptr;
+    if (mesh->dirichlet_mask) {
+        if (dalloc(h, &extra, nnf) != cudaSuccess ||
+            cudaMemcpyAsync(extra, mesh->dirichlet_mask, nnf, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
+            free_all(h);
+            delete h;
+            return PFF_ECUDA;
+        }
+    }
+    e = launch_face_mask(F.g, mesh->dirichlet_faces, extra, h->dir_mask, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F.mask, h->dir_mask, nnf, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = propagate_state(h);
+    if (e == cudaSuccess) e = launch_lumped_mass(F.g, h->lumped, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return PFF_ECUDA;
+    }
+    *out = h;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_destroy_hierarchy(pff_hierarchy* h) {
+    if (!h) return PFF_OK;
+    cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    free_all(h);
+    delete h;
+    return PFF_OK;
+}
+
+static int resolve_level(const pff_hierarchy* h, int level) { return level < 0 ? h->L - 1 : level; }
+
+extern "C" pff_status pff_level_info(const pff_hierarchy* h, int level, int64_t* n_nodes, int64_t* n_cells,
+                                     int nodes_per_axis[3]) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return PFF_EINVAL;
+    const Geom& g = h->lv[l].g;
+    if (n_nodes) *n_nodes = g.n_nodes;
+    if (n_cells) *n_cells = g.n_cells;
+    if (nodes_per_axis)
+        for (int a = 0; a < 3; ++a) nodes_per_axis[a] = g.nn[a];
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_set_params(pff_hierarchy* h, const pff_params* params) {
+    if (!h) return PFF_EINVAL;
+    const char* why = check_params(params);
+    REQUIRE(h, !why, PFF_EINVAL, why ? why : "");
+    h->prm = *params;
+    h->ph = make_phys(*params);
+    h->stale = true;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_set_state(pff_hierarchy* h, const double* U, const double* phi_old,
+                                    const double* phi_tilde) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, U && phi_old && phi_tilde, PFF_EINVAL, "pff_set_state: NULL vector");
+    Level& F = h->lv[h->L - 1];
+    const size_t nn = (size_t)F.g.n_nodes, nd = (size_t)n_dofs(F.g);
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(F.pt64, phi_tilde, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->phi_old, phi_old, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_OR_FAIL(h, propagate_state(h));
+    h->has_state = true;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_set_active_set(pff_hierarchy* h, const uint8_t* active) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, active, PFF_EINVAL, "pff_set_active_set: NULL");
+    Level& F = h->lv[h->L - 1];
+    CUDA_OR_FAIL(h, launch_set_active(F.g, active, F.mask, h->stream));
+    CUDA_OR_FAIL(h, propagate_state(h));
+    h->active_known = true;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_get_active_set(const pff_hierarchy* h, uint8_t* active) {
+    if (!h || !active) return PFF_EINVAL;
+    const Level& F = h->lv[h->L - 1];
+    cudaError_t e = launch_get_active(F.g, F.mask, active, h->stream);
+    return e == cudaSuccess ? PFF_OK : PFF_ECUDA;
+}
+
+// Steps 1 and 3 of Algorithm 1; returns counts on the host.
+static pff_status update_active(pff_hierarchy* h, int* n_active, int* n_changed) {
+    Level& F = h->lv[h->L - 1];
+    CUDA_OR_FAIL(h, residual_fine(h, h->R));
+    CUDA_OR_FAIL(h, cudaMemsetAsync(h->d_counts, 0, 2 * sizeof(int), h->stream));
+    CUDA_OR_FAIL(h, launch_active_set(F.g, h->R, h->lumped, F.U64, h->phi_old, h->prm.c_as, h->prm.tol_as, F.mask,
+                                      h->d_counts, h->stream));
+    int cnt[2] = {0, 0};
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(cnt, h->d_counts, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    if (!h->active_known) cnt[1] = cnt[0];
+    h->active_known = true;
+    CUDA_OR_FAIL(h, propagate_state(h));
+    if (n_active) *n_active = cnt[0];
+    if (n_changed) *n_changed = cnt[1];
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_update_active_set(pff_hierarchy* h, int* n_active, int* n_changed) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, h->has_state, PFF_ESTATE, "pff_update_active_set before pff_set_state");
+    return update_active(h, n_active, n_changed);
+}
+
+extern "C" pff_status pff_residual(pff_hierarchy* h, double* R) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, R, PFF_EINVAL, "pff_residual: NULL");
+    REQUIRE(h, h->has_state, PFF_ESTATE, "pff_residual before pff_set_state");
+    CUDA_OR_FAIL(h, residual_fine(h, R));
+    return PFF_OK;
+}
+
+template <typename T>
+static pff_status apply_checked(pff_hierarchy* h, int level, const T* x, T* y) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, level);
+    REQUIRE(h, l >= 0 && l < h->L, PFF_EINVAL, "level out of range");
+    REQUIRE(h, x && y && (const void*)x != (const void*)y, PFF_EINVAL, "apply: NULL or aliased vectors");
+    REQUIRE(h, h->has_state, PFF_ESTATE, "apply before pff_set_state");
+    CUDA_OR_FAIL(h, apply_level<T>(h, l, OP_APPLY, x, y, PHI_BITS_ALL));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_apply_jacobian(pff_hierarchy* h, int level, const double* x, double* y) {
+    return apply_checked<double>(h, level, x, y);
+}
+
+extern "C" pff_status pff_apply_jacobian_f32(pff_hierarchy* h, int level, const float* x, float* y) {
+    return apply_checked<float>(h, level, x, y);
+}
+
+extern "C" pff_status pff_diagonal(pff_hierarchy* h, int level, int precision, void* d) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, level);
+    REQUIRE(h, l >= 0 && l < h->L && d, PFF_EINVAL, "pff_diagonal: bad level or NULL");
+    REQUIRE(h, precision == 32 || precision == 64, PFF_EINVAL, "precision must be 32 or 64");
+    REQUIRE(h, h->has_state, PFF_ESTATE, "pff_diagonal before pff_set_state");
+    if (precision == 64) CUDA_OR_FAIL(h, diagonal_level<double>(h, l, (double*)d));
+    else CUDA_OR_FAIL(h, diagonal_level<float>(h, l, (float*)d));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_level_state(const pff_hierarchy* h, int level, double* U, double* phi_tilde,
+                                      uint8_t* mask) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return PFF_EINVAL;
+    const Level& L = h->lv[l];
+    cudaError_t e = cudaSuccess;
+    if (U) e = cudaMemcpyAsync(U, L.U64, sizeof(double) * n_dofs(L.g), cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && phi_tilde)
+        e = cudaMemcpyAsync(phi_tilde, L.pt64, sizeof(double) * L.g.n_nodes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && mask) e = cudaMemcpyAsync(mask, L.mask, L.g.n_nodes, cudaMemcpyDeviceToDevice, h->stream);
+    return e == cudaSuccess ? PFF_OK : PFF_ECUDA;
+}
+
+extern "C" pff_status pff_restrict(pff_hierarchy* h, int fine_level, int precision, const void* r_fine,
+                                   void* r_coarse) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, fine_level);
+    REQUIRE(h, l >= 1 && l < h->L && r_fine && r_coarse, PFF_EINVAL, "pff_restrict: bad level or NULL");
+    REQUIRE(h, precision == 32 || precision == 64, PFF_EINVAL, "precision must be 32 or 64");
+    Level& C = h->lv[l - 1];
+    Level& F = h->lv[l];
+    if (precision == 64)
+        CUDA_OR_FAIL(h, launch_restrict<double>(C.g, F.g, (const double*)r_fine, (double*)r_coarse, C.mask, h->stream));
+    else
+        CUDA_OR_FAIL(h, launch_restrict<float>(C.g, F.g, (const float*)r_fine, (float*)r_coarse, C.mask, h->stream));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_prolongate_add(pff_hierarchy* h, int fine_level, int precision, const void* e_coarse,
+                                         void* x_fine) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, fine_level);
+    REQUIRE(h, l >= 1 && l < h->L && e_coarse && x_fine, PFF_EINVAL, "pff_prolongate_add: bad level or NULL");
+    REQUIRE(h, precision == 32 || precision == 64, PFF_EINVAL, "precision must be 32 or 64");
+    Level& C = h->lv[l - 1];
+    Level& F = h->lv[l];
+    if (precision == 64)
+        CUDA_OR_FAIL(h, launch_prolongate_add<double>(C.g, F.g, (const double*)e_coarse, (double*)x_fine, F.mask,
+                                                      h->stream));
+    else
+        CUDA_OR_FAIL(h, launch_prolongate_add<float>(C.g, F.g, (const float*)e_coarse, (float*)x_fine, F.mask,
+                                                     h->stream));
+    return PFF_OK;
+}
+
+static pff_status ensure_setup(pff_hierarchy* h) {
+    REQUIRE(h, h->has_state, PFF_ESTATE, "preconditioner needs pff_set_state first");
+    if (h->stale) CUDA_OR_FAIL(h, setup(h));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_setup(pff_hierarchy* h) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, h->has_state, PFF_ESTATE, "pff_setup before pff_set_state");
+    CUDA_OR_FAIL(h, setup(h));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_eigen_estimates(pff_hierarchy* h, int level, double out[4]) {
+    if (!h || !out) return PFF_EINVAL;
+    const int l = resolve_level(h, level);
+    REQUIRE(h, l >= 0 && l < h->L, PFF_EINVAL, "level out of range");
+    pff_status st = ensure_setup(h);
+    if (st != PFF_OK) return st;
+    const Level& L = h->lv[l];
+    out[0] = L.lam_min[0];
+    out[1] = L.lam_max[0];
+    out[2] = L.lam_min[1];
+    out[3] = L.lam_max[1];
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_smooth(pff_hierarchy* h, int level, int precision, const void* b, void* x, int zero_guess) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, level);
+    REQUIRE(h, l >= 0 && l < h->L && b && x && b != x, PFF_EINVAL, "pff_smooth: bad level, NULL or aliased");
+    REQUIRE(h, precision == 32 || precision == 64, PFF_EINVAL, "precision must be 32 or 64");
+    pff_status st = ensure_setup(h);
+    if (st != PFF_OK) return st;
+    if (precision == 64) CUDA_OR_FAIL(h, smooth<double>(h, l, (const double*)b, (double*)x, zero_guess));
+    else CUDA_OR_FAIL(h, smooth<float>(h, l, (const float*)b, (float*)x, zero_guess));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_coarse_solve(pff_hierarchy* h, const double* b, double* x) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, b && x && b != x, PFF_EINVAL, "pff_coarse_solve: NULL or aliased");
+    pff_status st = ensure_setup(h);
+    if (st != PFF_OK) return st;
+    CUDA_OR_FAIL(h, coarse_solve(h, b, x));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_vcycle(pff_hierarchy* h, const double* r, double* z) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, r && z && r != z, PFF_EINVAL, "pff_vcycle: NULL or aliased");
+    pff_status st = ensure_setup(h);
+    if (st != PFF_OK) return st;
+    CUDA_OR_FAIL(h, vcycle(h, r, z));
+    return PFF_OK;
+}
+
+static pff_status ensure_krylov(pff_hierarchy* h, int m) {
+    if (h->kr_m >= m) return PFF_OK;
+    const size_t n = (size_t)n_dofs(h->lv[h->L - 1].g);
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    if (h->kr_V) {   // release the old workspace
+        for (void* p : {(void*)h->kr_V, (void*)h->kr_Z, (void*)h->kr_h}) {
+            for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+                if (*it == p) { cudaFree(p); h->allocs.erase(it); break; }
+        }
+        h->kr_V = h->kr_Z = h->kr_h = nullptr;
+        h->kr_m = 0;
+    }
+    cudaError_t e = dalloc(h, &h->kr_V, (size_t)(m + 1) * n);
+    if (e == cudaSuccess) e = dalloc(h, &h->kr_Z, (size_t)m * n);
+    if (e == cudaSuccess) e = dalloc(h, &h->kr_h, (size_t)2 * (m + 1) + 2);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, e == cudaErrorMemoryAllocation ? PFF_ENOMEM : PFF_ECUDA, "Krylov workspace allocation failed");
+    }
+    h->kr_m = m;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_gmres_solve(pff_hierarchy* h, const double* b, double* x, double rtol, int restart,
+                                      int maxit, pff_solve_info* info) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, b && x && b != x, PFF_EINVAL, "pff_gmres_solve: NULL or aliased");
+    REQUIRE(h, rtol > 0 && rtol < 1 && restart >= 1 && restart <= 1000 && maxit >= 1, PFF_EINVAL,
+            "pff_gmres_solve: need 0 < rtol < 1, 1 <= restart <= 1000, maxit >= 1");
+    pff_status st = ensure_setup(h);
+    if (st != PFF_OK) return st;
+    st = ensure_krylov(h, restart);
+    if (st != PFF_OK) return st;
+    std::string err;
+    st = fgmres(h, b, x, rtol, restart, maxit, info, err);
+    if (st != PFF_OK) h->err = err;
+    return st;
+}
+
+extern "C" pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_info* info) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, U, PFF_EINVAL, "pff_newton_step: NULL");
+    REQUIRE(h, h->has_state, PFF_ESTATE, "pff_newton_step before pff_set_state");
+    Level& F = h->lv[h->L - 1];
+    const int64_t nd = n_dofs(F.g);
+    cudaStream_t s = h->stream;
+    // state U (phi_old, phi~ from the last pff_set_state)
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_OR_FAIL(h, propagate_state(h));
+    int n_act = 0, n_chg = 0;
+    pff_status st = update_active(h, &n_act, &n_chg);
+    if (st != PFF_OK) return st;
+    // eliminated right-hand side: active rows carry phi_old - phi, their columns move right
+    double* Rt = h->tmp64[1];
+    double* t = h->tmp64[2];
+    CUDA_OR_FAIL(h, launch_active_delta(F.g, F.U64, h->phi_old, F.mask, Rt, s));
+    CUDA_OR_FAIL(h, apply_level<double>(h, h->L - 1, OP_APPLY, Rt, t, PFF_MASK_PHI_DIR));
+    CUDA_OR_FAIL(h, launch_newton_rhs(F.g, h->R, t, F.U64, h->phi_old, F.mask, Rt, s));
+    CUDA_OR_FAIL(h, launch_norm2(nd, Rt, h->d_scratch, h->d_scal + 300, s));
+    double res = 0.0;
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(&res, h->d_scal + 300, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(s));
+    // solve G~ dU = R~
+    st = ensure_setup(h);
+    if (st != PFF_OK) return st;
+    st = ensure_krylov(h, 30);
+    if (st != PFF_OK) return st;
+    double* dU = h->tmp64[2];
+    CUDA_OR_FAIL(h, cudaMemsetAsync(dU, 0, nd * sizeof(double), s));
+    pff_solve_info si;
+    memset(&si, 0, sizeof(si));
+    std::string err;
+    st = fgmres(h, Rt, dU, 1e-8, 30, 200, &si, err);
+    if (st != PFF_OK && st != PFF_ENOCONV) {
+        h->err = err;
+        return st;
+    }
+    CUDA_OR_FAIL(h, launch_axpby<double>(nd, 1.0, dU, 1.0, U, s));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_OR_FAIL(h, propagate_state(h));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(s));
+    if (info) {
+        info->n_active = n_act;
+        info->n_changed = n_chg;
+        info->res_norm = res;
+        info->solve = si;
+        info->converged = (n_chg == 0 && res <= h->prm.tol_as) ? 1 : 0;
+    }
+    if (st == PFF_ENOCONV) h->err = err;
+    return st;
+}
+
+extern "C" pff_status pff_profile(pff_hierarchy* h, int enable) {
+    if (!h) return PFF_EINVAL;
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    for (auto& v : h->prof) v.clear();
+    h->ev_used = 0;
+    h->prof_on = enable != 0;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_profile_read(pff_hierarchy* h, int cls, int* count, double* total_ms) {
+    if (!h || cls < 0 || cls >= PFF_PROF_NCLASS) return PFF_EINVAL;
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    double tot = 0.0;
+    for (auto& pr : h->prof[cls]) {
+        float ms = 0.f;
+        CUDA_OR_FAIL(h, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+    }
+    if (count) *count = (int)h->prof[cls].size();
+    if (total_ms) *total_ms = tot;
+    return PFF_OK;
+}
+
+extern "C" const char* pff_last_error(const pff_hierarchy* h) {
+    if (!h) return "null hierarchy";
+    return h->err.c_str();
+}
+
+#include <atomic>
+
+namespace pff {
+static std::atomic<long long> g_launches{0};
+cudaError_t count_launch(cudaError_t e) {
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace pff
+
+extern "C" long long pff_launch_count(void) { return pff::launch_count(); }

@@ -1,0 +1,196 @@
+"""GPU parity of the level operators, transfers and preconditioner pieces against the oracle.
+
+All calls go through the C ABI (paper_1902_08112_gb300.pff).  Inputs come from the seeded
+generators of paper_1902_08112_gb300.workloads; expected values from oracle/ only.
+
+Tolerances: FP64 operators 1e-12 relative (normwise, the spec bar); FP32 operators 2e-5
+(FP32 unit roundoff 6e-8 times the ~100-term sums of a cell evaluation, with margin); solver
+pieces built on the FP64 operators 1e-9 (eigenvalue estimates enter through Chebyshev
+coefficients; 10 CG steps amplify rounding).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fem, multigrid as mg  # noqa: E402
+from paper_1902_08112_gb300 import pff, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def t(a, dtype=None):
+    x = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        x = x.to(dtype)
+    return x.to(DEV)
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy().astype(np.float64) if hasattr(a, "cpu") else np.asarray(a, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+class Case:
+    """A hierarchy on the GPU and the oracle's levels for the same inputs."""
+
+    def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0):
+        self.w = w
+        if state == "random":
+            U, po, pt = W.random_state(w)
+        else:
+            U, po, pt = W.initial_state(w, displacement="smooth")
+        self.U, self.po, self.pt = U, po, pt
+        self.prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu,
+                                      Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f)
+        self.h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), self.prm)
+        pff.set_state(self.h, t(U), t(po), t(pt))
+        act = W.random_active(w, active_fraction) if active_fraction > 0 else np.zeros(w.n_nodes, np.uint8)
+        pff.set_active_set(self.h, t(act))
+        self.mesh = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
+        self.phys = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, f=f)
+        self.mask = fem.dirichlet_face_mask(self.mesh, 0x3F) | (act * fem.BIT_ACTIVE).astype(np.uint8)
+        self.levels = mg.build_levels(self.mesh, w.n_levels, self.phys, U, pt, self.mask)
+
+    def close(self):
+        pff.destroy_hierarchy(self.h)
+
+
+CASES = {
+    "2d_q1": lambda: W.small(W.config_2d_single_crack(), 24, 3),
+    "2d_q2": lambda: W.small(W.config_2d_single_crack(deg=2), 12, 2),
+    "3d_q1": lambda: W.small(W.config_3d_penny(), 12, 2),
+    "3d_q2": lambda: W.small(W.config_3d_penny(deg=2), 6, 2),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    c = Case(CASES[request.param]())
+    yield c
+    c.close()
+
+
+def test_level_state_restriction_exact(case):
+    for l, lev in enumerate(case.levels):
+        n = lev.mesh.n_nodes
+        U = torch.empty(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        pt = torch.empty(n, dtype=torch.float64, device=DEV)
+        m = torch.empty(n, dtype=torch.uint8, device=DEV)
+        pff.level_state(case.h, l, U, pt, m)
+        np.testing.assert_array_equal(U.cpu().numpy(), lev.U)
+        np.testing.assert_array_equal(pt.cpu().numpy(), lev.ptil)
+        np.testing.assert_array_equal(m.cpu().numpy(), lev.mask)
+
+
+def test_apply_fp64_matches_assembled_product(case):
+    for l, lev in enumerate(case.levels):
+        x = W.random_vector(lev.mesh.n_dofs, 100 + l)
+        y = torch.empty(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        pff.apply_jacobian(case.h, l, t(x), y)
+        ref = lev.G @ x
+        assert rel(y, ref) <= 1e-12, (l, rel(y, ref))
+
+
+def test_apply_fp32_matches_assembled_product(case):
+    for l, lev in enumerate(case.levels):
+        x = W.random_vector(lev.mesh.n_dofs, 200 + l).astype(np.float32)
+        y = torch.empty(lev.mesh.n_dofs, dtype=torch.float32, device=DEV)
+        pff.apply_jacobian_f32(case.h, l, t(x), y)
+        ref = lev.G @ x.astype(np.float64)
+        assert rel(y, ref) <= 2e-5, (l, rel(y, ref))
+
+
+def test_eliminated_rows_are_identity(case):
+    lev = case.levels[-1]
+    x = W.random_vector(lev.mesh.n_dofs, 300)
+    y = torch.empty(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+    pff.apply_jacobian(case.h, -1, t(x), y)
+    cons = ~lev.free
+    np.testing.assert_array_equal(y.cpu().numpy()[cons], x[cons])
+
+
+def test_residual_matches_oracle(case):
+    R = torch.empty(case.mesh.n_dofs, dtype=torch.float64, device=DEV)
+    pff.residual(case.h, R)
+    ref = -fem.residual_A(case.mesh, case.phys, case.U, case.pt)
+    assert rel(R, ref) <= 1e-12
+
+
+def test_diagonal_matches_oracle(case):
+    for l, lev in enumerate(case.levels):
+        d = torch.empty(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        pff.diagonal(case.h, l, 64, d)
+        assert rel(d, lev.G.diagonal()) <= 1e-12
+
+
+def test_transfers_match_oracle(case):
+    for l in range(1, len(case.levels)):
+        f, c = case.levels[l], case.levels[l - 1]
+        r = W.random_vector(f.mesh.n_dofs, 400 + l)
+        rc = torch.empty(c.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        pff.restrict(case.h, l, 64, t(r), rc)
+        ref = f.P.T @ r
+        ref[~c.free] = 0.0
+        assert rel(rc, ref) <= 1e-14
+        e = W.random_vector(c.mesh.n_dofs, 500 + l)
+        x0 = W.random_vector(f.mesh.n_dofs, 600 + l)
+        xf = t(x0.copy())
+        pff.prolongate_add(case.h, l, 64, t(e), xf)
+        corr = f.P @ e
+        corr[~f.free] = 0.0
+        assert rel(xf, x0 + corr) <= 1e-14
+
+
+@pytest.fixture(scope="module")
+def solver_case():
+    c = Case(W.small(W.config_3d_penny(), 8, 2), active_fraction=0.05, state="initial")
+    mg.estimate_levels(c.levels, 12345, 10)
+    yield c
+    c.close()
+
+
+def test_eigen_estimates_match_oracle(solver_case):
+    c = solver_case
+    for l, lev in enumerate(c.levels):
+        lm = pff.eigen_estimates(c.h, l)
+        np.testing.assert_allclose(lm, [lev.lam_min[0], lev.lam_max[0], lev.lam_min[1], lev.lam_max[1]], rtol=1e-9)
+
+
+def test_smoother_matches_oracle(solver_case):
+    c = solver_case
+    prm = mg.MGParams()
+    for l, lev in enumerate(c.levels):
+        b = np.where(lev.free, W.random_vector(lev.mesh.n_dofs, 700 + l), 0.0)
+        x = torch.zeros(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        pff.smooth(c.h, l, 64, t(b), x, True)
+        ref = mg.smooth_zero(lev, b, prm)
+        assert rel(x, ref) <= 1e-9
+        # with an initial guess: x0 + S(b - G x0)
+        x0 = np.where(lev.free, W.random_vector(lev.mesh.n_dofs, 800 + l), 0.0)
+        xg = t(x0.copy())
+        pff.smooth(c.h, l, 64, t(b), xg, False)
+        ref = x0 + mg.smooth_zero(lev, b - lev.G @ x0, prm)
+        assert rel(xg, ref) <= 1e-9
+
+
+def test_coarse_solve_matches_oracle(solver_case):
+    c = solver_case
+    lev = c.levels[0]
+    b = np.where(lev.free, W.random_vector(lev.mesh.n_dofs, 900), 0.0)
+    x = torch.zeros(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+    pff.coarse_solve(c.h, t(b), x)
+    ref = mg.coarse_solve(lev, b, mg.MGParams())
+    assert rel(x, ref) <= 1e-9
+
+
+def test_vcycle_fp64_matches_oracle(solver_case):
+    c = solver_case
+    v = W.random_vector(c.mesh.n_dofs, 1000)
+    z = torch.zeros(c.mesh.n_dofs, dtype=torch.float64, device=DEV)
+    pff.vcycle(c.h, t(v), z)
+    ref = mg.precondition(c.levels, v, mg.MGParams())
+    assert rel(z, ref) <= 1e-9

@@ -1,0 +1,134 @@
+"""GPU solver parity against the oracle: FGMRES + V-cycle iteration counts (within 10%, the
+spec bar; +-1 allowed for the FP32 V-cycle whose smoother runs in FP32), true residual
+at 1e-8, one active-set step of Algorithm 1 (same active set, same residual norm, solution
+satisfying the oracle's eliminated system), and sampled full-size apply parity."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fem, multigrid as mg, krylov, pdas  # noqa: E402
+from paper_1902_08112_gb300 import pff, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def make(w, mg_precision, state="initial"):
+    U, po, pt = W.initial_state(w, displacement="smooth") if state == "initial" else W.random_state(w)
+    prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu, Gc=w.Gc,
+                             mg_precision=mg_precision)
+    h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), prm)
+    pff.set_state(h, t(U), t(po), t(pt))
+    return h, U, po, pt
+
+
+def oracle_system(w, U, po, pt):
+    m = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+    R = -fem.residual_A(m, ph, U, pt)
+    act = pdas.active_set(m, R, fem.lumped_mass(m), U, po, 100.0, 1e-10)
+    dmask = fem.dirichlet_face_mask(m, 0x3F)
+    Rt, mask = pdas.eliminated_rhs(m, ph, U, pt, po, dmask, act, R)
+    lv = mg.build_levels(m, w.n_levels, ph, U, pt, mask)
+    mg.estimate_levels(lv, 12345, 10)
+    return m, ph, act, Rt, lv
+
+
+SOLVE_CASES = {
+    "2d_q1_64": lambda: W.config_2d_single_crack(),            # the 2D config itself (3 levels)
+    "3d_q1_16": lambda: W.small(W.config_3d_penny(), 16, 3),
+    "3d_q2_8": lambda: W.small(W.config_3d_penny(deg=2), 8, 2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SOLVE_CASES))
+@pytest.mark.parametrize("mgp", [64, 32])
+def test_fgmres_iterations_match_oracle(name, mgp):
+    w = SOLVE_CASES[name]()
+    h, U, po, pt = make(w, mgp)
+    try:
+        na, _ = pff.update_active_set(h)
+        m, ph, act, Rt, lv = oracle_system(w, U, po, pt)
+        active = torch.empty(w.n_nodes, dtype=torch.uint8, device=DEV)
+        pff.get_active_set(h, active)
+        np.testing.assert_array_equal(active.cpu().numpy().astype(bool), act)
+        G = lv[-1].G
+        _, its_o, res_o, res0_o, _ = krylov.fgmres(lambda v: G @ v, Rt,
+                                                   lambda v: mg.precondition(lv, v, mg.MGParams()),
+                                                   rtol=1e-8, restart=30, maxit=200)
+        x = torch.zeros(w.n_dofs, dtype=torch.float64, device=DEV)
+        info = pff.gmres_solve(h, t(Rt), x, rtol=1e-8, restart=30, maxit=200)
+        assert info.converged
+        slack = max(1, math.floor(0.1 * its_o)) if mgp == 32 else math.floor(0.1 * its_o)
+        assert abs(info.iterations - its_o) <= slack, (info.iterations, its_o)
+        # the GPU solution satisfies the oracle's assembled system to the solver tolerance
+        xr = x.cpu().numpy()
+        assert np.linalg.norm(Rt - G @ xr) <= 1.01e-8 * np.linalg.norm(Rt)
+    finally:
+        pff.destroy_hierarchy(h)
+
+
+@pytest.mark.parametrize("mgp", [64, 32])
+def test_newton_step_matches_oracle(mgp):
+    w = W.small(W.config_2d_single_crack(), 32, 3)
+    w.pressure = 0.05
+    h, U, po, pt = make(w, mgp)
+    try:
+        m = fem.Mesh(2, 1, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+        dmask = fem.dirichlet_face_mask(m, 0x3F)
+        Ud = t(U)
+        Uo = U.copy()
+        prev = None
+        for k in range(3):
+            info = pff.newton_step(h, Ud)
+            Uo_new, oi = pdas.newton_step(m, ph, 3, Uo, po, pt, dmask, prev)
+            assert info.n_active == int(oi.active.sum())
+            assert info.n_changed == oi.n_changed
+            assert info.res_norm == pytest.approx(oi.res_norm, rel=1e-6, abs=1e-12)
+            slack = 1 if mgp == 32 else 0
+            assert abs(info.solve.iterations - oi.gmres_its) <= max(slack, math.floor(0.1 * oi.gmres_its))
+            Ug = Ud.cpu().numpy()
+            assert np.linalg.norm(Ug - Uo_new) <= 1e-6 * np.linalg.norm(Uo_new)
+            Uo, prev = Uo_new, oi.active
+            Ud = t(Uo)     # continue both from the oracle's iterate
+            if oi.converged:
+                break
+    finally:
+        pff.destroy_hierarchy(h)
+
+
+def test_full_size_apply_sampled_rows():
+    """The 3D penny workload at its full size (128^3 Q1, 8.6M DoFs), FP64 apply, 4000 sampled
+    rows against the oracle's row-by-row element computation."""
+    w = W.config_3d_penny()
+    h, U, po, pt = make(w, 32)
+    try:
+        pff.update_active_set(h)
+        active = torch.empty(w.n_nodes, dtype=torch.uint8, device=DEV)
+        pff.get_active_set(h, active)
+        act = active.cpu().numpy()
+        m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+        mask = fem.dirichlet_face_mask(m, 0x3F) | (act * fem.BIT_ACTIVE).astype(np.uint8)
+        x = W.random_vector(w.n_dofs, 11)
+        y = torch.empty(w.n_dofs, dtype=torch.float64, device=DEV)
+        pff.apply_jacobian(h, -1, t(x), y)
+        rng = np.random.default_rng(5)
+        rows = rng.choice(w.n_dofs, 4000, replace=False)
+        # include rows at the crack and on the boundary
+        crack_nodes = np.flatnonzero(po == 0.0)
+        rows = np.concatenate([rows, crack_nodes[:200] + 3 * w.n_nodes, crack_nodes[:200], np.arange(50)])
+        ref = fem.apply_rows(m, ph, U, pt, mask, x, rows)
+        got = y.cpu().numpy()[rows]
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-12 * scale
+    finally:
+        pff.destroy_hierarchy(h)
