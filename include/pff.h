@@ -139,6 +139,12 @@ pff_status pff_level_info(const pff_hierarchy* h, int level, int64_t* n_nodes, i
 /* Replace the parameters used by later calls (same mesh).  Marks the preconditioner stale. */
 pff_status pff_set_params(pff_hierarchy* h, const pff_params* params);
 
+/* Kernel variant of the level operators: 0 (default) = Q1 fast path (Gauss-point linearisation
+ * data precomputed in FP64 per state; FP64-accurate operators evaluated in double-float
+ * arithmetic, FP32 operators in FP32), 1 = generic kernels (Q1 and Q2, native FP64 or FP32,
+ * state evaluated at every apply).  Q2 meshes always use the generic kernels. */
+pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant);
+
 /* Set the linearisation point.  U: FP64 [u | phi] (n_dofs), phi_old: FP64 (n_nodes) = the
  * irreversibility bound, phi_tilde: FP64 (n_nodes) = the extrapolation used in the
  * displacement equation (Eq. (semilinear)).  The library copies them, restricts U and

@@ -5,6 +5,7 @@
 #include <new>
 #include <string>
 
+#include "pff_q1.cuh"
 #include "pff_solver.cuh"
 
 using namespace pff;
@@ -178,6 +179,11 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
         if (e == cudaSuccess) e = dalloc(h, &L.pt32, nn);
         if (e == cudaSuccess) e = dalloc(h, &L.dinv64, nd);
         if (e == cudaSuccess) e = dalloc(h, &L.dinv32, nd);
+        if (e == cudaSuccess && g.deg == 1) {
+            const size_t nq = (size_t)q1_nk(g.dim) * (size_t)(1 << g.dim) * (size_t)g.n_cells;
+            e = dalloc(h, &L.qpd32, nq);
+            if (e == cudaSuccess) e = dalloc(h, &L.qpd64, nq);
+        }
         for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
             float* wf = nullptr;
             double* wd = nullptr;
@@ -260,6 +266,15 @@ extern "C" pff_status pff_set_params(pff_hierarchy* h, const pff_params* params)
     REQUIRE(h, !why, PFF_EINVAL, why ? why : "");
     h->prm = *params;
     h->ph = make_phys(*params);
+    if (h->has_state) CUDA_OR_FAIL(h, propagate_state(h));   // linearisation data depend on the physics
+    h->stale = true;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, variant == 0 || variant == 1, PFF_EINVAL, "variant must be 0 (Q1 fast path) or 1 (generic)");
+    h->fast_q1 = variant == 0;
     h->stale = true;
     return PFF_OK;
 }

@@ -51,6 +51,8 @@ struct Level {
     double* dinv64 = nullptr;    // inverse operator diagonal (1 on eliminated rows)
     float* dinv32 = nullptr;
     void* w[2][6] = {{nullptr}}; // V-cycle work vectors, [0]=FP32, [1]=FP64
+    float* qpd32 = nullptr;      // Q1: Gauss-point linearisation coefficients, FP32
+    float2* qpd64 = nullptr;     // Q1: the same as df64 pairs (hi, lo)
     double lam_min[2] = {1, 1};  // eigenvalue estimates of D^-1 G_bb, blocks u / phi
     double lam_max[2] = {1, 1};
 };
@@ -186,6 +188,7 @@ struct pff_hierarchy {
     double* kr_Z = nullptr;
     double* kr_h = nullptr;          // device column of H (2 * (m + 1))
     bool has_state = false;
+    bool fast_q1 = true;             // Q1 levels use the linearisation-data kernels of pff_q1.cu
     bool active_known = false;       // an active set has been computed or set
     bool stale = true;               // preconditioner data out of date
     std::vector<void*> allocs;       // every device allocation, freed on destroy

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <vector>
 
+#include "pff_q1.cuh"
 #include "pff_solver.cuh"
 
 namespace pff {
@@ -56,18 +57,26 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
         if (e0 && e1) CK(cudaEventRecord(e0, h->stream));
     }
     CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, phi_bits, x, y, T(0), h->stream));
-    CellArgs<T> a;
-    a.g = L.g;
-    a.ph = h->ph;
-    a.tb = h->tb;
-    a.x = x;
-    a.y = y;
-    a.U = stU<T>(L);
-    a.pt = stPt<T>(L);
-    a.mask = L.mask;
-    a.phi_bits = phi_bits;
-    a.u_bits = MASK_U_ALL;
-    CK(launch_cell_op<T>(op, a, h->stream));
+    if (h->fast_q1 && L.g.deg == 1 && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
+        const bool bd = op == OP_APPLY_BLOCKDIAG;
+        if constexpr (sizeof(T) == 8)
+            CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd, h->stream));
+        else
+            CK(launch_q1_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd, h->stream));
+    } else {
+        CellArgs<T> a;
+        a.g = L.g;
+        a.ph = h->ph;
+        a.tb = h->tb;
+        a.x = x;
+        a.y = y;
+        a.U = stU<T>(L);
+        a.pt = stPt<T>(L);
+        a.mask = L.mask;
+        a.phi_bits = phi_bits;
+        a.u_bits = MASK_U_ALL;
+        CK(launch_cell_op<T>(op, a, h->stream));
+    }
     if (e0 && e1) {
         CK(cudaEventRecord(e1, h->stream));
         const int cls = sizeof(T) == 4 ? PFF_PROF_APPLY32 : (l == h->L - 1 ? PFF_PROF_APPLY64_FINE : PFF_PROF_APPLY64_COARSE);
@@ -125,6 +134,7 @@ cudaError_t propagate_state(pff_hierarchy* h) {
     for (auto& L : h->lv) {
         CK(launch_cast_f64_f32(L.U64, L.U32, n_dofs(L.g), h->stream));
         CK(launch_cast_f64_f32(L.pt64, L.pt32, L.g.n_nodes, h->stream));
+        if (L.qpd64) CK(launch_q1_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
     }
     h->stale = true;
     return cudaSuccess;

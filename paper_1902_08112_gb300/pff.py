@@ -52,6 +52,7 @@ SIGNATURES = {
     "pff_destroy_hierarchy": (_I, [_VP]),
     "pff_level_info": (_I, [_VP, _I, _I64P, _I64P, ctypes.POINTER(ctypes.c_int)]),
     "pff_set_params": (_I, [_VP, ctypes.POINTER(Params)]),
+    "pff_set_kernel_variant": (_I, [_VP, _I]),
     "pff_set_state": (_I, [_VP, _VP, _VP, _VP]),
     "pff_set_active_set": (_I, [_VP, _VP]),
     "pff_get_active_set": (_I, [_VP, _VP]),
@@ -164,6 +165,10 @@ def level_info(h, level=-1):
 
 def set_params(h, params: Params):
     return _check(h, load().pff_set_params(h, ctypes.byref(params)), "pff_set_params")
+
+
+def set_kernel_variant(h, variant: int):
+    return _check(h, load().pff_set_kernel_variant(h, variant), "pff_set_kernel_variant")
 
 
 def set_state(h, U, phi_old, phi_tilde):

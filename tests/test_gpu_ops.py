@@ -37,7 +37,7 @@ def rel(a, b):
 class Case:
     """A hierarchy on the GPU and the oracle's levels for the same inputs."""
 
-    def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0):
+    def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0, variant=0):
         self.w = w
         if state == "random":
             U, po, pt = W.random_state(w)
@@ -47,6 +47,7 @@ class Case:
         self.prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu,
                                       Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f)
         self.h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), self.prm)
+        pff.set_kernel_variant(self.h, variant)
         pff.set_state(self.h, t(U), t(po), t(pt))
         act = W.random_active(w, active_fraction) if active_fraction > 0 else np.zeros(w.n_nodes, np.uint8)
         pff.set_active_set(self.h, t(act))
@@ -59,17 +60,22 @@ class Case:
         pff.destroy_hierarchy(self.h)
 
 
+# (workload, kernel variant): 0 = Q1 fast path (df64 / FP32 with stored linearisation data),
+# 1 = generic kernels.  Sizes span several tiles with ragged edges.
 CASES = {
-    "2d_q1": lambda: W.small(W.config_2d_single_crack(), 24, 3),
-    "2d_q2": lambda: W.small(W.config_2d_single_crack(deg=2), 12, 2),
-    "3d_q1": lambda: W.small(W.config_3d_penny(), 12, 2),
-    "3d_q2": lambda: W.small(W.config_3d_penny(deg=2), 6, 2),
+    "2d_q1": (lambda: W.small(W.config_2d_single_crack(), 40, 3), 0),
+    "2d_q1_generic": (lambda: W.small(W.config_2d_single_crack(), 24, 3), 1),
+    "2d_q2": (lambda: W.small(W.config_2d_single_crack(deg=2), 12, 2), 1),
+    "3d_q1": (lambda: W.small(W.config_3d_penny(), 20, 3), 0),
+    "3d_q1_generic": (lambda: W.small(W.config_3d_penny(), 12, 2), 1),
+    "3d_q2": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1),
 }
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
 def case(request):
-    c = Case(CASES[request.param]())
+    make_w, variant = CASES[request.param]
+    c = Case(make_w(), variant=variant)
     yield c
     c.close()
 
