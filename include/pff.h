@@ -243,6 +243,28 @@ enum { PFF_PROF_APPLY64_FINE = 0, PFF_PROF_APPLY64_COARSE = 1, PFF_PROF_APPLY32 
 pff_status pff_profile(pff_hierarchy* h, int enable);
 pff_status pff_profile_read(pff_hierarchy* h, int cls, int* count, double* total_ms);
 
+/* Allocation-free active-set decision for callers that cannot allocate device memory (for
+ * example a process whose GPU memory belongs to another allocator, or code that may not call
+ * cudaMalloc and so cannot create a hierarchy).  The paper has no counterpart: this is the
+ * decision of pff_update_active_set (Algorithm 1, step 3: active iff
+ * R_i / M_ii + c (phi_i - phi_old_i) > tol_as with the Gauss-Lobatto lumped mass M) on caller
+ * buffers, without a hierarchy and without any device allocation.
+ *   mesh     the fine mesh (dim, degree, n_cells, lo, hi are used; n_levels is ignored).
+ *   params   c_as and tol_as are used.
+ *   R        device FP64, n_dofs: the residual -A(U), e.g. from pff_residual.
+ *   U        device FP64, n_dofs: the state [u | phi].   phi_old: device FP64, n_nodes.
+ *   mask     device uint8, n_nodes, in/out: PFF_MASK_ACTIVE is rewritten, other bits kept.
+ *   n_active, n_changed  host outputs (may be NULL); the call synchronises cuda_stream.
+ * Scratch: a file-scope device array of 2 * 65536 + 2 ints (about 512 KB) that every GPU which
+ * loads the library holds until the process exits; meshes with more than 65536 * 1024 nodes
+ * are rejected with PFF_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race.
+ * Errors: PFF_EINVAL (NULL, bad mesh, too many nodes), PFF_ECUDA. */
+pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_params* params, const double* R,
+                                  const double* U, const double* phi_old, uint8_t* mask, int* n_active,
+                                  int* n_changed, void* cuda_stream);
+
 /* Number of kernel launches this library has issued in the process so far (tracing). */
 long long pff_launch_count(void);
 

@@ -73,6 +73,8 @@ SIGNATURES = {
     "pff_newton_step": (_I, [_VP, _VP, ctypes.POINTER(NewtonInfo)]),
     "pff_profile": (_I, [_VP, _I]),
     "pff_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "pff_active_set_noalloc": (_I, [ctypes.POINTER(Mesh), ctypes.POINTER(Params), _VP, _VP, _VP, _VP,
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _VP]),
     "pff_launch_count": (ctypes.c_longlong, []),
     "pff_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -263,6 +265,17 @@ def profile_read(h, cls: int):
     n, ms = ctypes.c_int(), ctypes.c_double()
     _check(h, load().pff_profile_read(h, cls, ctypes.byref(n), ctypes.byref(ms)), "pff_profile_read")
     return n.value, ms.value
+
+
+def active_set_noalloc(mesh: Mesh, params: Params, R, U, phi_old, mask, stream=None):
+    """Allocation-free active-set decision on caller buffers (no hierarchy); returns
+    (n_active, n_changed)."""
+    na, nc = ctypes.c_int(), ctypes.c_int()
+    s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+    st = load().pff_active_set_noalloc(ctypes.byref(mesh), ctypes.byref(params), _ptr(R), _ptr(U), _ptr(phi_old),
+                                       _ptr(mask), ctypes.byref(na), ctypes.byref(nc), s)
+    _check(None, st, "pff_active_set_noalloc")
+    return na.value, nc.value
 
 
 def launch_count() -> int:
