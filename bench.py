@@ -121,6 +121,81 @@ def cpu_baseline(n: int = 24, seconds: float = 3.0):
                       f"assembled Jacobian, {reps} applies in {el:.2f} s; assembly {t_asm:.1f} s excluded"}, float(y[0])
 
 
+def bench_batch(count: int, dev):
+    """Batching pattern: 'count' instances of the batch recipe (N in {16,24,32,48,64}), one active-set
+    step each (one linear solve to 1e-8).  Solves/s of the batched FP32-MG solver against the same
+    instances solved one after another by the plain FP64 single-instance solver (FP64 V-cycle)."""
+    import torch
+    from paper_1902_08112_gb300 import pff, workloads as W
+    ws = W.batch_instances(count)
+
+    def build(mgp):
+        hs, Us = [], []
+        for w in ws:
+            U, po, pt = W.initial_state(w, displacement="smooth")
+            prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
+                                     mg_precision=mgp, seed=w.seed)
+            h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm)
+            Ud = torch.from_numpy(U).to(dev)
+            pff.set_state(h, Ud, torch.from_numpy(po).to(dev), torch.from_numpy(pt).to(dev))
+            hs.append(h)
+            Us.append(Ud)
+        torch.cuda.synchronize()
+        return hs, Us
+
+    hs, Us = build(32)
+    U0 = [u.clone() for u in Us]
+    b = pff.batch_create(hs)
+    pff.batch_newton_step(b, Us, allow_noconv=True)          # warm-up
+    for u, u0 in zip(Us, U0):
+        u.copy_(u0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = pff.batch_newton_step(b, Us, allow_noconv=True)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    pff.batch_destroy(b)
+    for h in hs:
+        pff.destroy_hierarchy(h)
+    hs, Us = build(64)
+    pff.newton_step(hs[0], Us[0].clone(), allow_noconv=True)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sinfos = [pff.newton_step(h, u, allow_noconv=True) for h, u in zip(hs, Us)]
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    for h in hs:
+        pff.destroy_hierarchy(h)
+    dofs = sum(w.n_dofs for w in ws)
+    return {"instances": count, "dofs": dofs, "sizes": sorted({w.n_cells[0] for w in ws}),
+            "batched_fp32mg_solves_per_s": count / tb, "single_fp64mg_solves_per_s": count / ts,
+            "speedup": ts / tb, "gmres_its_batched": [i.solve.iterations for i in infos][:16],
+            "gmres_its_single": [i.solve.iterations for i in sinfos][:16],
+            "all_converged": all(i.solve.converged for i in infos)}
+
+
+def bench_serve(count: int):
+    """Serving pattern: Poisson arrivals of random pressurised-crack requests (N in {16,24,32},
+    2 load steps each) served by the continuous-batching loop; rate = 80% of the measured
+    closed-loop capacity."""
+    from paper_1902_08112_gb300 import serve
+    # capacity: all requests queued at once
+    cal = serve.poisson_requests(max(4, count // 4), 1.0, seed=99)
+    srv = serve.Server(serve.PffBackend(), hbm_budget=64 << 30)
+    t0 = srv.now()
+    srv.run(cal, realtime=False)
+    cap = len(cal) / (srv.now() - t0)       # requests per second
+    rate = 0.8 * cap
+    reqs = serve.poisson_requests(count, rate, seed=12345)
+    srv = serve.Server(serve.PffBackend(), hbm_budget=64 << 30)
+    t0 = srv.now()
+    srv.run(reqs, realtime=True)
+    wall = srv.now() - t0
+    out = serve.summarize(srv.results, wall)
+    out.update({"arrival_rate_per_s": rate, "capacity_requests_per_s": cap, "load_steps": 2, "ticks": srv.ticks})
+    return out
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -163,6 +238,8 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="cells per edge of the 3D penny workload")
     ap.add_argument("--levels", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=32, help="instances in the batching measurement (0: skip)")
+    ap.add_argument("--serve", type=int, default=24, help="requests in the serving measurement (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -324,10 +401,14 @@ def main():
         "newton": {"gmres_iterations": [i.solve.iterations for i in infos], "n_active": n_act},
         "solve": res,
     }
+    pff.destroy_hierarchy(h)
+    if args.batch > 0:
+        line["batch"] = bench_batch(args.batch, dev)
+    if args.serve > 0:
+        line["serve"] = bench_serve(args.serve)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline()
         line["cpu_baseline"] = cb
-    pff.destroy_hierarchy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -129,6 +129,11 @@ void pff_default_params(pff_params* p);
 pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_params* params, void* cuda_stream,
                                 pff_hierarchy** out);
 
+/* Device bytes pff_create_hierarchy allocates for this mesh, plus the FGMRES workspace for
+ * 'restart' (0: none); -1 for an invalid mesh.  Host-only, no CUDA call: a scheduler uses it to
+ * admit instances into a device-memory budget. */
+int64_t pff_hierarchy_bytes(const pff_mesh* mesh, int restart);
+
 /* Free every allocation of the hierarchy (synchronises its stream).  NULL is a no-op. */
 pff_status pff_destroy_hierarchy(pff_hierarchy* h);
 
@@ -141,8 +146,10 @@ pff_status pff_set_params(pff_hierarchy* h, const pff_params* params);
 
 /* Kernel variant of the level operators: 0 (default) = Q1 fast path (Gauss-point linearisation
  * data precomputed in FP64 per state; FP64-accurate operators evaluated in double-float
- * arithmetic, FP32 operators in FP32), 1 = generic kernels (Q1 and Q2, native FP64 or FP32,
- * state evaluated at every apply).  Q2 meshes always use the generic kernels. */
+ * arithmetic with one thread per Gauss point, FP32 operators in FP32 with one thread per cell),
+ * 1 = generic kernels (Q1 and Q2, native FP64 or FP32, state evaluated at every apply),
+ * 2 = fast path with one thread per Gauss point in both precisions, 3 = fast path with one
+ * thread per cell in both precisions.  Q2 meshes always use the generic kernels. */
 pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant);
 
 /* Set the linearisation point.  U: FP64 [u | phi] (n_dofs), phi_old: FP64 (n_nodes) = the
@@ -232,6 +239,30 @@ pff_status pff_gmres_solve(pff_hierarchy* h, const double* b, double* x, double 
  * (active rows carry phi_old - phi), FGMRES + V-cycle solve to rtol 1e-8 (restart 30,
  * maxit 200), U += dU.  The new U becomes the hierarchy's state. */
 pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_info* info);
+
+/* ---- Batches of independent instances (one launch per level and operation across instances).
+ * A batch is a view over n existing hierarchies created on the same stream, all Q1 with the same
+ * dimension, mg_precision 32 and cheb_degree; instances may differ in mesh size, number of levels
+ * and physical parameters.  The batch owns only descriptor tables and reduction scratch; the
+ * hierarchies keep their data (a hierarchy may belong to several batches, but batches that share a
+ * hierarchy must not run concurrently).  Per-instance results equal those of the single-instance
+ * calls up to rounding.  restart: FGMRES restart length used by the batch (1..200). */
+typedef struct pff_batch pff_batch;
+pff_status pff_batch_create(int n, pff_hierarchy* const* hierarchies, int restart, pff_batch** out);
+pff_status pff_batch_destroy(pff_batch* b);
+/* Diagonals and eigenvalue bounds of every instance (batched CG estimates, Sec. 3.2.1). */
+pff_status pff_batch_setup(pff_batch* b);
+/* z_i ~ G~_i^-1 r_i for every instance: one FP32 V-cycle run in lockstep over all instances. */
+pff_status pff_batch_vcycle(pff_batch* b, const double* const* r, double* const* z);
+/* FGMRES(restart) of every instance to ||b_i - G~_i x_i|| <= rtol ||b_i - G~_i x0_i|| (device arrays
+ * of pointers are NOT used: 'rhs' and 'x' are host arrays of n device pointers).  info: host array of
+ * n entries or NULL.  Synchronises. */
+pff_status pff_batch_gmres_solve(pff_batch* b, const double* const* rhs, double* const* x, double rtol,
+                                 int maxit, pff_solve_info* info);
+/* One active-set step (Algorithm 1) of every instance at U_i (host array of n device pointers,
+ * updated in place), the linear solves batched.  infos: host array of n entries or NULL. */
+pff_status pff_batch_newton_step(pff_batch* b, double* const* U, pff_newton_info* infos);
+const char* pff_batch_last_error(const pff_batch* b);
 
 /* Kernel timing (tracing).  pff_profile(h, 1) clears the counters and starts recording CUDA
  * events on the hierarchy's stream around every level-operator launch (the preset of eliminated

@@ -247,6 +247,39 @@ extern "C" pff_status pff_destroy_hierarchy(pff_hierarchy* h) {
 
 static int resolve_level(const pff_hierarchy* h, int level) { return level < 0 ? h->L - 1 : level; }
 
+extern "C" int64_t pff_hierarchy_bytes(const pff_mesh* mesh, int restart) {
+    if (!mesh || (mesh->dim != 2 && mesh->dim != 3) || (mesh->degree != 1 && mesh->degree != 2) ||
+        mesh->n_levels < 1 || mesh->n_levels > 16 || restart < 0)
+        return -1;
+    const int div = 1 << (mesh->n_levels - 1);
+    for (int a = 0; a < mesh->dim; ++a)
+        if (mesh->n_cells[a] < 1 || mesh->n_cells[a] % div != 0) return -1;
+    const int64_t pad = 16;   // every allocation carries 16 spare bytes
+    int64_t total = 0, nn_f = 0, nd_f = 0;
+    for (int l = 0; l < mesh->n_levels; ++l) {
+        const int f = 1 << (mesh->n_levels - 1 - l);
+        int64_t nn = 1, nc = 1;
+        for (int a = 0; a < mesh->dim; ++a) {
+            nn *= (int64_t)mesh->degree * (mesh->n_cells[a] / f) + 1;
+            nc *= mesh->n_cells[a] / f;
+        }
+        const int64_t nd = (mesh->dim + 1) * nn;
+        total += (nn + pad) + (nd * 8 + pad) + (nn * 8 + pad) + (nd * 4 + pad) + (nn * 4 + pad) + (nd * 8 + pad) +
+                 (nd * 4 + pad) + 6 * ((nd * 4 + pad) + (nd * 8 + pad));
+        if (mesh->degree == 1) {
+            const int64_t nq = (int64_t)(mesh->dim == 3 ? 8 : 5) * (1 << mesh->dim) * nc;
+            total += (nq * 4 + pad) + (nq * 8 + pad);
+        }
+        nn_f = nn;
+        nd_f = nd;
+    }
+    total += (nn_f + pad) + 2 * (nn_f * 8 + pad) + (nd_f * 8 + pad) + 4 * (nd_f * 8 + pad) + (nn_f + pad) +
+             (16 * 4 + pad) + (4096 * 8 + pad) + ((int64_t)dot_partials() * 64 * 8 + pad);
+    if (restart > 0) total += ((int64_t)(restart + 1) * nd_f * 8 + pad) + ((int64_t)restart * nd_f * 8 + pad) +
+                              ((int64_t)(2 * (restart + 1) + 2) * 8 + pad);
+    return total;
+}
+
 extern "C" pff_status pff_level_info(const pff_hierarchy* h, int level, int64_t* n_nodes, int64_t* n_cells,
                                      int nodes_per_axis[3]) {
     if (!h) return PFF_EINVAL;
@@ -273,8 +306,9 @@ extern "C" pff_status pff_set_params(pff_hierarchy* h, const pff_params* params)
 
 extern "C" pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant) {
     if (!h) return PFF_EINVAL;
-    REQUIRE(h, variant == 0 || variant == 1, PFF_EINVAL, "variant must be 0 (Q1 fast path) or 1 (generic)");
-    h->fast_q1 = variant == 0;
+    REQUIRE(h, variant >= 0 && variant <= 3, PFF_EINVAL, "variant must be 0, 1, 2 or 3");
+    h->fast_q1 = variant != 1;
+    h->q1_style = variant == 2 ? 3 : (variant == 3 ? 0 : 1);
     h->stale = true;
     return PFF_OK;
 }
@@ -514,18 +548,19 @@ extern "C" pff_status pff_gmres_solve(pff_hierarchy* h, const double* b, double*
     return st;
 }
 
-extern "C" pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_info* info) {
-    if (!h) return PFF_EINVAL;
+pff_status pff_internal_ensure_krylov(pff_hierarchy* h, int m) { return ensure_krylov(h, m); }
+
+// Algorithm 1 up to the linear solve: state U, residual, active set, eliminated right-hand side
+// R~ in tmp64[1] and its norm.
+pff_status pff_internal_newton_prepare(pff_hierarchy* h, double* U, int* n_act, int* n_chg, double* res) {
     REQUIRE(h, U, PFF_EINVAL, "pff_newton_step: NULL");
     REQUIRE(h, h->has_state, PFF_ESTATE, "pff_newton_step before pff_set_state");
     Level& F = h->lv[h->L - 1];
     const int64_t nd = n_dofs(F.g);
     cudaStream_t s = h->stream;
-    // state U (phi_old, phi~ from the last pff_set_state)
     CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CUDA_OR_FAIL(h, propagate_state(h));
-    int n_act = 0, n_chg = 0;
-    pff_status st = update_active(h, &n_act, &n_chg);
+    pff_status st = update_active(h, n_act, n_chg);
     if (st != PFF_OK) return st;
     // eliminated right-hand side: active rows carry phi_old - phi, their columns move right
     double* Rt = h->tmp64[1];
@@ -534,28 +569,46 @@ extern "C" pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_in
     CUDA_OR_FAIL(h, apply_level<double>(h, h->L - 1, OP_APPLY, Rt, t, PFF_MASK_PHI_DIR));
     CUDA_OR_FAIL(h, launch_newton_rhs(F.g, h->R, t, F.U64, h->phi_old, F.mask, Rt, s));
     CUDA_OR_FAIL(h, launch_norm2(nd, Rt, h->d_scratch, h->d_scal + 300, s));
-    double res = 0.0;
-    CUDA_OR_FAIL(h, cudaMemcpyAsync(&res, h->d_scal + 300, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(res, h->d_scal + 300, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_OR_FAIL(h, cudaStreamSynchronize(s));
-    // solve G~ dU = R~
+    return PFF_OK;
+}
+
+// U += dU (tmp64[2]); the new U becomes the hierarchy's state.
+pff_status pff_internal_newton_finish(pff_hierarchy* h, double* U) {
+    Level& F = h->lv[h->L - 1];
+    const int64_t nd = n_dofs(F.g);
+    CUDA_OR_FAIL(h, launch_axpby<double>(nd, 1.0, h->tmp64[2], 1.0, U, h->stream));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_OR_FAIL(h, propagate_state(h));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_info* info) {
+    if (!h) return PFF_EINVAL;
+    int n_act = 0, n_chg = 0;
+    double res = 0.0;
+    pff_status st = pff_internal_newton_prepare(h, U, &n_act, &n_chg, &res);
+    if (st != PFF_OK) return st;
+    Level& F = h->lv[h->L - 1];
+    const int64_t nd = n_dofs(F.g);
     st = ensure_setup(h);
     if (st != PFF_OK) return st;
     st = ensure_krylov(h, 30);
     if (st != PFF_OK) return st;
     double* dU = h->tmp64[2];
-    CUDA_OR_FAIL(h, cudaMemsetAsync(dU, 0, nd * sizeof(double), s));
+    CUDA_OR_FAIL(h, cudaMemsetAsync(dU, 0, nd * sizeof(double), h->stream));
     pff_solve_info si;
     memset(&si, 0, sizeof(si));
     std::string err;
-    st = fgmres(h, Rt, dU, 1e-8, 30, 200, &si, err);
+    st = fgmres(h, h->tmp64[1], dU, 1e-8, 30, 200, &si, err);
     if (st != PFF_OK && st != PFF_ENOCONV) {
         h->err = err;
         return st;
     }
-    CUDA_OR_FAIL(h, launch_axpby<double>(nd, 1.0, dU, 1.0, U, s));
-    CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CUDA_OR_FAIL(h, propagate_state(h));
-    CUDA_OR_FAIL(h, cudaStreamSynchronize(s));
+    pff_status s2 = pff_internal_newton_finish(h, U);
+    if (s2 != PFF_OK) return s2;
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
     if (info) {
         info->n_active = n_act;
         info->n_changed = n_chg;

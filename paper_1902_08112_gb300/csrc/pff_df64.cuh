@@ -48,12 +48,39 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
 __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
 
-// exact split of a double into hi + lo (one FP64 subtraction)
+// Conversions without FP64 instructions (on GB300 conversions to and from FP64 issue on the slow
+// FP64 unit).  They work on the IEEE-754 fields: a double (1.m) 2^(e-1023) with a 52-bit m splits
+// into hi = the double with m truncated to its top 23 bits and lo = the remaining 29 bits of m
+// times 2^(e-1075), rounded to a float (48 significant bits in total).  Magnitudes below 2^-126
+// become 0; below 2^-104 the lo part is dropped.  Inf and NaN map to Inf and NaN.
 __device__ __forceinline__ df64 df_from_double(double d) {
-    const float h = __double2float_rn(d);
-    return df_make(h, __double2float_rn(d - (double)h));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return df_make(__uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u)), 0.f);
+    const int fe = e - 1023 + 127;               // biased float exponent
+    if (fe <= 0) return df_make(0.f, 0.f);
+    if (fe >= 255) return df_make(__uint_as_float(sign | 0x7F800000u), 0.f);
+    const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(m >> 29));
+    const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);
+    const int se = fe - 23;                      // biased exponent of 2^(e - 1046)
+    float lo = 0.f;
+    if (se > 0 && rem) lo = __fmul_rn(__fmul_rn(__uint2float_rn(rem), 0x1.0p-29f), __uint_as_float((unsigned)se << 23));
+    return df_make(hi, sign ? -lo : lo);
 }
-__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+// exact float -> double by field arithmetic (subnormal floats become 0)
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const int e = (int)((u >> 23) & 0xFF);
+    const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    if (e == 0xFF) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | m));
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896) << 52) | m));
+}
+// hi + lo rounded to a double: one FP64 addition
+__device__ __forceinline__ double df_to_double(df64 a) { return f32_to_f64_bits(a.hi) + f32_to_f64_bits(a.lo); }
 
 // ---- scalar traits so kernels can be written once for float and df64
 template <typename S>

@@ -38,7 +38,7 @@ struct Geom {
     double h[3];         // cell edge lengths (1 beyond dim)
 };
 
-inline int64_t n_dofs(const Geom& g) { return (int64_t)(g.dim + 1) * g.n_nodes; }
+__host__ __device__ inline int64_t n_dofs(const Geom& g) { return (int64_t)(g.dim + 1) * g.n_nodes; }
 
 // Device arrays of one level.
 struct Level {
@@ -189,6 +189,7 @@ struct pff_hierarchy {
     double* kr_h = nullptr;          // device column of H (2 * (m + 1))
     bool has_state = false;
     bool fast_q1 = true;             // Q1 levels use the linearisation-data kernels of pff_q1.cu
+    int q1_style = 1;                // bit 0: df64 applies per Gauss-point lane; bit 1: FP32 likewise
     bool active_known = false;       // an active set has been computed or set
     bool stale = true;               // preconditioner data out of date
     std::vector<void*> allocs;       // every device allocation, freed on destroy

@@ -20,6 +20,7 @@
 #include "pff_df64.cuh"
 #include "pff_internal.cuh"
 #include "pff_q1.cuh"
+#include "pff_batch.cuh"
 
 namespace pff {
 
@@ -175,10 +176,41 @@ cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, 
 // ------------------------------------------------------------------ modal apply
 template <int DIM, typename S>
 struct Q1Tile;
-template <> struct Q1Tile<3, float> { static constexpr int TX = 8, TY = 8, TZ = 4; };
-template <> struct Q1Tile<3, df64> { static constexpr int TX = 8, TY = 4, TZ = 4; };
-template <> struct Q1Tile<2, float> { static constexpr int TX = 16, TY = 16, TZ = 1; };
-template <> struct Q1Tile<2, df64> { static constexpr int TX = 16, TY = 8, TZ = 1; };
+template <> struct Q1Tile<3, float> { static constexpr int TX = 8, TY = 8, TZ = 4, MINB = 2; };
+template <> struct Q1Tile<3, df64> { static constexpr int TX = 8, TY = 4, TZ = 4, MINB = 1; };
+template <> struct Q1Tile<2, float> { static constexpr int TX = 16, TY = 16, TZ = 1, MINB = 2; };
+template <> struct Q1Tile<2, df64> { static constexpr int TX = 16, TY = 8, TZ = 1, MINB = 1; };
+
+template <typename S>
+__device__ __forceinline__ S cpair(float2 v);
+template <>
+__device__ __forceinline__ float cpair<float>(float2 v) { return v.x; }
+template <>
+__device__ __forceinline__ df64 cpair<df64>(float2 v) { return df_make(v.x, v.y); }
+
+static float2 split_pair(double d) {
+    const float hi = (float)d;
+    return make_float2(hi, (float)(d - (double)hi));
+}
+
+Q1Consts make_q1_consts(const Geom& g, const Phys& ph) {
+    Q1Consts k;
+    const int dim = g.dim, NV = 1 << dim;
+    const double gpt = 1.0 / sqrt(3.0);
+    const double gp[4] = {1.0, gpt, gpt * gpt, gpt * gpt * gpt};
+    for (int j = 0; j <= 3; ++j) k.cv[j] = split_pair(gp[j] / NV);
+    for (int d = 0; d < 3; ++d)
+        for (int j = 0; j < 3; ++j) k.cg[d][j] = split_pair(d < dim ? gp[j] * 2.0 / (g.h[d] * NV) : 0.0);
+    double vol = 1.0;
+    for (int d = 0; d < dim; ++d) vol *= g.h[d];
+    k.mu = split_pair(ph.mu);
+    k.mu2 = split_pair(2.0 * ph.mu);
+    k.lam = split_pair(ph.lam);
+    k.gcew = split_pair(ph.Gc * ph.eps * vol / NV);
+    k.g2 = split_pair(0.5 * gpt);
+    for (int d = 0; d < 3; ++d) k.ih[d] = split_pair(d < dim ? 1.0 / g.h[d] : 0.0);
+    return k;
+}
 
 template <typename S>
 struct QData;
@@ -195,8 +227,8 @@ template <> struct QData<df64> {
 };
 
 template <int DIM, typename S, bool BLOCKDIAG>
-__global__ void __launch_bounds__(Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ)
-k_q1_apply(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
+__device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
+                                              int bx, int by, int bz) {
     using T = Q1Tile<DIM, S>;
     using D = Q1Dims<DIM>;
     using St = typename Scalar<S>::storage;
@@ -210,7 +242,7 @@ k_q1_apply(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) 
     __shared__ uint8_t smask[NT];
 
     const Geom& g = a.g;
-    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = DIM == 3 ? blockIdx.z * T::TZ : 0;
+    const int ci0 = bx * T::TX, cj0 = by * T::TY, ck0 = DIM == 3 ? bz * T::TZ : 0;
     const int64_t nn = g.n_nodes;
 
     for (int t = threadIdx.x; t < NT; t += blockDim.x) {
@@ -236,15 +268,15 @@ k_q1_apply(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) 
         const int tb = li + NTX * (lj + NTY * lk);
         S cv[DIM + 1], cg[DIM][DIM];
 #pragma unroll
-        for (int j = 0; j <= DIM; ++j) cv[j] = Scalar<S>::from_double(a.cv[j]);
+        for (int j = 0; j <= DIM; ++j) cv[j] = cpair<S>(a.k.cv[j]);
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
 #pragma unroll
-            for (int j = 0; j < DIM; ++j) cg[d][j] = Scalar<S>::from_double(a.cg[d][j]);
-        const S mu2 = Scalar<S>::from_double(2.0 * a.mu), lam = Scalar<S>::from_double(a.lam);
-        const S gcew = Scalar<S>::from_double(a.gcew);
+            for (int j = 0; j < DIM; ++j) cg[d][j] = cpair<S>(a.k.cg[d][j]);
+        const S mu2 = cpair<S>(a.k.mu2), lam = cpair<S>(a.k.lam);
+        const S gcew = cpair<S>(a.k.gcew);
 
-        const S mu = Scalar<S>::from_double(a.mu);
+        const S mu = cpair<S>(a.k.mu);
 
         // ======== pass 1: displacement rows (G_uu) and the coupling term of the phi rows
         S cpl[NV];
@@ -469,6 +501,318 @@ k_q1_apply(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) 
     }
 }
 
+// ------------------------------------------------------------------ lane apply
+// One thread per (cell, node) = (cell, Gauss point): 2^d lanes of a warp form a cell.  Lane n
+// holds node n's value and, after one shuffle butterfly per axis e, the value at Gauss point
+// n: along e the pair (a, b) becomes ((1+g)/2 a + (1-g)/2 b, (1-g)/2 a + (1+g)/2 b), written
+// per lane as (v + p)/2 + (g/2)(v - p) with p the partner's value; the derivative channel of axis
+// e is s_e (v - p) / h_e (s_e = +1 on the upper side).  Integration runs the transposed
+// butterflies in reverse axis order: the interpolation matrix is symmetric, and the derivative
+// stage transposes to s_e (f + p) / h_e.
+template <typename S>
+__device__ __forceinline__ S shfl_xor(S v, int m);
+template <>
+__device__ __forceinline__ float shfl_xor<float>(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+template <>
+__device__ __forceinline__ df64 shfl_xor<df64>(df64 v, int m) {
+    return df_make(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+__device__ __forceinline__ float half_of(float v) { return 0.5f * v; }
+__device__ __forceinline__ df64 half_of(df64 v) { return df_make(0.5f * v.hi, 0.5f * v.lo); }
+
+template <int DIM, typename S>
+struct LaneConst {
+    S g2;           // g / 2
+    S ih[DIM];      // 1 / h_e
+};
+
+// value (if WANT_VAL) and gradient at this lane's Gauss point from this lane's nodal value
+template <int DIM, typename S, bool WANT_VAL>
+__device__ __forceinline__ void lane_eval(S v, int n, const LaneConst<DIM, S>& k, S& val, S (&grad)[DIM]) {
+#pragma unroll
+    for (int e = 0; e < DIM; ++e) {
+        // derivative channels of earlier axes are interpolated along e
+#pragma unroll
+        for (int d = 0; d < e; ++d) {
+            const S p = shfl_xor(grad[d], 1 << e);
+            grad[d] = half_of(grad[d] + p) + k.g2 * (grad[d] - p);
+        }
+        const S p = shfl_xor(v, 1 << e);
+        const S diff = v - p;
+        grad[e] = ((n >> e) & 1) ? diff * k.ih[e] : -(diff * k.ih[e]);
+        if (WANT_VAL || e + 1 < DIM) v = half_of(v + p) + k.g2 * diff;
+    }
+    if (WANT_VAL) val = v;
+}
+
+// transposed: fluxes on the test function value (fv, if HAS_VAL) and gradient (fg) at this
+// lane's Gauss point -> contribution to this lane's node
+template <int DIM, typename S, bool HAS_VAL>
+__device__ __forceinline__ S lane_integrate(S fv, S (&fg)[DIM], int n, const LaneConst<DIM, S>& k) {
+    S tv = fv;
+#pragma unroll
+    for (int e = DIM - 1; e >= 0; --e) {
+        const S pd = shfl_xor(fg[e], 1 << e);
+        const S td = ((n >> e) & 1) ? (fg[e] + pd) * k.ih[e] : -((fg[e] + pd) * k.ih[e]);
+        if (HAS_VAL || e + 1 < DIM) {
+            const S p = shfl_xor(tv, 1 << e);
+            tv = half_of(tv + p) + k.g2 * (tv - p) + td;
+        } else {
+            tv = td;
+        }
+#pragma unroll
+        for (int d = 0; d < e; ++d) {
+            const S p = shfl_xor(fg[d], 1 << e);
+            fg[d] = half_of(fg[d] + p) + k.g2 * (fg[d] - p);
+        }
+    }
+    return tv;
+}
+
+template <int DIM>
+struct LaneTile;
+template <> struct LaneTile<3> { static constexpr int TX = 4, TY = 4, TZ = 2; };
+template <> struct LaneTile<2> { static constexpr int TX = 8, TY = 8, TZ = 1; };
+
+template <int DIM, typename S, bool BLOCKDIAG>
+__device__ __forceinline__ void q1_apply_lanes_tile(
+    const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a, int bx, int by, int bz) {
+    using T = LaneTile<DIM>;
+    using D = Q1Dims<DIM>;
+    constexpr int NV = D::NV, NC = D::NC, NK = D::NK;
+    constexpr int NCELL = T::TX * T::TY * T::TZ;
+    constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = DIM == 3 ? T::TZ + 1 : 1;
+    constexpr int NT = NTX * NTY * NTZ;
+    static_assert(NCELL * NV == 256, "one CTA = 256 lanes");
+
+    __shared__ S sx[NC * NT];
+    __shared__ S sel[NV * NC * NCELL];
+    __shared__ uint8_t smask[NT];
+
+    const Geom& g = a.g;
+    const int ci0 = bx * T::TX, cj0 = by * T::TY, ck0 = DIM == 3 ? bz * T::TZ : 0;
+    const int64_t nn = g.n_nodes;
+    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+        const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
+        const int gi = ci0 + ti, gj = cj0 + tj, gk = ck0 + tk;
+        const bool in = gi < g.nn[0] && gj < g.nn[1] && gk < g.nn[2];
+        const int64_t gn = in ? (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk) : 0;
+        const uint8_t m = in ? a.mask[gn] : 0;
+        smask[t] = m;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const bool el = c < DIM ? ((m >> c) & 1) != 0 : (m & a.phi_bits) != 0;
+            sx[c * NT + t] = (in && !el) ? Scalar<S>::load(a.x[c * nn + gn]) : Scalar<S>::zero();
+        }
+    }
+    __syncthreads();
+
+    const int cell = threadIdx.x / NV, n = threadIdx.x % NV;
+    const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
+    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+    // every lane runs the shuffles; invalid cells work on zeros and are not stored
+    const int tnode = (li + (n & 1)) + NTX * ((lj + ((n >> 1) & 1)) + NTY * (DIM == 3 ? lk + ((n >> 2) & 1) : 0));
+    const int64_t gid = valid ? (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)) : 0;
+    LaneConst<DIM, S> k;
+    k.g2 = cpair<S>(a.k.g2);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) k.ih[d] = cpair<S>(a.k.ih[d]);
+    const S mu = cpair<S>(a.k.mu), mu2 = cpair<S>(a.k.mu2);
+    const S lam = cpair<S>(a.k.lam), gcew = cpair<S>(a.k.gcew);
+
+    // displacement gradients at Gauss point n
+    S gd[DIM][DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        S dummy;
+        lane_eval<DIM, S, false>(sx[c * NT + tnode], n, k, dummy, gd[c]);
+    }
+    S dphi, gphi[DIM];
+    lane_eval<DIM, S, true>(sx[DIM * NT + tnode], n, k, dphi, gphi);
+    const int64_t qbase = (int64_t)(n * NK) * g.n_cells + gid;
+    const S c0 = valid ? QData<S>::get(a.qd, qbase) : Scalar<S>::zero();
+    const S c1 = valid ? QData<S>::get(a.qd, qbase + (int64_t)(NK - 1) * g.n_cells) : Scalar<S>::zero();
+    S tr = gd[0][0];
+#pragma unroll
+    for (int i = 1; i < DIM; ++i) tr = tr + gd[i][i];
+    const S ltr = lam * tr;
+    S fu[DIM][DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = i; j < DIM; ++j) {
+            const S sg = (i == j) ? mu2 * gd[i][i] + ltr : mu * (gd[i][j] + gd[j][i]);
+            const S f = c0 * sg;
+            fu[i][j] = f;
+            fu[j][i] = f;
+        }
+    S fp = c1 * dphi;
+    if constexpr (!BLOCKDIAG) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = i; j < DIM; ++j) {
+                const S sp = valid ? QData<S>::get(a.qd, qbase + (int64_t)(1 + sidx<DIM>(i, j)) * g.n_cells)
+                                   : Scalar<S>::zero();
+                fp = fp + sp * ((i == j) ? gd[i][i] : gd[i][j] + gd[j][i]);
+            }
+    }
+    S out[NC];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) out[c] = lane_integrate<DIM, S, false>(Scalar<S>::zero(), fu[c], n, k);
+    S fg[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) fg[d] = gcew * gphi[d];
+    out[DIM] = lane_integrate<DIM, S, true>(fp, fg, n, k);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sel[(n * NC + c) * NCELL + cell] = valid ? out[c] : Scalar<S>::zero();
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+        const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
+        const int gi = ci0 + ti, gj = cj0 + tj, gk = ck0 + tk;
+        if (!(gi < g.nn[0] && gj < g.nn[1] && gk < g.nn[2])) continue;
+        const int64_t gn = (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk);
+        const uint8_t m = smask[t];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const bool el = c < DIM ? ((m >> c) & 1) != 0 : (m & a.phi_bits) != 0;
+            if (el) continue;
+            S sum = Scalar<S>::zero();
+#pragma unroll
+            for (int dk = 0; dk < (DIM == 3 ? 2 : 1); ++dk) {
+                const int ck = tk - dk;
+                if (DIM == 3 && (ck < 0 || ck >= T::TZ)) continue;
+#pragma unroll
+                for (int dj = 0; dj < 2; ++dj) {
+                    const int cj = tj - dj;
+                    if (cj < 0 || cj >= T::TY) continue;
+#pragma unroll
+                    for (int di = 0; di < 2; ++di) {
+                        const int cx = ti - di;
+                        if (cx < 0 || cx >= T::TX) continue;
+                        const int nl = di + 2 * dj + 4 * dk;
+                        sum = sum + sel[(nl * NC + c) * NCELL + cx + T::TX * (cj + T::TY * (DIM == 3 ? ck : 0))];
+                    }
+                }
+            }
+            atomicAdd(&a.y[c * nn + gn], Scalar<S>::store(sum));
+        }
+    }
+}
+
+template <int DIM, typename S, bool BLOCKDIAG>
+__global__ void __launch_bounds__(Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ, Q1Tile<DIM, S>::MINB)
+k_q1_apply(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
+    q1_apply_tile<DIM, S, BLOCKDIAG>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <int DIM, typename S, bool BLOCKDIAG>
+__global__ void __launch_bounds__(256) k_q1_apply_lanes(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
+    q1_apply_lanes_tile<DIM, S, BLOCKDIAG>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---- batched: one launch over the tiles of all instances of a level
+template <int DIM, typename S, bool LANES>
+struct TileOf {
+    static constexpr int TX = LANES ? LaneTile<DIM>::TX : Q1Tile<DIM, S>::TX;
+    static constexpr int TY = LANES ? LaneTile<DIM>::TY : Q1Tile<DIM, S>::TY;
+    static constexpr int TZ = LANES ? LaneTile<DIM>::TZ : Q1Tile<DIM, S>::TZ;
+};
+
+template <int DIM, typename S, bool BLOCKDIAG, bool LANES>
+__global__ void __launch_bounds__(LANES ? 256 : Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ,
+                                  LANES ? 1 : Q1Tile<DIM, S>::MINB)
+k_q1_apply_batched(const BLevel* __restrict__ L, const int* __restrict__ tile_start, int n, int sx, int sy,
+                   int phi_bits) {
+    // instance = last i with tile_start[i] <= blockIdx.x
+    int lo = 0, hi = n - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_start[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const BLevel& d = L[lo];
+    using St = typename Scalar<S>::storage;
+    using QT = typename QData<S>::type;
+    using TT = TileOf<DIM, S, LANES>;
+    Q1ApplyArgs<St, QT> a;
+    a.g = d.g;
+    a.qd = sizeof(St) == 8 ? reinterpret_cast<const QT*>(d.qpd64) : reinterpret_cast<const QT*>(d.qpd32);
+    a.x = bvec<St>(d, sx);
+    a.y = bvec<St>(d, sy);
+    a.mask = d.mask;
+    a.phi_bits = phi_bits;
+    a.k = d.k;
+    const int local = b - tile_start[lo];
+    const int tx = (d.g.nc[0] + TT::TX - 1) / TT::TX, ty = (d.g.nc[1] + TT::TY - 1) / TT::TY;
+    const int bx = local % tx, by = (local / tx) % ty, bz = local / (tx * ty);
+    if constexpr (LANES) q1_apply_lanes_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);
+    else q1_apply_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);
+}
+
+int q1_tiles(const Geom& g, bool fp64, bool lanes) {
+    int TX, TY, TZ;
+    if (g.dim == 3) {
+        if (lanes) { TX = LaneTile<3>::TX; TY = LaneTile<3>::TY; TZ = LaneTile<3>::TZ; }
+        else if (fp64) { TX = Q1Tile<3, df64>::TX; TY = Q1Tile<3, df64>::TY; TZ = Q1Tile<3, df64>::TZ; }
+        else { TX = Q1Tile<3, float>::TX; TY = Q1Tile<3, float>::TY; TZ = Q1Tile<3, float>::TZ; }
+    } else {
+        if (lanes) { TX = LaneTile<2>::TX; TY = LaneTile<2>::TY; TZ = 1; }
+        else if (fp64) { TX = Q1Tile<2, df64>::TX; TY = Q1Tile<2, df64>::TY; TZ = 1; }
+        else { TX = Q1Tile<2, float>::TX; TY = Q1Tile<2, float>::TY; TZ = 1; }
+    }
+    const int tz = g.dim == 3 ? (g.nc[2] + TZ - 1) / TZ : 1;
+    return ((g.nc[0] + TX - 1) / TX) * ((g.nc[1] + TY - 1) / TY) * tz;
+}
+
+template <int DIM, typename S, bool BD, bool LANES>
+static void launch_b(const BLevel* L, const int* ts, int n, int total, int sx, int sy, int pb, cudaStream_t s) {
+    constexpr int threads = LANES ? 256 : Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ;
+    k_q1_apply_batched<DIM, S, BD, LANES><<<total, threads, 0, s>>>(L, ts, n, sx, sy, pb);
+}
+
+cudaError_t launch_q1_apply_batched(int dim, bool fp64, bool blockdiag, bool lanes, const BLevel* L, int n,
+                                    const int* tile_start, int total_tiles, int sx, int sy, int phi_bits,
+                                    cudaStream_t s) {
+    if (total_tiles <= 0) return cudaSuccess;
+#define PFF_B(D, S, BD, LN) launch_b<D, S, BD, LN>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s)
+    if (dim == 3) {
+        if (fp64) {
+            if (lanes) { if (blockdiag) PFF_B(3, df64, true, true); else PFF_B(3, df64, false, true); }
+            else { if (blockdiag) PFF_B(3, df64, true, false); else PFF_B(3, df64, false, false); }
+        } else {
+            if (lanes) { if (blockdiag) PFF_B(3, float, true, true); else PFF_B(3, float, false, true); }
+            else { if (blockdiag) PFF_B(3, float, true, false); else PFF_B(3, float, false, false); }
+        }
+    } else {
+        if (fp64) {
+            if (lanes) { if (blockdiag) PFF_B(2, df64, true, true); else PFF_B(2, df64, false, true); }
+            else { if (blockdiag) PFF_B(2, df64, true, false); else PFF_B(2, df64, false, false); }
+        } else {
+            if (lanes) { if (blockdiag) PFF_B(2, float, true, true); else PFF_B(2, float, false, true); }
+            else { if (blockdiag) PFF_B(2, float, true, false); else PFF_B(2, float, false, false); }
+        }
+    }
+#undef PFF_B
+    return count_launch(cudaGetLastError());
+}
+
+template <typename S, bool BD>
+static cudaError_t launch_lanes_dim(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
+                                    cudaStream_t s) {
+    if (a.g.dim == 3) {
+        using T = LaneTile<3>;
+        dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, (a.g.nc[2] + T::TZ - 1) / T::TZ);
+        k_q1_apply_lanes<3, S, BD><<<grid, 256, 0, s>>>(a);
+    } else {
+        using T = LaneTile<2>;
+        dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, 1);
+        k_q1_apply_lanes<2, S, BD><<<grid, 256, 0, s>>>(a);
+    }
+    return count_launch(cudaGetLastError());
+}
+
 template <typename S, bool BD>
 static cudaError_t launch_apply_dim(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
                                    cudaStream_t s) {
@@ -486,21 +830,11 @@ static cudaError_t launch_apply_dim(const Q1ApplyArgs<typename Scalar<S>::storag
 
 template <typename St, typename QT>
 static void fill_consts(Q1ApplyArgs<St, QT>& a, const Phys& ph) {
-    const int dim = a.g.dim, NV = 1 << dim;
-    const double gpt = 1.0 / sqrt(3.0);
-    double gp[4] = {1.0, gpt, gpt * gpt, gpt * gpt * gpt};
-    for (int j = 0; j <= 3; ++j) a.cv[j] = gp[j] / NV;
-    for (int d = 0; d < 3; ++d)
-        for (int j = 0; j < 3; ++j) a.cg[d][j] = d < dim ? gp[j] * 2.0 / (a.g.h[d] * NV) : 0.0;
-    double vol = 1.0;
-    for (int d = 0; d < dim; ++d) vol *= a.g.h[d];
-    a.mu = ph.mu;
-    a.lam = ph.lam;
-    a.gcew = ph.Gc * ph.eps * vol / NV;
+    a.k = make_q1_consts(a.g, ph);
 }
 
 cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s) {
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s) {
     Q1ApplyArgs<double, float2> a;
     a.g = g;
     a.qd = qd;
@@ -509,11 +843,12 @@ cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, c
     a.mask = mask;
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
+    if (lanes) return blockdiag ? launch_lanes_dim<df64, true>(a, s) : launch_lanes_dim<df64, false>(a, s);
     return blockdiag ? launch_apply_dim<df64, true>(a, s) : launch_apply_dim<df64, false>(a, s);
 }
 
 cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s) {
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s) {
     Q1ApplyArgs<float, float> a;
     a.g = g;
     a.qd = qd;
@@ -522,7 +857,265 @@ cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, co
     a.mask = mask;
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
+    if (lanes) return blockdiag ? launch_lanes_dim<float, true>(a, s) : launch_lanes_dim<float, false>(a, s);
     return blockdiag ? launch_apply_dim<float, true>(a, s) : launch_apply_dim<float, false>(a, s);
+}
+
+// ------------------------------------------------------------------ residual and diagonal (FP64)
+// Residual -A(U) of Eq. (semilinear) (OP 0) and diagonal of G~ (OP 1) for Q1 levels.  Same tile
+// and fixed-order gather as the applies.  The residual evaluates the state from the nodal
+// values in modal form; the diagonal uses the stored Gauss-point coefficients c0, c1 and the
+// squared shape gradients, which on a uniform cell depend only on n xor q:
+// (d_d N_n(q))^2 = h_d^-2 prod_{e != d} A(n,q,e), N_n(q)^2 = prod_e A(n,q,e), with
+// A = ((1 + g)/2)^2 if node n and Gauss point q lie on the same side in direction e, else
+// ((1 - g)/2)^2.
+namespace {
+template <int DIM>
+struct RDTile;
+template <> struct RDTile<3> { static constexpr int TX = 8, TY = 4, TZ = 4; };
+template <> struct RDTile<2> { static constexpr int TX = 16, TY = 8, TZ = 1; };
+}  // namespace
+
+template <int DIM, int OP>
+__global__ void __launch_bounds__(RDTile<DIM>::TX * RDTile<DIM>::TY * RDTile<DIM>::TZ)
+k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __restrict__ pt,
+             const float2* __restrict__ q64, const uint8_t* __restrict__ mask, double* __restrict__ y, double gpt) {
+    using T = RDTile<DIM>;
+    using D = Q1Dims<DIM>;
+    constexpr int NV = D::NV, NC = D::NC, NK = D::NK;
+    constexpr int NCELL = T::TX * T::TY * T::TZ;
+    constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = DIM == 3 ? T::TZ + 1 : 1;
+    constexpr int NT = NTX * NTY * NTZ;
+    constexpr int NS = OP == 0 ? NC + 1 : 1;   // staged fields: U and phi~ (residual only)
+    __shared__ double sv[NS * NT];
+    __shared__ double sel[NV * NC * NCELL];
+
+    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = DIM == 3 ? blockIdx.z * T::TZ : 0;
+    const int64_t nn = g.n_nodes;
+    if constexpr (OP == 0) {
+        for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+            const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
+            const int gi = ci0 + ti, gj = cj0 + tj, gk = ck0 + tk;
+            const bool in = gi < g.nn[0] && gj < g.nn[1] && gk < g.nn[2];
+            const int64_t gn = in ? (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk) : 0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) sv[c * NT + t] = in ? U[c * nn + gn] : 0.0;
+            sv[NC * NT + t] = in ? pt[gn] : 0.0;
+        }
+        __syncthreads();
+    }
+    double vol = 1.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) vol *= g.h[a];
+    const double w = vol / NV;
+    double gp[DIM + 1];
+    gp[0] = 1.0;
+#pragma unroll
+    for (int j = 1; j <= DIM; ++j) gp[j] = gp[j - 1] * gpt;
+
+    const int cell = threadIdx.x;
+    const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
+    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+    double el[NV][NC];
+#pragma unroll
+    for (int n = 0; n < NV; ++n)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) el[n][c] = 0.0;
+    if (valid) {
+        const int64_t gid = (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk));
+        if constexpr (OP == 1) {
+            const double Ap = 0.25 * (1.0 + gpt) * (1.0 + gpt), Am = 0.25 * (1.0 - gpt) * (1.0 - gpt);
+            const double gcew = ph.Gc * ph.eps * w;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const float2 a0 = q64[(int64_t)(q * NK + 0) * g.n_cells + gid];
+                const float2 a1 = q64[(int64_t)(q * NK + NK - 1) * g.n_cells + gid];
+                const double c0 = (double)a0.x + (double)a0.y, c1 = (double)a1.x + (double)a1.y;
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    const int m = n ^ q;
+                    double P = 1.0, Wd[DIM], Ws = 0.0;
+#pragma unroll
+                    for (int e = 0; e < DIM; ++e) P *= (m >> e) & 1 ? Am : Ap;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        double f = 1.0 / (g.h[d] * g.h[d]);
+#pragma unroll
+                        for (int e = 0; e < DIM; ++e)
+                            if (e != d) f *= (m >> e) & 1 ? Am : Ap;
+                        Wd[d] = f;
+                        Ws += f;
+                    }
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) el[n][c] += c0 * (ph.mu * Ws + (ph.mu + ph.lam) * Wd[c]);
+                    el[n][DIM] += c1 * P + gcew * Ws;
+                }
+            }
+        } else {
+            const int tb = li + NTX * (lj + NTY * lk);
+            double m_[NC + 1][NV];
+#pragma unroll
+            for (int c = 0; c <= NC; ++c) {
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    const int off = (n & 1) + NTX * (((n >> 1) & 1) + NTY * (DIM == 3 ? (n >> 2) & 1 : 0));
+                    m_[c][n] = sv[c * NT + tb + off];
+                }
+                fwd<DIM>(m_[c]);
+            }
+            double H[NC][DIM][NV / 2], F[NV];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                    for (int j = 0; j < NV / 2; ++j) H[c][d][j] = 0.0;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) F[k] = 0.0;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                double gu[DIM][DIM], gphi[DIM], phi = 0.0, ptv = 0.0;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const double sc = sgn(k, q) * gp[popc(k)] / NV;
+                    phi += sc * m_[DIM][k];
+                    ptv += sc * m_[NC][k];
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        double acc = 0.0;
+#pragma unroll
+                        for (int kp = 0; kp < NV; ++kp) {
+                            if (kp & (1 << d)) continue;
+                            acc += sgn(kp, q) * gp[popc(kp)] * m_[c][kp | (1 << d)];
+                        }
+                        acc *= 2.0 / (g.h[d] * NV);
+                        if (c < DIM) gu[c][d] = acc; else gphi[d] = acc;
+                    }
+                double e[DIM][DIM], tr = 0.0, ee = 0.0;
+#pragma unroll
+                for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                    for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) tr += e[i][i];
+#pragma unroll
+                for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                    for (int j = 0; j < DIM; ++j) ee += e[i][j] * e[i][j];
+                const double Es = 0.5 * ph.lam * tr * tr + ph.mu * ee;
+                const double gk = (1.0 - ph.kappa) * ptv * ptv + ph.kappa;
+                // -A(U): u-rows g(phi~) sigma(u) + phi~^2 p I; phi-rows f g'(phi) E_s + 2 phi p div u
+                // - Gc/eps (1 - phi); gradient part Gc eps grad phi
+                double fl[NC][DIM];
+#pragma unroll
+                for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                    for (int j = 0; j < DIM; ++j)
+                        fl[i][j] = -w * (gk * (2.0 * ph.mu * e[i][j] + (i == j ? ph.lam * tr : 0.0)) +
+                                         (i == j ? ptv * ptv * ph.p : 0.0));
+#pragma unroll
+                for (int j = 0; j < DIM; ++j) fl[DIM][j] = -w * ph.Gc * ph.eps * gphi[j];
+                const double fv = -w * (ph.f * 2.0 * (1.0 - ph.kappa) * phi * Es + 2.0 * phi * ph.p * tr -
+                                        ph.Gc / ph.eps * (1.0 - phi));
+#pragma unroll
+                for (int k = 0; k < NV; ++k) F[k] += sgn(k, q) * fv;
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        int j = 0;
+#pragma unroll
+                        for (int kp = 0; kp < NV; ++kp) {
+                            if (kp & (1 << d)) continue;
+                            H[c][d][j] += sgn(kp, q) * fl[c][d];
+                            ++j;
+                        }
+                    }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                double Y[NV];
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    double acc = (c == DIM) ? F[k] * gp[popc(k)] / NV : 0.0;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        if (!(k & (1 << d))) continue;
+                        const int kp = k & ~(1 << d);
+                        const int j = (kp & ((1 << d) - 1)) | ((kp >> (d + 1)) << d);
+                        acc += H[c][d][j] * gp[popc(kp)] * (2.0 / (g.h[d] * NV));
+                    }
+                    Y[k] = acc;
+                }
+                inv<DIM>(Y);
+#pragma unroll
+                for (int n = 0; n < NV; ++n) el[n][c] = Y[n];
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NV; ++n)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sel[(n * NC + c) * NCELL + cell] = el[n][c];
+    __syncthreads();
+    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+        const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
+        const int gi = ci0 + ti, gj = cj0 + tj, gk = ck0 + tk;
+        if (!(gi < g.nn[0] && gj < g.nn[1] && gk < g.nn[2])) continue;
+        const int64_t gn = (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk);
+        const uint8_t m = OP == 1 ? mask[gn] : 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (OP == 1 && (c < DIM ? ((m >> c) & 1) != 0 : (m & PHI_BITS_ALL) != 0)) continue;
+            double s = 0.0;
+#pragma unroll
+            for (int dk = 0; dk < (DIM == 3 ? 2 : 1); ++dk) {
+                const int ck = tk - dk;
+                if (DIM == 3 && (ck < 0 || ck >= T::TZ)) continue;
+#pragma unroll
+                for (int dj = 0; dj < 2; ++dj) {
+                    const int cj = tj - dj;
+                    if (cj < 0 || cj >= T::TY) continue;
+#pragma unroll
+                    for (int di = 0; di < 2; ++di) {
+                        const int cx = ti - di;
+                        if (cx < 0 || cx >= T::TX) continue;
+                        const int n = di + 2 * dj + 4 * dk;
+                        s += sel[(n * NC + c) * NCELL + cx + T::TX * (cj + T::TY * (DIM == 3 ? ck : 0))];
+                    }
+                }
+            }
+            atomicAdd(&y[c * nn + gn], s);
+        }
+    }
+}
+
+template <int OP>
+static cudaError_t launch_resdiag(const Geom& g, const Phys& ph, const double* U, const double* pt,
+                                  const float2* q64, const uint8_t* mask, double* y, cudaStream_t s) {
+    const double gpt = 1.0 / sqrt(3.0);
+    if (g.dim == 3) {
+        using T = RDTile<3>;
+        dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
+        k_q1_resdiag<3, OP><<<grid, T::TX * T::TY * T::TZ, 0, s>>>(g, ph, U, pt, q64, mask, y, gpt);
+    } else {
+        using T = RDTile<2>;
+        dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, 1);
+        k_q1_resdiag<2, OP><<<grid, T::TX * T::TY, 0, s>>>(g, ph, U, pt, q64, mask, y, gpt);
+    }
+    return count_launch(cudaGetLastError());
+}
+
+cudaError_t launch_q1_residual(const Geom& g, const Phys& ph, const double* U, const double* pt, double* R,
+                               cudaStream_t s) {
+    return launch_resdiag<0>(g, ph, U, pt, nullptr, nullptr, R, s);
+}
+cudaError_t launch_q1_diagonal(const Geom& g, const Phys& ph, const float2* q64, const uint8_t* mask, double* d,
+                               cudaStream_t s) {
+    return launch_resdiag<1>(g, ph, nullptr, nullptr, q64, mask, d, s);
 }
 
 }  // namespace pff

@@ -5,6 +5,18 @@
 
 namespace pff {
 
+// Constants of the Q1 applies as (hi, lo) float pairs prepared on the host: the kernels use .x in
+// FP32 and (x, y) as a double-float, so no FP64 instruction runs in the applies.
+struct Q1Consts {
+    float2 cv[4];            // g^j / 2^d
+    float2 cg[3][3];         // g^j * 2 / (h_d 2^d)
+    float2 mu, mu2, lam;     // Lame coefficients, 2 mu
+    float2 gcew;             // Gc eps w (w = Gauss weight x |K|)
+    float2 g2;               // g / 2
+    float2 ih[3];            // 1 / h_d
+};
+Q1Consts make_q1_consts(const Geom& g, const Phys& ph);
+
 // St: element type of x/y in global memory (float or double); QT: element type of the stored
 // Gauss-point coefficients (float for the FP32 operator, float2 = df64 pair for FP64).
 template <typename St, typename QT>
@@ -15,9 +27,7 @@ struct Q1ApplyArgs {
     St* y;
     const uint8_t* mask;
     int phi_bits;
-    double cv[4];            // g^j / 2^d
-    double cg[3][3];         // g^j * 2 / (h_d 2^d)
-    double mu, lam, gcew;    // Lame coefficients, Gc eps w
+    Q1Consts k;
 };
 
 // number of stored coefficients per Gauss point and cell (c0, Sp, c1)
@@ -25,9 +35,17 @@ inline int q1_nk(int dim) { return dim == 3 ? 8 : 5; }
 
 cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, const double* pt, float* q32,
                                 float2* q64, cudaStream_t s);
+// lanes = true: one thread per (cell, Gauss point) with shuffle butterflies; false: one thread
+// per cell with the modal form in registers
 cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s);
 cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s);
+
+// -A(U) on a Q1 level (R zeroed by the caller) and diag(G~) on free rows (eliminated rows preset)
+cudaError_t launch_q1_residual(const Geom& g, const Phys& ph, const double* U, const double* pt, double* R,
+                               cudaStream_t s);
+cudaError_t launch_q1_diagonal(const Geom& g, const Phys& ph, const float2* q64, const uint8_t* mask, double* d,
+                               cudaStream_t s);
 
 }  // namespace pff

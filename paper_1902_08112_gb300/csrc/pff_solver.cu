@@ -60,9 +60,11 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
     if (h->fast_q1 && L.g.deg == 1 && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
         const bool bd = op == OP_APPLY_BLOCKDIAG;
         if constexpr (sizeof(T) == 8)
-            CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd, h->stream));
+            CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd,
+                                 (h->q1_style & 1) != 0, h->stream));
         else
-            CK(launch_q1_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd, h->stream));
+            CK(launch_q1_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd,
+                                 (h->q1_style & 2) != 0, h->stream));
     } else {
         CellArgs<T> a;
         a.g = L.g;
@@ -91,6 +93,9 @@ template <typename T>
 cudaError_t diagonal_level(pff_hierarchy* h, int l, T* d) {
     Level& L = h->lv[l];
     CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, PHI_BITS_ALL, (const T*)nullptr, d, T(1), h->stream));
+    if constexpr (sizeof(T) == 8) {
+        if (h->fast_q1 && L.g.deg == 1) return launch_q1_diagonal(L.g, h->ph, L.qpd64, L.mask, (double*)d, h->stream);
+    }
     CellArgs<T> a;
     a.g = L.g;
     a.ph = h->ph;
@@ -110,6 +115,7 @@ template cudaError_t diagonal_level<float>(pff_hierarchy*, int, float*);
 cudaError_t residual_fine(pff_hierarchy* h, double* R) {
     Level& L = h->lv[h->L - 1];
     CK(cudaMemsetAsync(R, 0, sizeof(double) * n_dofs(L.g), h->stream));
+    if (h->fast_q1 && L.g.deg == 1) return launch_q1_residual(L.g, h->ph, L.U64, L.pt64, R, h->stream);
     CellArgs<double> a;
     a.g = L.g;
     a.ph = h->ph;
@@ -190,10 +196,14 @@ __device__ int sturm_count(const double* a, const double* e, int k, double x) {
 }
 
 // Lanczos tridiagonal from CG coefficients (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
-// T_j,j+1 = sqrt(beta_j)/alpha_j) and its extreme eigenvalues by bisection.
+// T_j,j+1 = sqrt(beta_j)/alpha_j) and its extreme eigenvalues by multisection: one warp per
+// (block, extreme); each round the 32 lanes evaluate Sturm counts at 32 interior points of the
+// bracket and the bracket shrinks to the sub-interval where the count crosses the target
+// (count >= 1 for the smallest eigenvalue, count >= k for the largest).
 __global__ void k_cg_eigs(const double* s, int steps, double* out /* lmin_u, lmax_u, lmin_p, lmax_p */) {
-    const int b = threadIdx.x;
-    if (b >= 2) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= 4) return;
+    const int b = w >> 1, want_max = w & 1;
     const double* hist = s + S_HIST;
     double a[MAX_CG], e[MAX_CG];
     int k = 0;
@@ -203,8 +213,7 @@ __global__ void k_cg_eigs(const double* s, int steps, double* out /* lmin_u, lma
         k = it + 1;
     }
     if (k == 0) {
-        out[2 * b] = 1.0;
-        out[2 * b + 1] = 1.0;
+        if (lane == 0) out[2 * b + want_max] = 1.0;
         return;
     }
     for (int j = 0; j < k; ++j) {
@@ -216,28 +225,24 @@ __global__ void k_cg_eigs(const double* s, int steps, double* out /* lmin_u, lma
         }
         e[j] = sqrt(be) / al;
     }
-    // Gershgorin bounds
-    double lo = 1e300, hi = -1e300;
+    double lo = 1e300, hi = -1e300;   // Gershgorin bracket
     for (int j = 0; j < k; ++j) {
         const double r = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j + 1 < k ? fabs(e[j]) : 0.0);
         lo = fmin(lo, a[j] - r);
         hi = fmax(hi, a[j] + r);
     }
-    // smallest: largest x with count(x) == 0; largest: smallest x with count(x) == k
-    double l0 = lo, h0 = hi;
-    for (int it = 0; it < 200; ++it) {
-        const double m = 0.5 * (l0 + h0);
-        if (m <= l0 || m >= h0) break;
-        if (sturm_count(a, e, k, m) >= 1) h0 = m; else l0 = m;
+    const int target = want_max ? k : 1;
+    for (int round = 0; round < 16; ++round) {
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const unsigned hit = __ballot_sync(0xffffffffu, sturm_count(a, e, k, x) >= target);
+        const int first = hit ? __ffs(hit) - 1 : 32;   // first lane whose point reaches the target
+        const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / 33.0;
+        const double nhi = first == 32 ? hi : lo + (hi - lo) * (double)(first + 1) / 33.0;
+        if (!(nhi - nlo < hi - lo)) break;
+        lo = nlo;
+        hi = nhi;
     }
-    double l1 = lo, h1 = hi;
-    for (int it = 0; it < 200; ++it) {
-        const double m = 0.5 * (l1 + h1);
-        if (m <= l1 || m >= h1) break;
-        if (sturm_count(a, e, k, m) >= k) h1 = m; else l1 = m;
-    }
-    out[2 * b] = 0.5 * (l0 + h0);
-    out[2 * b + 1] = 0.5 * (l1 + h1);
+    if (lane == 0) out[2 * b + want_max] = 0.5 * (lo + hi);
 }
 
 template <typename T>
@@ -267,7 +272,7 @@ static cudaError_t eigen_estimate(pff_hierarchy* h, int l, double* d_out) {
         CK(count_launch(cudaGetLastError()));
         CK(launch_cg_update_p<T>(L.g, p, z, sc + S_BE, s));
     }
-    k_cg_eigs<<<1, 32, 0, s>>>(sc, steps, d_out);
+    k_cg_eigs<<<1, 128, 0, s>>>(sc, steps, d_out);
     return count_launch(cudaGetLastError());
 }
 

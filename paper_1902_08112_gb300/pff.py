@@ -50,6 +50,7 @@ SIGNATURES = {
     "pff_default_params": (None, [ctypes.POINTER(Params)]),
     "pff_create_hierarchy": (_I, [ctypes.POINTER(Mesh), ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]),
     "pff_destroy_hierarchy": (_I, [_VP]),
+    "pff_hierarchy_bytes": (ctypes.c_int64, [ctypes.POINTER(Mesh), _I]),
     "pff_level_info": (_I, [_VP, _I, _I64P, _I64P, ctypes.POINTER(ctypes.c_int)]),
     "pff_set_params": (_I, [_VP, ctypes.POINTER(Params)]),
     "pff_set_kernel_variant": (_I, [_VP, _I]),
@@ -75,6 +76,13 @@ SIGNATURES = {
     "pff_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "pff_active_set_noalloc": (_I, [ctypes.POINTER(Mesh), ctypes.POINTER(Params), _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _VP]),
+    "pff_batch_create": (_I, [_I, ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)]),
+    "pff_batch_destroy": (_I, [_VP]),
+    "pff_batch_setup": (_I, [_VP]),
+    "pff_batch_vcycle": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "pff_batch_gmres_solve": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _I, ctypes.POINTER(SolveInfo)]),
+    "pff_batch_newton_step": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(NewtonInfo)]),
+    "pff_batch_last_error": (ctypes.c_char_p, [_VP]),
     "pff_launch_count": (ctypes.c_longlong, []),
     "pff_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -152,6 +160,10 @@ def create_hierarchy(mesh: Mesh, params: Params, stream=None):
     st = load().pff_create_hierarchy(ctypes.byref(mesh), ctypes.byref(params), s, ctypes.byref(h))
     _check(None, st, "pff_create_hierarchy")
     return h
+
+
+def hierarchy_bytes(mesh: Mesh, restart: int = 30) -> int:
+    return int(load().pff_hierarchy_bytes(ctypes.byref(mesh), restart))
 
 
 def destroy_hierarchy(h):
@@ -276,6 +288,55 @@ def active_set_noalloc(mesh: Mesh, params: Params, R, U, phi_old, mask, stream=N
                                        _ptr(mask), ctypes.byref(na), ctypes.byref(nc), s)
     _check(None, st, "pff_active_set_noalloc")
     return na.value, nc.value
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t_ in enumerate(ts):
+        arr[i] = _ptr(t_).value
+    return arr
+
+
+def _bcheck(b, st, where, allow=()):
+    if st != OK and st not in allow:
+        msg = load().pff_batch_last_error(b).decode() if b else ""
+        raise PffError(st, where, msg)
+    return st
+
+
+def batch_create(hierarchies, restart=30):
+    arr = (ctypes.c_void_p * len(hierarchies))(*[h.value for h in hierarchies])
+    b = ctypes.c_void_p()
+    st = load().pff_batch_create(len(hierarchies), arr, restart, ctypes.byref(b))
+    _check(None, st, "pff_batch_create")
+    return b
+
+
+def batch_destroy(b):
+    return _bcheck(b, load().pff_batch_destroy(b), "pff_batch_destroy")
+
+
+def batch_setup(b):
+    return _bcheck(b, load().pff_batch_setup(b), "pff_batch_setup")
+
+
+def batch_vcycle(b, rs, zs):
+    return _bcheck(b, load().pff_batch_vcycle(b, _ptr_array(rs), _ptr_array(zs)), "pff_batch_vcycle")
+
+
+def batch_gmres_solve(b, rhs, xs, rtol=1e-8, maxit=200, allow_noconv=False):
+    infos = (SolveInfo * len(rhs))()
+    allow = (ENOCONV,) if allow_noconv else ()
+    st = load().pff_batch_gmres_solve(b, _ptr_array(rhs), _ptr_array(xs), rtol, maxit, infos)
+    _bcheck(b, st, "pff_batch_gmres_solve", allow)
+    return list(infos)
+
+
+def batch_newton_step(b, Us, allow_noconv=False):
+    infos = (NewtonInfo * len(Us))()
+    allow = (ENOCONV,) if allow_noconv else ()
+    _bcheck(b, load().pff_batch_newton_step(b, _ptr_array(Us), infos), "pff_batch_newton_step", allow)
+    return list(infos)
 
 
 def launch_count() -> int:

@@ -68,6 +68,10 @@ CASES = {
     "2d_q2": (lambda: W.small(W.config_2d_single_crack(deg=2), 12, 2), 1),
     "3d_q1": (lambda: W.small(W.config_3d_penny(), 20, 3), 0),
     "3d_q1_generic": (lambda: W.small(W.config_3d_penny(), 12, 2), 1),
+    "3d_q1_lanes": (lambda: W.small(W.config_3d_penny(), 12, 2), 2),
+    "3d_q1_percell": (lambda: W.small(W.config_3d_penny(), 12, 2), 3),
+    "2d_q1_lanes": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 2),
+    "2d_q1_percell": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 3),
     "3d_q2": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1),
 }
 
