@@ -303,6 +303,7 @@ def main():
     cnt64, ms64 = pff.profile_read(h, pff.PROF_APPLY64_FINE)
     cnt64c, ms64c = pff.profile_read(h, pff.PROF_APPLY64_COARSE)
     cnt32, ms32 = pff.profile_read(h, pff.PROF_APPLY32)
+    cntv, msv = pff.profile_read(h, pff.PROF_VCYCLE)
     pff.profile(h, False)
     if ws > 1:
         t = torch.tensor([ms_total, ms64 / max(cnt64, 1)], device=dev, dtype=torch.float64)
@@ -367,23 +368,37 @@ def main():
             yh.copy_(yd, non_blocking=True)
     e2e_ms = timed(e2e_step, reps=max(3, args.steps))
 
-    # ---- roofline of the dominant kernel class inside the timed steps
-    classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32)}
-    dom = max(classes, key=lambda k: classes[k][1])
+    # ---- FP32 fine-level apply (the V-cycle operator), timed alone
+    x32 = torch.randn(nd, dtype=torch.float32, device=dev)
+    y32 = torch.empty_like(x32)
+    ms32_fine = timed(lambda: pff.apply_jacobian_f32(h, -1, x32, y32), reps=10)
+
+    # ---- rooflines.  The applies are arithmetic-bound on GB300: the FP64-accurate apply runs as
+    # double-float on the FP32 pipes.  Peak = FP32 pipe from unit counts and the max clock:
+    # 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  Algorithmic FP32 flops per cell of the
+    # double-float lane apply: 8 lanes x (92 double-float adds x 8 + 131 multiplies x 7) = 13224;
+    # of the FP32 per-cell apply: 1448 (the modal algorithm's adds and multiplies).
+    classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32),
+               "vcycle_graph": (cntv, msv)}
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    if dom == "apply64_fine":
-        bytes_per = 105.0 * nn
-        achieved = bytes_per / (apply_ms * 1e-3) / 1e9
-    else:
-        c, ms = classes[dom]
-        bytes_per = None
-        achieved = None
-    roof = {"kernel": "level_apply FP64 fine (k_cell OP_APPLY)" if dom == "apply64_fine" else dom,
-            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": (achieved / hbm) if achieved else None, "traffic": None,
-            "algorithmic_bytes_per_launch": bytes_per,
-            "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    cells = w.n_cells_total
+    fl64 = 13224.0 * cells
+    fl32 = 1448.0 * cells
+    roof = {"kernel": "k_q1_apply_lanes<3, df64> (FP64-accurate fine-level Jacobian apply)",
+            "bound": "alu", "achieved": fl64 / (apply_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+            "traffic": None, "algorithmic_flops_per_launch": fl64,
+            "note": "peak: FP32 pipe derived from unit counts and 2.07 GHz; double-float arithmetic on FP32 pipes",
+            "hbm": {"achieved": 105.0 * nn / (apply_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": 105.0 * nn / (apply_ms * 1e-3) / 1e9 / hbm,
+                    "algorithmic_bytes_per_launch": 105.0 * nn, "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "fp64_equivalent_tflops": 8 * 223.0 * cells / (apply_ms * 1e-3) / 1e12}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof32 = {"kernel": "k_q1_apply<3, float> (FP32 fine-level V-cycle operator)", "ms": ms32_fine,
+              "bound": "alu", "achieved": fl32 / (ms32_fine * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+              "frac": fl32 / (ms32_fine * 1e-3) / 1e12 / fp32_peak,
+              "hbm_frac": 53.0 * nn / (ms32_fine * 1e-3) / 1e9 / hbm, "gdofs": nd / (ms32_fine * 1e-3) / 1e9}
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -397,6 +412,7 @@ def main():
                 "d2h_bytes_per_step": nd * 8},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_fp32_apply": roof32,
         "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in classes.items()},
         "newton": {"gmres_iterations": [i.solve.iterations for i in infos], "n_active": n_act},
         "solve": res,

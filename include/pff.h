@@ -177,6 +177,11 @@ pff_status pff_update_active_set(pff_hierarchy* h, int* n_active, int* n_changed
  * (FP64, device output of n_dofs). */
 pff_status pff_residual(pff_hierarchy* h, double* R);
 
+/* Bulk energy int g(phi) E_s(e(u)) + phi^2 p div u and crack energy
+ * int Gc/2 ((1 - phi)^2 / eps + eps |grad phi|^2) of Sec. 5 (no stress split) at the current fine
+ * state, FP64, Q1 meshes.  out (host): [bulk, crack].  Synchronises. */
+pff_status pff_energies(pff_hierarchy* h, double out[2]);
+
 /* Matrix-free Jacobian apply y = G~_l(U_l) x on a level (Sec. 4.1, 4.2), FP64: the level's
  * operator at its restricted state, eliminated rows give y = x, eliminated columns are
  * ignored.  x and y must not overlap.  The finest level is the Newton Jacobian G~_k. */
@@ -240,6 +245,25 @@ pff_status pff_gmres_solve(pff_hierarchy* h, const double* b, double* x, double 
  * maxit 200), U += dU.  The new U becomes the hierarchy's state. */
 pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_info* info);
 
+/* One incremental (load) step n of the quasi-static problem (Sec. 2.1, 2.3) solved by Algorithm 1.
+ * U (device, in/out, FP64, component-blocked) holds U^{n-1} on entry and U^n on return.
+ * The step sets phi_old := phi^{n-1} (the phi block of U), the pressure to 'pressure' (the rest of
+ * the parameters unchanged), and the time-lagged extrapolation phi~ = clamp(2 phi^{n-1} - phi^{n-2},
+ * 0, 1), or phi~ = phi^{n-1} when phi_prev (device, n_nodes, phi^{n-2}) is NULL.  It then runs
+ * active-set Newton steps (pff_newton_step) until Algorithm 1's stop test holds or max_newton
+ * steps ran.  The active set of the previous load step serves as A_{k-1} of the first step.
+ * phi_prev must not alias U.  info (host, nullable) receives the step counts and the last step's
+ * Newton info.  Errors: those of pff_newton_step; PFF_EINVAL for max_newton < 1 or a non-finite
+ * pressure.  A step cap reached without convergence returns PFF_OK with info->converged = 0. */
+typedef struct {
+    int newton_steps;      /* active-set steps run */
+    int converged;         /* 1 if Algorithm 1 stopped by its test */
+    int gmres_iterations;  /* summed over the steps */
+    pff_newton_info last;  /* the last step */
+} pff_load_info;
+pff_status pff_load_step(pff_hierarchy* h, double* U, const double* phi_prev, double pressure, int max_newton,
+                         pff_load_info* info);
+
 /* ---- Batches of independent instances (one launch per level and operation across instances).
  * A batch is a view over n existing hierarchies created on the same stream, all Q1 with the same
  * dimension, mg_precision 32 and cheb_degree; instances may differ in mesh size, number of levels
@@ -269,8 +293,11 @@ const char* pff_batch_last_error(const pff_batch* b);
  * rows plus the cell kernel); pff_profile(h, 0) stops.  pff_profile_read synchronises and
  * returns, for one class, the number of launches and their summed device time in ms.
  * Classes: PFF_PROF_APPLY64_FINE (FP64 operator on the finest level), PFF_PROF_APPLY64_COARSE
- * (FP64 operators on coarser levels), PFF_PROF_APPLY32 (FP32 operators, all levels). */
-enum { PFF_PROF_APPLY64_FINE = 0, PFF_PROF_APPLY64_COARSE = 1, PFF_PROF_APPLY32 = 2, PFF_PROF_NCLASS = 3 };
+ * (FP64 operators on coarser levels), PFF_PROF_APPLY32 (FP32 operators, all levels), and
+ * PFF_PROF_VCYCLE (replays of a captured V-cycle graph: the operators inside a replayed graph are
+ * timed as part of the replay, not in their own classes). */
+enum { PFF_PROF_APPLY64_FINE = 0, PFF_PROF_APPLY64_COARSE = 1, PFF_PROF_APPLY32 = 2, PFF_PROF_VCYCLE = 3,
+       PFF_PROF_NCLASS = 4 };
 pff_status pff_profile(pff_hierarchy* h, int enable);
 pff_status pff_profile_read(pff_hierarchy* h, int cls, int* count, double* total_ms);
 

@@ -63,6 +63,7 @@ def lib():
         L.om_energy.restype = ctypes.c_double
         L.om_energy.argtypes = [P(_Mesh), P(_Phys), d]
         L.om_lumped_mass.argtypes = [P(_Mesh), d]
+        L.om_energy_parts.argtypes = [P(_Mesh), P(_Phys), d, d]
         L.om_csr_structure.restype = ctypes.c_int64
         L.om_csr_structure.argtypes = [P(_Mesh), i64]
         L.om_assemble.argtypes = [P(_Mesh), P(_Phys), d, d, u8, ctypes.c_int, i64, i64, d]
@@ -175,6 +176,15 @@ def energy(mesh: Mesh, phys: Phys, U) -> float:
     U = _f64(U)
     m, ph = mesh.c(), phys.c()
     return lib().om_energy(ctypes.byref(m), ctypes.byref(ph), _dp(U))
+
+
+def energy_parts(mesh: Mesh, phys: Phys, U) -> tuple:
+    """(bulk, crack) energies of Sec. 5 (no stress split)."""
+    U = _f64(U)
+    out = np.zeros(2)
+    m, ph = mesh.c(), phys.c()
+    lib().om_energy_parts(ctypes.byref(m), ctypes.byref(ph), _dp(U), _dp(out))
+    return float(out[0]), float(out[1])
 
 
 def lumped_mass(mesh: Mesh) -> np.ndarray:

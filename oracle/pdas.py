@@ -15,6 +15,11 @@ Step k, with the lumped Gauss-Lobatto mass M of the remark after Algorithm 1:
   5. solve G~ dU = R~ with FGMRES preconditioned by the monolithic V-cycle (Sec. 3.3)
   6. U_{k+1} = U_k + dU
 Stop when the active set repeats and ||R~_k||_2 <= eps_as.
+
+Load stepping (Sec. 2.1, 2.3): at incremental step n, phi_old = phi^{n-1} and the time-lagged
+extrapolation phi~ = clamp(2 phi^{n-1} - phi^{n-2}, 0, 1) (phi^{n-1} at the first step) enters
+g(phi~) and phi~^2 of the u-equation; Algorithm 1 runs until its stop test, the previous load
+step's active set serving as A_{k-1} of the first Newton step.
 """
 from __future__ import annotations
 
@@ -79,3 +84,26 @@ def newton_step(mesh, phys, n_levels, U, phi_old, ptil, dir_mask, prev_active, c
     res = float(np.linalg.norm(Rt))
     conv = prev_active is not None and n_changed == 0 and res <= tol_as
     return U + dU, StepInfo(act, n_changed, res, its, lin_res, lin_res0, conv)
+
+
+def extrapolate(phi_nm1, phi_nm2=None):
+    """phi~ of Sec. 2.3 (linear in time, clamped to [0, 1])."""
+    phi_nm1 = np.asarray(phi_nm1, dtype=np.float64)
+    if phi_nm2 is None:
+        return phi_nm1.copy()
+    return np.clip(2.0 * phi_nm1 - np.asarray(phi_nm2, dtype=np.float64), 0.0, 1.0)
+
+
+def load_step(mesh, phys, n_levels, U, phi_prev, dir_mask, prev_active, max_newton=20, **kw):
+    """One incremental step at phys.p; returns (U^n, list of StepInfo)."""
+    nn = mesh.n_nodes
+    phi_old = np.array(U[mesh.dim * nn:], dtype=np.float64)
+    ptil = extrapolate(phi_old, phi_prev)
+    infos = []
+    for _ in range(max_newton):
+        U, info = newton_step(mesh, phys, n_levels, U, phi_old, ptil, dir_mask, prev_active, **kw)
+        infos.append(info)
+        prev_active = info.active
+        if info.converged:
+            break
+    return U, infos

@@ -396,6 +396,27 @@ void om_residual(const om_mesh *m, const om_phys *ph, const double *U, const dou
     free(qd);
 }
 
+/* Bulk and crack energies of Sec. 5 separately (no split): out[0] = int g(phi) E_s + phi^2 p div u,
+ * out[1] = int Gc/2 ( (1-phi)^2/eps + eps |grad phi|^2 ).  Evaluated with Gc = 0 and with E = p = 0
+ * through element_energy, so the two parts add up to om_energy exactly in exact arithmetic. */
+void om_energy_parts(const om_mesh *m, const om_phys *ph, const double *U, double *out) {
+    int64_t nn = om_n_nodes(m), ncell = om_n_cells(m);
+    om_qpdata *qd = malloc(sizeof(om_qpdata));
+    cell_qpdata(m, qd);
+    int64_t nodes[MAXN];
+    om_phys bulk = *ph, crack = *ph;
+    bulk.Gc = 0.0;
+    crack.mu = 0.0; crack.lam = 0.0; crack.p = 0.0;
+    out[0] = 0.0;
+    out[1] = 0.0;
+    for (int64_t cell = 0; cell < ncell; ++cell) {
+        cell_nodes(m, cell, nodes);
+        out[0] += element_energy(m, &bulk, qd, nodes, nn, U);
+        out[1] += element_energy(m, &crack, qd, nodes, nn, U);
+    }
+    free(qd);
+}
+
 double om_energy(const om_mesh *m, const om_phys *ph, const double *U) {
     int64_t nn = om_n_nodes(m), ncell = om_n_cells(m);
     om_qpdata *qd = malloc(sizeof(om_qpdata));

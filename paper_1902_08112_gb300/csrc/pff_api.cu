@@ -239,6 +239,7 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
 extern "C" pff_status pff_destroy_hierarchy(pff_hierarchy* h) {
     if (!h) return PFF_OK;
     cudaStreamSynchronize(h->stream);
+    drop_graph(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     free_all(h);
     delete h;
@@ -307,6 +308,7 @@ extern "C" pff_status pff_set_params(pff_hierarchy* h, const pff_params* params)
 extern "C" pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant) {
     if (!h) return PFF_EINVAL;
     REQUIRE(h, variant >= 0 && variant <= 3, PFF_EINVAL, "variant must be 0, 1, 2 or 3");
+    drop_graph(h);
     h->fast_q1 = variant != 1;
     h->q1_style = variant == 2 ? 3 : (variant == 3 ? 0 : 1);
     h->stale = true;
@@ -366,6 +368,17 @@ extern "C" pff_status pff_update_active_set(pff_hierarchy* h, int* n_active, int
     if (!h) return PFF_EINVAL;
     REQUIRE(h, h->has_state, PFF_ESTATE, "pff_update_active_set before pff_set_state");
     return update_active(h, n_active, n_changed);
+}
+
+extern "C" pff_status pff_energies(pff_hierarchy* h, double out[2]) {
+    if (!h || !out) return PFF_EINVAL;
+    REQUIRE(h, h->has_state, PFF_ESTATE, "pff_energies before pff_set_state");
+    REQUIRE(h, h->mesh.degree == 1, PFF_EINVAL, "pff_energies supports Q1 meshes");
+    Level& F = h->lv[h->L - 1];
+    CUDA_OR_FAIL(h, launch_q1_energies(F.g, h->ph, F.U64, h->d_scratch, h->d_scal + 400, h->stream));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(out, h->d_scal + 400, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    return PFF_OK;
 }
 
 extern "C" pff_status pff_residual(pff_hierarchy* h, double* R) {
@@ -617,6 +630,42 @@ extern "C" pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_in
         info->converged = (n_chg == 0 && res <= h->prm.tol_as) ? 1 : 0;
     }
     if (st == PFF_ENOCONV) h->err = err;
+    return st;
+}
+
+extern "C" pff_status pff_load_step(pff_hierarchy* h, double* U, const double* phi_prev, double pressure,
+                                    int max_newton, pff_load_info* info) {
+    if (!h) return PFF_EINVAL;
+    REQUIRE(h, U, PFF_EINVAL, "pff_load_step: NULL U");
+    REQUIRE(h, max_newton >= 1, PFF_EINVAL, "pff_load_step: max_newton must be >= 1");
+    REQUIRE(h, std::isfinite(pressure), PFF_EINVAL, "pff_load_step: non-finite pressure");
+    Level& F = h->lv[h->L - 1];
+    const int64_t nn = F.g.n_nodes;
+    cudaStream_t s = h->stream;
+    h->prm.pressure = pressure;
+    h->ph = make_phys(h->prm);
+    h->stale = true;
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->phi_old, U + (int64_t)F.g.dim * nn, nn * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+    CUDA_OR_FAIL(h, launch_extrapolate(nn, h->phi_old, phi_prev, F.pt64, s));
+    h->has_state = true;
+    pff_load_info li;
+    memset(&li, 0, sizeof(li));
+    pff_status st = PFF_OK;
+    for (int k = 0; k < max_newton; ++k) {
+        pff_newton_info ni;
+        memset(&ni, 0, sizeof(ni));
+        st = pff_newton_step(h, U, &ni);
+        if (st != PFF_OK && st != PFF_ENOCONV) break;
+        li.newton_steps = k + 1;
+        li.gmres_iterations += ni.solve.iterations;
+        li.last = ni;
+        if (ni.converged) {
+            li.converged = 1;
+            break;
+        }
+    }
+    if (info) *info = li;
     return st;
 }
 

@@ -31,19 +31,21 @@ __device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {   // require
     return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
+// The pairs are kept unnormalised: the high parts combine exactly (TwoSum, TwoProduct) and the low
+// parts accumulate in plain FP32, without the FastTwoSum renormalisation after each operation.
+// The applies are chains of linear stages whose low parts stay ~2^-24 of the magnitudes involved,
+// so each operation still carries a relative error of order 2^-48 of its operands.
 __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
     const df64 s = df_two_sum(a.hi, b.hi);
-    const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
-    return df_fast_two_sum(s.hi, e);
+    return df_make(s.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo));
 }
 __device__ __forceinline__ df64 operator-(df64 a) { return df_make(-a.hi, -a.lo); }
 __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    return df_fast_two_sum(p, e);
+    return df_make(p, __fmaf_rn(a.hi, b.lo, e));
 }
 __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { a = a - b; return a; }

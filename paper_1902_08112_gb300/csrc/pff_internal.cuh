@@ -147,6 +147,8 @@ cudaError_t launch_active_set(const Geom& g, const double* R, const double* M, c
                               int* counts, cudaStream_t s);
 cudaError_t launch_newton_rhs(const Geom& g, const double* R, const double* t, const double* U,
                               const double* phi_old, const uint8_t* mask, double* Rt, cudaStream_t s);
+cudaError_t launch_extrapolate(int64_t n, const double* phi_nm1, const double* phi_nm2, double* out,
+                               cudaStream_t s);
 cudaError_t launch_active_delta(const Geom& g, const double* U, const double* phi_old,
                                 const uint8_t* mask, double* delta, cudaStream_t s);
 
@@ -190,6 +192,9 @@ struct pff_hierarchy {
     bool has_state = false;
     bool fast_q1 = true;             // Q1 levels use the linearisation-data kernels of pff_q1.cu
     int q1_style = 1;                // bit 0: df64 applies per Gauss-point lane; bit 1: FP32 likewise
+    bool use_graphs = true;          // replay the V-cycle body from a captured CUDA graph
+    cudaGraphExec_t vgraph = nullptr;   // captured V-cycle body (valid until the next setup)
+    long long vgraph_nodes = 0;
     bool active_known = false;       // an active set has been computed or set
     bool stale = true;               // preconditioner data out of date
     std::vector<void*> allocs;       // every device allocation, freed on destroy
@@ -197,7 +202,7 @@ struct pff_hierarchy {
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[3];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[PFF_PROF_NCLASS];
     std::string err;
 };
 

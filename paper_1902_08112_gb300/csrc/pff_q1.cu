@@ -208,6 +208,8 @@ Q1Consts make_q1_consts(const Geom& g, const Phys& ph) {
     k.lam = split_pair(ph.lam);
     k.gcew = split_pair(ph.Gc * ph.eps * vol / NV);
     k.g2 = split_pair(0.5 * gpt);
+    k.al = split_pair(0.5 * (1.0 + gpt));
+    k.be = split_pair(0.5 * (1.0 - gpt));
     for (int d = 0; d < 3; ++d) k.ih[d] = split_pair(d < dim ? 1.0 / g.h[d] : 0.0);
     return k;
 }
@@ -523,6 +525,7 @@ __device__ __forceinline__ df64 half_of(df64 v) { return df_make(0.5f * v.hi, 0.
 template <int DIM, typename S>
 struct LaneConst {
     S g2;           // g / 2
+    S al, be;       // (1 + g) / 2, (1 - g) / 2: interpolation weights of the near and far node
     S ih[DIM];      // 1 / h_e
 };
 
@@ -535,12 +538,12 @@ __device__ __forceinline__ void lane_eval(S v, int n, const LaneConst<DIM, S>& k
 #pragma unroll
         for (int d = 0; d < e; ++d) {
             const S p = shfl_xor(grad[d], 1 << e);
-            grad[d] = half_of(grad[d] + p) + k.g2 * (grad[d] - p);
+            grad[d] = k.al * grad[d] + k.be * p;
         }
         const S p = shfl_xor(v, 1 << e);
         const S diff = v - p;
         grad[e] = ((n >> e) & 1) ? diff * k.ih[e] : -(diff * k.ih[e]);
-        if (WANT_VAL || e + 1 < DIM) v = half_of(v + p) + k.g2 * diff;
+        if (WANT_VAL || e + 1 < DIM) v = k.al * v + k.be * p;
     }
     if (WANT_VAL) val = v;
 }
@@ -556,14 +559,14 @@ __device__ __forceinline__ S lane_integrate(S fv, S (&fg)[DIM], int n, const Lan
         const S td = ((n >> e) & 1) ? (fg[e] + pd) * k.ih[e] : -((fg[e] + pd) * k.ih[e]);
         if (HAS_VAL || e + 1 < DIM) {
             const S p = shfl_xor(tv, 1 << e);
-            tv = half_of(tv + p) + k.g2 * (tv - p) + td;
+            tv = k.al * tv + k.be * p + td;
         } else {
             tv = td;
         }
 #pragma unroll
         for (int d = 0; d < e; ++d) {
             const S p = shfl_xor(fg[d], 1 << e);
-            fg[d] = half_of(fg[d] + p) + k.g2 * (fg[d] - p);
+            fg[d] = k.al * fg[d] + k.be * p;
         }
     }
     return tv;
@@ -615,6 +618,8 @@ __device__ __forceinline__ void q1_apply_lanes_tile(
     const int64_t gid = valid ? (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)) : 0;
     LaneConst<DIM, S> k;
     k.g2 = cpair<S>(a.k.g2);
+    k.al = cpair<S>(a.k.al);
+    k.be = cpair<S>(a.k.be);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) k.ih[d] = cpair<S>(a.k.ih[d]);
     const S mu = cpair<S>(a.k.mu), mu2 = cpair<S>(a.k.mu2);
@@ -1116,6 +1121,107 @@ cudaError_t launch_q1_residual(const Geom& g, const Phys& ph, const double* U, c
 cudaError_t launch_q1_diagonal(const Geom& g, const Phys& ph, const float2* q64, const uint8_t* mask, double* d,
                                cudaStream_t s) {
     return launch_resdiag<1>(g, ph, nullptr, nullptr, q64, mask, d, s);
+}
+
+// ------------------------------------------------------------------ energies (Sec. 5)
+// bulk = int g(phi) E_s(e(u)) + phi^2 p div u, crack = int Gc/2 ((1 - phi)^2 / eps + eps |grad phi|^2)
+// per cell in FP64 at the Gauss points; per-CTA partials (fixed grid) summed in a fixed order.
+constexpr int kEnergyBlocks = 304;
+
+template <int DIM>
+__global__ void k_q1_energy(Geom g, Phys ph, const double* __restrict__ U, double gpt, double* __restrict__ part) {
+    constexpr int NV = 1 << DIM;
+    const int64_t nn = g.n_nodes;
+    double vol = 1.0;
+    for (int a = 0; a < DIM; ++a) vol *= g.h[a];
+    const double w = vol / NV;
+    double gp[DIM + 1];
+    gp[0] = 1.0;
+    for (int j = 1; j <= DIM; ++j) gp[j] = gp[j - 1] * gpt;
+    double eb = 0.0, ec = 0.0;
+    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < g.n_cells;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        int ci[3] = {0, 0, 0};
+        int64_t r = cell;
+        for (int a = 0; a < DIM; ++a) { ci[a] = (int)(r % g.nc[a]); r /= g.nc[a]; }
+        double m_[DIM + 1][NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) {
+            const int i = ci[0] + (n & 1), j = ci[1] + ((n >> 1) & 1), k = DIM == 3 ? ci[2] + ((n >> 2) & 1) : 0;
+            const int64_t node = (int64_t)i + (int64_t)g.nn[0] * ((int64_t)j + (int64_t)g.nn[1] * k);
+#pragma unroll
+            for (int c = 0; c <= DIM; ++c) m_[c][n] = U[c * nn + node];
+        }
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) fwd<DIM>(m_[c]);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double gr[DIM + 1][DIM], phi = 0.0;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) phi += sgn(k, q) * gp[popc(k)] / NV * m_[DIM][k];
+#pragma unroll
+            for (int c = 0; c <= DIM; ++c)
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int kp = 0; kp < NV; ++kp) {
+                        if (kp & (1 << d)) continue;
+                        acc += sgn(kp, q) * gp[popc(kp)] * m_[c][kp | (1 << d)];
+                    }
+                    gr[c][d] = acc * (2.0 / (g.h[d] * NV));
+                }
+            double tr = 0.0, ee = 0.0, gg = 0.0;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) tr += gr[i][i];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                for (int j = 0; j < DIM; ++j) {
+                    const double eij = 0.5 * (gr[i][j] + gr[j][i]);
+                    ee += eij * eij;
+                }
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) gg += gr[DIM][d] * gr[DIM][d];
+            const double Es = 0.5 * ph.lam * tr * tr + ph.mu * ee;
+            const double gk = (1.0 - ph.kappa) * phi * phi + ph.kappa;
+            eb += w * (gk * Es + phi * phi * ph.p * tr);
+            ec += w * 0.5 * ph.Gc * ((1.0 - phi) * (1.0 - phi) / ph.eps + ph.eps * gg);
+        }
+    }
+    __shared__ double sb[32], sc[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        eb += __shfl_xor_sync(0xffffffffu, eb, o);
+        ec += __shfl_xor_sync(0xffffffffu, ec, o);
+    }
+    const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sb[wid] = eb; sc[wid] = ec; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tb = 0.0, tc = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { tb += sb[i]; tc += sc[i]; }
+        part[2 * blockIdx.x] = tb;
+        part[2 * blockIdx.x + 1] = tc;
+    }
+}
+
+__global__ void k_energy_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double b = 0.0, c = 0.0;
+        for (int i = 0; i < n; ++i) { b += part[2 * i]; c += part[2 * i + 1]; }
+        out[0] = b;
+        out[1] = c;
+    }
+}
+
+cudaError_t launch_q1_energies(const Geom& g, const Phys& ph, const double* U, double* part, double* out,
+                               cudaStream_t s) {
+    const double gpt = 1.0 / sqrt(3.0);
+    if (g.dim == 3) k_q1_energy<3><<<kEnergyBlocks, 128, 0, s>>>(g, ph, U, gpt, part);
+    else k_q1_energy<2><<<kEnergyBlocks, 128, 0, s>>>(g, ph, U, gpt, part);
+    count_launch(cudaGetLastError());
+    k_energy_sum<<<1, 32, 0, s>>>(part, kEnergyBlocks, out);
+    return count_launch(cudaGetLastError());
 }
 
 }  // namespace pff

@@ -13,6 +13,7 @@ struct Q1Consts {
     float2 mu, mu2, lam;     // Lame coefficients, 2 mu
     float2 gcew;             // Gc eps w (w = Gauss weight x |K|)
     float2 g2;               // g / 2
+    float2 al, be;           // (1 + g) / 2, (1 - g) / 2
     float2 ih[3];            // 1 / h_d
 };
 Q1Consts make_q1_consts(const Geom& g, const Phys& ph);
@@ -46,6 +47,11 @@ cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, co
 cudaError_t launch_q1_residual(const Geom& g, const Phys& ph, const double* U, const double* pt, double* R,
                                cudaStream_t s);
 cudaError_t launch_q1_diagonal(const Geom& g, const Phys& ph, const float2* q64, const uint8_t* mask, double* d,
+                               cudaStream_t s);
+
+// bulk and crack energies of Sec. 5 at the state U (out[0] bulk, out[1] crack, device); part holds
+// 2 * 304 partial sums
+cudaError_t launch_q1_energies(const Geom& g, const Phys& ph, const double* U, double* part, double* out,
                                cudaStream_t s);
 
 }  // namespace pff

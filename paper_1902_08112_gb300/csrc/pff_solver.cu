@@ -276,8 +276,15 @@ static cudaError_t eigen_estimate(pff_hierarchy* h, int l, double* d_out) {
     return count_launch(cudaGetLastError());
 }
 
+void drop_graph(pff_hierarchy* h) {
+    if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
+    h->vgraph = nullptr;
+    h->vgraph_nodes = 0;
+}
+
 cudaError_t setup(pff_hierarchy* h) {
     cudaStream_t s = h->stream;
+    drop_graph(h);
     const bool f32 = h->prm.mg_precision == 32;
     double* d_eigs = h->d_scal + 512;   // 4 per level
     for (int l = 0; l < h->L; ++l) {
@@ -427,6 +434,52 @@ static cudaError_t vcycle_rec(pff_hierarchy* h, int l) {
     return smooth<T>(h, l, b, x, 0);
 }
 
+// The V-cycle between the fixed level buffers (input work 0, output work 1 of the finest level).
+// On a non-default stream it is captured once per setup into a CUDA graph and replayed: every
+// kernel argument (Chebyshev coefficients included) is fixed between setups.
+template <typename T>
+static cudaError_t vcycle_body(pff_hierarchy* h) {
+    if (!h->use_graphs || h->stream == nullptr) return vcycle_rec<T>(h, h->L - 1);
+    if (!h->vgraph) {
+        cudaGraph_t g = nullptr;
+        const bool prof = h->prof_on;
+        h->prof_on = false;                   // no timing events inside the captured body
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const long long c0 = launch_count();
+        cudaError_t e = vcycle_rec<T>(h, h->L - 1);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        h->prof_on = prof;
+        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            h->use_graphs = false;            // fall back to direct launches from now on
+            return vcycle_rec<T>(h, h->L - 1);
+        }
+        e = cudaGraphInstantiate(&h->vgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->vgraph = nullptr;
+            h->use_graphs = false;
+            return vcycle_rec<T>(h, h->L - 1);
+        }
+        h->vgraph_nodes = launch_count() - c0;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->prof_on) {
+        e0 = next_event(h);
+        e1 = next_event(h);
+        if (e0 && e1) CK(cudaEventRecord(e0, h->stream));
+    }
+    CK(cudaGraphLaunch(h->vgraph, h->stream));
+    if (e0 && e1) {
+        CK(cudaEventRecord(e1, h->stream));
+        h->prof[PFF_PROF_VCYCLE].push_back({e0, e1});
+    }
+    for (long long i = 0; i < h->vgraph_nodes; ++i) count_launch(cudaSuccess);
+    return cudaSuccess;
+}
+
 cudaError_t vcycle(pff_hierarchy* h, const double* r, double* z) {
     Level& F = h->lv[h->L - 1];
     const int64_t nd = n_dofs(F.g);
@@ -435,11 +488,11 @@ cudaError_t vcycle(pff_hierarchy* h, const double* r, double* z) {
         // b = free ? (float) r : 0
         CK(launch_mask_copy<double>(F.g, F.mask, r, h->tmp64[3], 1, h->stream));
         CK(launch_cast_f64_f32(h->tmp64[3], b, nd, h->stream));
-        CK(vcycle_rec<float>(h, h->L - 1));
+        CK(vcycle_body<float>(h));
         CK(launch_cast_f32_f64(work<float>(F, 1), z, nd, h->stream));
     } else {
         CK(launch_mask_copy<double>(F.g, F.mask, r, work<double>(F, 0), 1, h->stream));
-        CK(vcycle_rec<double>(h, h->L - 1));
+        CK(vcycle_body<double>(h));
         CK(cudaMemcpyAsync(z, work<double>(F, 1), sizeof(double) * nd, cudaMemcpyDeviceToDevice, h->stream));
     }
     return launch_mask_copy<double>(F.g, F.mask, r, z, 0, h->stream);

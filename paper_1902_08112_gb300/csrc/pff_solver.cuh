@@ -14,6 +14,7 @@ cudaError_t diagonal_level(pff_hierarchy* h, int l, T* d);
 cudaError_t residual_fine(pff_hierarchy* h, double* R);
 cudaError_t propagate_state(pff_hierarchy* h);
 cudaError_t setup(pff_hierarchy* h);
+void drop_graph(pff_hierarchy* h);
 template <typename T>
 cudaError_t smooth(pff_hierarchy* h, int l, const T* b, T* x, int zero_guess);
 cudaError_t coarse_solve(pff_hierarchy* h, const double* b, double* x);

@@ -534,6 +534,22 @@ cudaError_t launch_active_delta(const Geom& g, const double* U, const double* ph
     return count_launch(cudaGetLastError());
 }
 
+// time-lagged phi~ of Sec. 2.3: clamp(2 phi^{n-1} - phi^{n-2}, 0, 1); phi^{n-1} without phi^{n-2}
+__global__ void k_extrapolate(int64_t n, const double* __restrict__ p1, const double* __restrict__ p2,
+                              double* __restrict__ out) {
+    GRID_STRIDE(i, n) {
+        double v = p1[i];
+        if (p2) v = fmin(fmax(2.0 * v - p2[i], 0.0), 1.0);
+        out[i] = v;
+    }
+}
+cudaError_t launch_extrapolate(int64_t n, const double* phi_nm1, const double* phi_nm2, double* out,
+                               cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_extrapolate<<<grid_for(n), kThreads, 0, s>>>(n, phi_nm1, phi_nm2, out);
+    return count_launch(cudaGetLastError());
+}
+
 // R~ = R - t on free rows; phi_old - phi on active rows; 0 on Dirichlet rows (Algorithm 1, step 4)
 __global__ void k_newton_rhs(Geom g, const double* __restrict__ R, const double* __restrict__ t,
                              const double* __restrict__ U, const double* __restrict__ phi_old,

@@ -44,6 +44,11 @@ class NewtonInfo(ctypes.Structure):
                 ("converged", ctypes.c_int), ("solve", SolveInfo)]
 
 
+class LoadInfo(ctypes.Structure):
+    _fields_ = [("newton_steps", ctypes.c_int), ("converged", ctypes.c_int), ("gmres_iterations", ctypes.c_int),
+                ("last", NewtonInfo)]
+
+
 # C signatures: name -> (restype, argtypes)
 _VP, _I, _D, _I64P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
@@ -59,6 +64,7 @@ SIGNATURES = {
     "pff_get_active_set": (_I, [_VP, _VP]),
     "pff_update_active_set": (_I, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pff_residual": (_I, [_VP, _VP]),
+    "pff_energies": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pff_apply_jacobian": (_I, [_VP, _I, _VP, _VP]),
     "pff_apply_jacobian_f32": (_I, [_VP, _I, _VP, _VP]),
     "pff_diagonal": (_I, [_VP, _I, _I, _VP]),
@@ -72,6 +78,7 @@ SIGNATURES = {
     "pff_vcycle": (_I, [_VP, _VP, _VP]),
     "pff_gmres_solve": (_I, [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(SolveInfo)]),
     "pff_newton_step": (_I, [_VP, _VP, ctypes.POINTER(NewtonInfo)]),
+    "pff_load_step": (_I, [_VP, _VP, _VP, _D, _I, ctypes.POINTER(LoadInfo)]),
     "pff_profile": (_I, [_VP, _I]),
     "pff_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "pff_active_set_noalloc": (_I, [ctypes.POINTER(Mesh), ctypes.POINTER(Params), _VP, _VP, _VP, _VP,
@@ -87,7 +94,7 @@ SIGNATURES = {
     "pff_last_error": (ctypes.c_char_p, [_VP]),
 }
 
-PROF_APPLY64_FINE, PROF_APPLY64_COARSE, PROF_APPLY32 = 0, 1, 2
+PROF_APPLY64_FINE, PROF_APPLY64_COARSE, PROF_APPLY32, PROF_VCYCLE = 0, 1, 2, 3
 
 _lib = None
 
@@ -203,6 +210,12 @@ def update_active_set(h):
     return na.value, nc.value
 
 
+def energies(h):
+    out = (ctypes.c_double * 2)()
+    _check(h, load().pff_energies(h, out), "pff_energies")
+    return out[0], out[1]
+
+
 def residual(h, R):
     return _check(h, load().pff_residual(h, _ptr(R)), "pff_residual")
 
@@ -266,6 +279,14 @@ def newton_step(h, U, allow_noconv=False):
     info = NewtonInfo()
     allow = (ENOCONV,) if allow_noconv else ()
     _check(h, load().pff_newton_step(h, _ptr(U), ctypes.byref(info)), "pff_newton_step", allow)
+    return info
+
+
+def load_step(h, U, phi_prev, pressure: float, max_newton: int = 20, allow_noconv=False):
+    info = LoadInfo()
+    allow = (ENOCONV,) if allow_noconv else ()
+    st = load().pff_load_step(h, _ptr(U), _ptr(phi_prev), float(pressure), int(max_newton), ctypes.byref(info))
+    _check(h, st, "pff_load_step", allow)
     return info
 
 

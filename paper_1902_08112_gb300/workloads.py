@@ -135,9 +135,10 @@ def batch_instances(count: int = 256, sizes=(16, 24, 32, 48, 64), seed: int = SE
     return out
 
 
-def small(w: Workload, n: int, n_levels: int | None = None) -> Workload:
-    """Same recipe on an n^dim mesh (eps follows the new h)."""
-    v = replace(w, n_cells=(n,) * w.dim, n_levels=n_levels or w.n_levels, eps=0.0)
+def small(w: Workload, n, n_levels: int | None = None) -> Workload:
+    """Same recipe on an n^dim mesh, or n = cells per axis (eps follows the new h)."""
+    cells = (n,) * w.dim if isinstance(n, int) else tuple(int(c) for c in n)
+    v = replace(w, n_cells=cells, n_levels=n_levels or w.n_levels, eps=0.0)
     return v.finalize()
 
 

@@ -197,3 +197,19 @@ def test_row_sampler_matches_assembly(dim, deg):
     rows = np.arange(0, m.n_dofs, 5)
     np.testing.assert_allclose(fem.apply_rows(m, ph, U, ptil, mask, x, rows), (G @ x)[rows],
                                rtol=1e-13, atol=1e-13 * np.abs(G @ x).max())
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (3, 1), (3, 2)])
+def test_energy_parts_add_up_and_match_closed_forms(dim, deg):
+    """Bulk + crack = total energy; crack energy of a constant phase field c is
+    Gc/2 (1-c)^2/eps |D| and its bulk energy is 0 for u = 0 (Sec. 5 energies)."""
+    m = _mesh(dim, deg, 2)
+    ph = fem.Phys(E=1.3, nu=0.25, p=0.2, eps=0.4, Gc=1.7, kappa=1e-3)
+    U = _rand_state(m, 12)
+    b, c = fem.energy_parts(m, ph, U)
+    assert b + c == pytest.approx(fem.energy(m, ph, U), rel=1e-13)
+    cval = 0.4
+    U0 = np.concatenate([np.zeros(dim * m.n_nodes), np.full(m.n_nodes, cval)])
+    b0, c0 = fem.energy_parts(m, ph, U0)
+    assert b0 == 0.0
+    assert c0 == pytest.approx(0.5 * ph.Gc * (1 - cval) ** 2 / ph.eps * 2.0 ** dim, rel=1e-13)

@@ -247,3 +247,37 @@ def test_active_set_complementarity_at_convergence():
     np.testing.assert_allclose(phi[act], po[act], atol=1e-9)
     assert (lam[act] >= -1e-8).all()
     assert np.abs(lam[~act]).max() <= 1e-6
+
+
+def test_extrapolation_special_values():
+    """phi~ of Sec. 2.3: linear in time and clamped to [0, 1]; phi^{n-1} without a phi^{n-2}."""
+    a = np.array([1.0, 0.5, 0.25, 0.375, 0.0, 0.75])
+    b = np.array([1.0, 0.75, 0.875, 0.125, 0.0, 0.25])
+    assert np.array_equal(pdas.extrapolate(a, b), np.array([1.0, 0.25, 0.0, 0.625, 0.0, 1.0]))
+    assert np.array_equal(pdas.extrapolate(a, None), a)
+    assert np.array_equal(pdas.extrapolate(a, a), a)
+
+
+def test_load_stepping_converges_and_is_irreversible():
+    """Three load steps p_n = n p / 3: each ends by Algorithm 1's stop test, phi never grows
+    (phi^n <= phi^{n-1}, the irreversibility of Sec. 2.1), and the converged state satisfies the
+    free rows of A(U^n) = 0 evaluated with the extrapolated phi~ of its own step."""
+    w = W.small(W.config_2d_single_crack(), 16, 2)
+    m = fem.Mesh(2, 1, w.n_cells, w.lo, w.hi)
+    dmask = fem.dirichlet_face_mask(m, 0x3F)
+    U, _, _ = W.initial_state(w)
+    nn = m.n_nodes
+    prev_phi, prev_act = None, None
+    for n in (1, 2, 3):
+        ph = fem.Phys(eps=w.eps, p=w.pressure * 50 * n / 3, kappa=w.kappa)
+        phi_nm1 = U[2 * nn:].copy()
+        ptil = pdas.extrapolate(phi_nm1, prev_phi)
+        U, infos = pdas.load_step(m, ph, 2, U, prev_phi, dmask, prev_act, rtol=1e-12)
+        assert infos[-1].converged
+        phi = U[2 * nn:]
+        assert np.all(phi <= phi_nm1 + 1e-10)
+        act = infos[-1].active
+        R = -fem.residual_A(m, ph, U, ptil)
+        free = ~fem.constrained_dofs(m, dmask | np.where(act, fem.BIT_ACTIVE, 0).astype(np.uint8))
+        assert np.abs(R[free]).max() <= 1e-8 * max(np.abs(R).max(), 1e-30) + 1e-12
+        prev_phi, prev_act = phi_nm1, act
