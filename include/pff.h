@@ -89,7 +89,11 @@ typedef struct {
  *  cheb_safety, cheb_ratio  smoothing range [ratio*safety*l, safety*l] (1.2 and 1/5).
  *  coarse_rtol, coarse_maxit  Chebyshev coarse solver: steps from the Chebyshev error bound
  *                 for this reduction, capped (Sec. 3.2.2 gives neither).
- *  seed           seed of the SplitMix64 start vector of the CG eigenvalue estimate. */
+ *  seed           seed of the SplitMix64 start vector of the CG eigenvalue estimate.
+ *  preconditioner 0: P_full = MG(G~), the monolithic V-cycle (Sec. 3.3, default);
+ *                 1: P_diag = blockdiag(MG(U~), MG(P~)) (Sec. 3.3): the coupling G_phiu is
+ *                 left out of every V-cycle residual and of the coarse solve.  Batches
+ *                 (pff_batch_*) require 0. */
 typedef struct {
     double E, nu, Gc, kappa, eps, pressure;
     double c_as, tol_as;
@@ -102,6 +106,7 @@ typedef struct {
     double coarse_rtol;
     int coarse_maxit;
     uint64_t seed;
+    int preconditioner;
 } pff_params;
 
 typedef struct {
@@ -120,7 +125,8 @@ typedef struct {
 } pff_newton_info;
 
 /* Fill *p with the defaults quoted above (E=1, nu=0.2, Gc=1, kappa=1e-10, eps=1, p=1e-3,
- * c=100, eps_as=1e-10, f=1, FP32 V-cycle, degree 4, 10 CG steps, 1.2, 0.2, 1e-6, 200, 12345). */
+ * c=100, eps_as=1e-10, f=1, FP32 V-cycle, degree 4, 10 CG steps, 1.2, 0.2, 1e-6, 200, 12345,
+ * P_full). */
 void pff_default_params(pff_params* p);
 
 /* Create the level hierarchy (Sec. 3.2 and 4.2) on the current CUDA device.  cuda_stream is a
@@ -143,6 +149,14 @@ pff_status pff_level_info(const pff_hierarchy* h, int level, int64_t* n_nodes, i
 
 /* Replace the parameters used by later calls (same mesh).  Marks the preconditioner stale. */
 pff_status pff_set_params(pff_hierarchy* h, const pff_params* params);
+
+/* Spatially varying Young's modulus (Sec. 5.2 computes with a heterogeneous E): E = s_K E on
+ * every fine cell K, i.e. mu and lambda of the cell scaled by s_K in the residual, the Jacobian,
+ * the diagonal and the energies.  escale: device FP64 array of the finest level's n_cells
+ * (cells lexicographic, x fastest), copied; NULL restores a uniform modulus.  Coarse levels
+ * take on each cell the mean of its 2^d children.  Errors: PFF_EINVAL if a factor is not finite
+ * and positive; PFF_ENOMEM.  Synchronises. */
+pff_status pff_set_modulus(pff_hierarchy* h, const double* escale);
 
 /* Kernel variant of the level operators: 0 (default) = Q1 fast path (Gauss-point linearisation
  * data precomputed in FP64 per state; FP64-accurate operators evaluated in double-float
@@ -181,6 +195,13 @@ pff_status pff_residual(pff_hierarchy* h, double* R);
  * int Gc/2 ((1 - phi)^2 / eps + eps |grad phi|^2) of Sec. 5 (no stress split) at the current fine
  * state, FP64, Q1 meshes.  out (host): [bulk, crack].  Synchronises. */
 pff_status pff_energies(pff_hierarchy* h, double out[2]);
+
+/* Boundary load of Sec. 5, L_c = int_Gamma (sigma n)_c ds over one face of the box, evaluated as
+ * the reaction: the sum over the fine nodes on that face of A(U)(phi_i e_c) (Eq. (semilinear),
+ * current state, no elimination), which equals the traction integral for the discrete solution.
+ * face: 2a = lower face of axis a, 2a+1 = upper face; component c < dim.  out: host.
+ * Synchronises.  Errors: PFF_EINVAL (face, component), PFF_ESTATE (no state). */
+pff_status pff_boundary_load(pff_hierarchy* h, int face, int component, double* out);
 
 /* Matrix-free Jacobian apply y = G~_l(U_l) x on a level (Sec. 4.1, 4.2), FP64: the level's
  * operator at its restricted state, eliminated rows give y = x, eliminated columns are
@@ -266,7 +287,7 @@ pff_status pff_load_step(pff_hierarchy* h, double* U, const double* phi_prev, do
 
 /* ---- Batches of independent instances (one launch per level and operation across instances).
  * A batch is a view over n existing hierarchies created on the same stream, all Q1 with the same
- * dimension, mg_precision 32 and cheb_degree; instances may differ in mesh size, number of levels
+ * dimension, mg_precision 32, preconditioner 0 and cheb_degree; instances may differ in mesh size, number of levels
  * and physical parameters.  The batch owns only descriptor tables and reduction scratch; the
  * hierarchies keep their data (a hierarchy may belong to several batches, but batches that share a
  * hierarchy must not run concurrently).  Per-instance results equal those of the single-instance

@@ -43,7 +43,7 @@ class _Mesh(ctypes.Structure):
 class _Phys(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("lam", ctypes.c_double), ("Gc", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_double),
-                ("f", ctypes.c_double)]
+                ("f", ctypes.c_double), ("escale", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -140,11 +140,17 @@ class Phys:
     eps: float = 1.0
     p: float = 1e-3
     f: float = 1.0            # factor on the phi-equation elastic term (1 = energy consistent)
+    escale: np.ndarray | None = None   # per cell factor on E (n_cells, x fastest), None = uniform
     extra: dict = field(default_factory=dict)
 
     def c(self) -> _Phys:
         mu, lam = lame(self.E, self.nu)
-        return _Phys(mu, lam, self.Gc, self.kappa, self.eps, self.p, self.f)
+        ph = _Phys(mu, lam, self.Gc, self.kappa, self.eps, self.p, self.f, None)
+        if self.escale is not None:
+            arr = np.ascontiguousarray(self.escale, dtype=np.float64)
+            ph.escale = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            ph._keep = arr          # the C side reads the array during the call
+        return ph
 
 
 def _dp(a):
@@ -185,6 +191,21 @@ def energy_parts(mesh: Mesh, phys: Phys, U) -> tuple:
     m, ph = mesh.c(), phys.c()
     lib().om_energy_parts(ctypes.byref(m), ctypes.byref(ph), _dp(U), _dp(out))
     return float(out[0]), float(out[1])
+
+
+def face_nodes(mesh: Mesh, face: int) -> np.ndarray:
+    """Indices of the nodes on one face of the box (face 2a: lower, 2a+1: upper face of axis a)."""
+    npa = mesh.nodes_per_axis()
+    idx = np.indices(npa[::-1]).reshape(mesh.dim, -1)[::-1]
+    a, side = divmod(face, 2)
+    return np.nonzero(idx[a] == (npa[a] - 1 if side else 0))[0]
+
+
+def boundary_load(mesh: Mesh, phys: Phys, U, ptil, face: int, comp: int) -> float:
+    """L_c of Sec. 5 (traction (sigma n)_c integrated over a face), taken as the reaction: the sum of
+    A(U)(phi_i e_c) over the face's nodes."""
+    A = residual_A(mesh, phys, U, ptil)
+    return float(np.sum(A[comp * mesh.n_nodes + face_nodes(mesh, face)]))
 
 
 def lumped_mass(mesh: Mesh) -> np.ndarray:

@@ -17,7 +17,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 import scipy.sparse as sp
@@ -98,12 +98,31 @@ class Level:
     P: sp.csr_matrix | None = None   # prolongation from the next coarser level
 
 
+def coarsen_cell_field(mesh: fem.Mesh, s: np.ndarray) -> np.ndarray:
+    """Per-cell field on the next coarser mesh: the mean over the 2^d fine cells of each coarse
+    cell (how a varying modulus enters the rediscretised coarse operators of Sec. 4.2)."""
+    n = mesh.n
+    a = np.asarray(s, dtype=np.float64).reshape(tuple(n[::-1]))
+    for ax in range(mesh.dim):
+        sl0 = [slice(None)] * mesh.dim
+        sl1 = [slice(None)] * mesh.dim
+        sl0[ax] = slice(0, None, 2)
+        sl1[ax] = slice(1, None, 2)
+        a = 0.5 * (a[tuple(sl0)] + a[tuple(sl1)])
+    return a.ravel()
+
+
 def build_levels(mesh: fem.Mesh, n_levels: int, phys: fem.Phys, U, ptil, mask) -> list:
     """Level 0 = coarsest, n_levels-1 = finest (the given state and mask)."""
     meshes = [mesh]
     for _ in range(n_levels - 1):
         meshes.append(meshes[-1].coarsen())
+    phys_l = [phys]
+    for l in range(n_levels - 1):
+        es = phys_l[-1].escale
+        phys_l.append(replace(phys_l[-1], escale=None if es is None else coarsen_cell_field(meshes[l], es)))
     meshes = meshes[::-1]
+    phys_l = phys_l[::-1]
     states = [None] * n_levels
     states[-1] = (np.asarray(U, dtype=np.float64), np.asarray(ptil, dtype=np.float64),
                   np.asarray(mask, dtype=np.uint8))
@@ -117,7 +136,7 @@ def build_levels(mesh: fem.Mesh, n_levels: int, phys: fem.Phys, U, ptil, mask) -
     for l in range(n_levels):
         m = meshes[l]
         Ul, pl, ml = states[l]
-        G = fem.assemble(m, phys, Ul, pl, ml)
+        G = fem.assemble(m, phys_l[l], Ul, pl, ml)
         free = ~fem.constrained_dofs(m, ml)
         dinv = 1.0 / G.diagonal()
         nn = m.n_nodes
@@ -233,6 +252,21 @@ class MGParams:
     ratio: float = 0.2
     coarse_rtol: float = 1e-6
     coarse_maxit: int = 200
+    block_diagonal: bool = False   # P_diag = blockdiag(MG(U~), MG(P~)) of Sec. 3.3 instead of P_full
+
+
+def level_operator(lev: Level, prm: MGParams):
+    """Operator of the V-cycle on a level: G~ for P_full; for P_diag its two diagonal blocks
+    (the coupling block G_phiu, rows of phi and columns of u, is left out)."""
+    if not prm.block_diagonal:
+        return lev.G
+    if getattr(lev, "_Gbd", None) is None:
+        G = lev.G.tocoo()
+        is_phi_row = np.isin(G.row, lev.pblock)
+        is_u_col = np.isin(G.col, lev.ublock)
+        keep = ~(is_phi_row & is_u_col)
+        lev._Gbd = sp.csr_matrix((G.data[keep], (G.row[keep], G.col[keep])), shape=G.shape)
+    return lev._Gbd
 
 
 def smooth_zero(lev: Level, b: np.ndarray, prm: MGParams) -> np.ndarray:
@@ -254,7 +288,7 @@ def coarse_solve(lev: Level, b: np.ndarray, prm: MGParams) -> np.ndarray:
     a, c = coarse_range(lev.lam_min[0], lev.lam_max[0])
     k = coarse_steps(a, c, prm.coarse_rtol, prm.coarse_maxit)
     x[ub] = chebyshev_zero(lev.G[ub][:, ub], lev.dinv[ub], b[ub], a, c, k)
-    rphi = b[pb] - lev.G[pb][:, ub] @ x[ub]
+    rphi = b[pb] if prm.block_diagonal else b[pb] - lev.G[pb][:, ub] @ x[ub]
     a, c = coarse_range(lev.lam_min[1], lev.lam_max[1])
     k = coarse_steps(a, c, prm.coarse_rtol, prm.coarse_maxit)
     x[pb] = chebyshev_zero(lev.G[pb][:, pb], lev.dinv[pb], rphi, a, c, k)
@@ -266,8 +300,9 @@ def vcycle(levels: list, l: int, b: np.ndarray, prm: MGParams) -> np.ndarray:
     lev = levels[l]
     if l == 0:
         return coarse_solve(lev, b, prm)
+    G = level_operator(lev, prm)
     x = smooth_zero(lev, b, prm)
-    r = b - lev.G @ x
+    r = b - G @ x
     coarse = levels[l - 1]
     rc = lev.P.T @ r
     rc[~coarse.free] = 0.0
@@ -275,12 +310,13 @@ def vcycle(levels: list, l: int, b: np.ndarray, prm: MGParams) -> np.ndarray:
     corr = lev.P @ ec
     corr[~lev.free] = 0.0
     x = x + corr
-    x = x + smooth_zero(lev, b - lev.G @ x, prm)
+    x = x + smooth_zero(lev, b - G @ x, prm)
     return x
 
 
 def precondition(levels: list, v: np.ndarray, prm: MGParams) -> np.ndarray:
-    """P_full^-1 = MG(G~) (Sec. 3.3): V-cycle on the free DoFs, identity on eliminated ones."""
+    """P_full^-1 = MG(G~), or P_diag^-1 with prm.block_diagonal (Sec. 3.3): V-cycle on the free
+    DoFs, identity on eliminated ones."""
     fine = levels[-1]
     b = np.where(fine.free, v, 0.0)
     z = vcycle(levels, len(levels) - 1, b, prm)

@@ -16,7 +16,9 @@
  *     zero columns,
  *   - the energy functional whose first variation is the residual (Sec. 5, bulk + crack
  *     energy), used only as a finite-difference pin,
- *   - the Gauss-Lobatto lumped mass of the remark after Algorithm 1.
+ *   - the Gauss-Lobatto lumped mass of the remark after Algorithm 1,
+ *   - optionally a Young's modulus that varies per cell (E = s_cell E_0, Sec. 5.2 uses a
+ *     spatially varying E): mu and lambda of a cell are scaled by s_cell.
  *
  * Notation: d = dim, comps 0..d-1 = displacement u, comp d = phase field phi.
  * DoF index = comp * n_nodes + node, node lexicographic with x fastest.
@@ -38,7 +40,17 @@ typedef struct {
     double mu, lam;    /* Lame coefficients */
     double Gc, kappa, eps, p;
     double f;          /* factor on the phi-equation elastic term: 1 = energy consistent */
+    const double *escale;  /* per cell factor on mu and lam (n_cells), NULL = uniform */
 } om_phys;
+
+/* The physics of one cell: mu and lam scaled by the cell's modulus factor. */
+static const om_phys *cell_phys(const om_phys *ph, int64_t cell, om_phys *tmp) {
+    if (!ph->escale) return ph;
+    *tmp = *ph;
+    tmp->mu *= ph->escale[cell];
+    tmp->lam *= ph->escale[cell];
+    return tmp;
+}
 
 #define MAXN 27        /* nodes per cell, Q2 in 3D */
 #define MAXQ 27        /* quadrature points per cell */
@@ -389,7 +401,8 @@ void om_residual(const om_mesh *m, const om_phys *ph, const double *U, const dou
     int64_t nodes[MAXN];
     for (int64_t cell = 0; cell < ncell; ++cell) {
         int nl = cell_nodes(m, cell, nodes);
-        element_residual(m, ph, qd, nodes, nn, U, ptil, Re);
+        om_phys pc;
+        element_residual(m, cell_phys(ph, cell, &pc), qd, nodes, nn, U, ptil, Re);
         for (int n = 0; n < nl; ++n)
             for (int c = 0; c < nc; ++c) A[c * nn + nodes[n]] += Re[n * nc + c];
     }
@@ -411,7 +424,8 @@ void om_energy_parts(const om_mesh *m, const om_phys *ph, const double *U, doubl
     out[1] = 0.0;
     for (int64_t cell = 0; cell < ncell; ++cell) {
         cell_nodes(m, cell, nodes);
-        out[0] += element_energy(m, &bulk, qd, nodes, nn, U);
+        om_phys pc;
+        out[0] += element_energy(m, cell_phys(&bulk, cell, &pc), qd, nodes, nn, U);
         out[1] += element_energy(m, &crack, qd, nodes, nn, U);
     }
     free(qd);
@@ -425,7 +439,8 @@ double om_energy(const om_mesh *m, const om_phys *ph, const double *U) {
     double E = 0.0;
     for (int64_t cell = 0; cell < ncell; ++cell) {
         cell_nodes(m, cell, nodes);
-        E += element_energy(m, ph, qd, nodes, nn, U);
+        om_phys pc;
+        E += element_energy(m, cell_phys(ph, cell, &pc), qd, nodes, nn, U);
     }
     free(qd);
     return E;
@@ -535,7 +550,8 @@ void om_assemble(const om_mesh *m, const om_phys *ph, const double *U, const dou
     int64_t nodes[MAXN];
     for (int64_t cell = 0; cell < ncell; ++cell) {
         cell_nodes(m, cell, nodes);
-        element_jacobian(m, ph, qd, nodes, nn, U, ptil, Ke);
+        om_phys pc;
+        element_jacobian(m, cell_phys(ph, cell, &pc), qd, nodes, nn, U, ptil, Ke);
         for (int ni = 0; ni < nl; ++ni) {
             om_box b;
             row_box(m, nodes[ni], &b);
@@ -602,7 +618,8 @@ void om_apply_rows(const om_mesh *m, const om_phys *ph, const double *U, const d
                     int li = -1;
                     for (int n = 0; n < nl; ++n) if (nodes[n] == node) li = n;
                     if (li < 0) continue;
-                    element_jacobian(m, ph, qd, nodes, nn, U, ptil, Ke);
+                    om_phys pc;
+                    element_jacobian(m, cell_phys(ph, cell, &pc), qd, nodes, nn, U, ptil, Ke);
                     for (int nj = 0; nj < nl; ++nj)
                         for (int cj2 = 0; cj2 < nc; ++cj2) {
                             if (is_constrained(d, mask[nodes[nj]], cj2, phi_bits)) continue;

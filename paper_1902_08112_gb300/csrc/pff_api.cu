@@ -45,6 +45,7 @@ extern "C" void pff_default_params(pff_params* p) {
     p->coarse_rtol = 1e-6;
     p->coarse_maxit = 200;
     p->seed = 12345;
+    p->preconditioner = 0;
 }
 
 // Gauss-Legendre rule with deg+1 points mapped to [0,1] and the Lagrange basis on the
@@ -106,6 +107,7 @@ static const char* check_params(const pff_params* p) {
     if (p->cg_steps < 1 || p->cg_steps > 50) return "cg_steps must be in [1, 50]";
     if (!(p->cheb_safety > 0) || !(p->cheb_ratio > 0 && p->cheb_ratio < 1)) return "need cheb_safety > 0, 0 < cheb_ratio < 1";
     if (!(p->coarse_rtol > 0 && p->coarse_rtol < 1) || p->coarse_maxit < 1) return "need 0 < coarse_rtol < 1, coarse_maxit >= 1";
+    if (p->preconditioner != 0 && p->preconditioner != 1) return "preconditioner must be 0 (P_full) or 1 (P_diag)";
     return nullptr;
 }
 
@@ -155,6 +157,7 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
         Geom& g = L.g;
         g.dim = mesh->dim;
         g.deg = mesh->degree;
+        g.es = nullptr;
         const int f = 1 << (h->L - 1 - l);
         g.n_nodes = 1;
         g.n_cells = 1;
@@ -305,6 +308,33 @@ extern "C" pff_status pff_set_params(pff_hierarchy* h, const pff_params* params)
     return PFF_OK;
 }
 
+extern "C" pff_status pff_set_modulus(pff_hierarchy* h, const double* escale) {
+    if (!h) return PFF_EINVAL;
+    drop_graph(h);
+    h->stale = true;
+    if (!escale) {
+        for (auto& L : h->lv) L.g.es = nullptr;
+    } else {
+        Level& F = h->lv[h->L - 1];
+        CUDA_OR_FAIL(h, cudaMemsetAsync(h->d_counts, 0, sizeof(int), h->stream));
+        CUDA_OR_FAIL(h, launch_count_nonpositive(F.g.n_cells, escale, h->d_counts, h->stream));
+        int bad = 0;
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(&bad, h->d_counts, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+        REQUIRE(h, bad == 0, PFF_EINVAL, "pff_set_modulus: factors must be finite and > 0");
+        for (auto& L : h->lv)
+            if (!L.es_buf) CUDA_OR_FAIL(h, dalloc(h, &L.es_buf, (size_t)L.g.n_cells));
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(F.es_buf, escale, sizeof(double) * F.g.n_cells, cudaMemcpyDeviceToDevice,
+                                        h->stream));
+        for (int l = h->L - 2; l >= 0; --l)
+            CUDA_OR_FAIL(h, launch_coarsen_cells(h->lv[l].g, h->lv[l + 1].g, h->lv[l + 1].es_buf, h->lv[l].es_buf,
+                                                 h->stream));
+        for (auto& L : h->lv) L.g.es = L.es_buf;
+    }
+    if (h->has_state) CUDA_OR_FAIL(h, propagate_state(h));
+    return PFF_OK;
+}
+
 extern "C" pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant) {
     if (!h) return PFF_EINVAL;
     REQUIRE(h, variant >= 0 && variant <= 3, PFF_EINVAL, "variant must be 0, 1, 2 or 3");
@@ -334,7 +364,7 @@ extern "C" pff_status pff_set_active_set(pff_hierarchy* h, const uint8_t* active
     REQUIRE(h, active, PFF_EINVAL, "pff_set_active_set: NULL");
     Level& F = h->lv[h->L - 1];
     CUDA_OR_FAIL(h, launch_set_active(F.g, active, F.mask, h->stream));
-    CUDA_OR_FAIL(h, propagate_state(h));
+    CUDA_OR_FAIL(h, propagate_state(h, false));
     h->active_known = true;
     return PFF_OK;
 }
@@ -358,7 +388,7 @@ static pff_status update_active(pff_hierarchy* h, int* n_active, int* n_changed)
     CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
     if (!h->active_known) cnt[1] = cnt[0];
     h->active_known = true;
-    CUDA_OR_FAIL(h, propagate_state(h));
+    CUDA_OR_FAIL(h, propagate_state(h, false));
     if (n_active) *n_active = cnt[0];
     if (n_changed) *n_changed = cnt[1];
     return PFF_OK;
@@ -378,6 +408,22 @@ extern "C" pff_status pff_energies(pff_hierarchy* h, double out[2]) {
     CUDA_OR_FAIL(h, launch_q1_energies(F.g, h->ph, F.U64, h->d_scratch, h->d_scal + 400, h->stream));
     CUDA_OR_FAIL(h, cudaMemcpyAsync(out, h->d_scal + 400, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_boundary_load(pff_hierarchy* h, int face, int component, double* out) {
+    if (!h || !out) return PFF_EINVAL;
+    REQUIRE(h, h->has_state, PFF_ESTATE, "pff_boundary_load before pff_set_state");
+    Level& F = h->lv[h->L - 1];
+    REQUIRE(h, face >= 0 && face < 2 * F.g.dim, PFF_EINVAL, "pff_boundary_load: face out of range");
+    REQUIRE(h, component >= 0 && component < F.g.dim, PFF_EINVAL, "pff_boundary_load: component out of range");
+    double* R = h->tmp64[3];
+    CUDA_OR_FAIL(h, residual_fine(h, R));
+    CUDA_OR_FAIL(h, launch_face_sum(F.g, face / 2, face % 2, component, R, h->d_scal + 402, h->stream));
+    double v = 0.0;
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(&v, h->d_scal + 402, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    *out = -v;    // R = -A(U): the load is the sum of A(U)(phi_i e_c) over the face nodes
     return PFF_OK;
 }
 
@@ -706,6 +752,7 @@ cudaError_t count_launch(cudaError_t e) {
     return e;
 }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace pff
 
 extern "C" long long pff_launch_count(void) { return pff::launch_count(); }

@@ -628,7 +628,7 @@ extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int rest
         if (!hs[i]) return PFF_EINVAL;
         if (hs[i]->mesh.degree != 1 || hs[i]->mesh.dim != hs[0]->mesh.dim) return PFF_EINVAL;
         if (hs[i]->stream != hs[0]->stream) return PFF_EINVAL;
-        if (hs[i]->prm.mg_precision != 32 || hs[i]->prm.cheb_degree != hs[0]->prm.cheb_degree) return PFF_EINVAL;
+        if (hs[i]->prm.mg_precision != 32 || hs[i]->prm.preconditioner != 0 || hs[i]->prm.cheb_degree != hs[0]->prm.cheb_degree) return PFF_EINVAL;
         if (!hs[i]->fast_q1) return PFF_EINVAL;
     }
     pff_batch* b = new (std::nothrow) pff_batch();

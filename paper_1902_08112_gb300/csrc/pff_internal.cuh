@@ -36,6 +36,7 @@ struct Geom {
     int nn[3];           // nodes per axis (1 beyond dim)
     int64_t n_nodes, n_cells;
     double h[3];         // cell edge lengths (1 beyond dim)
+    const double* es;    // per-cell factor on E (n_cells, device), nullptr = uniform modulus
 };
 
 __host__ __device__ inline int64_t n_dofs(const Geom& g) { return (int64_t)(g.dim + 1) * g.n_nodes; }
@@ -53,6 +54,7 @@ struct Level {
     void* w[2][6] = {{nullptr}}; // V-cycle work vectors, [0]=FP32, [1]=FP64
     float* qpd32 = nullptr;      // Q1: Gauss-point linearisation coefficients, FP32
     float2* qpd64 = nullptr;     // Q1: the same as df64 pairs (hi, lo)
+    double* es_buf = nullptr;    // storage of g.es once a varying modulus is set
     double lam_min[2] = {1, 1};  // eigenvalue estimates of D^-1 G_bb, blocks u / phi
     double lam_max[2] = {1, 1};
 };
@@ -147,6 +149,10 @@ cudaError_t launch_active_set(const Geom& g, const double* R, const double* M, c
                               int* counts, cudaStream_t s);
 cudaError_t launch_newton_rhs(const Geom& g, const double* R, const double* t, const double* U,
                               const double* phi_old, const uint8_t* mask, double* Rt, cudaStream_t s);
+cudaError_t launch_coarsen_cells(const Geom& gc, const Geom& gf, const double* sf, double* sc, cudaStream_t s);
+cudaError_t launch_count_nonpositive(int64_t n, const double* v, int* bad, cudaStream_t s);
+cudaError_t launch_face_sum(const Geom& g, int axis, int side, int comp, const double* R, double* out,
+                            cudaStream_t s);
 cudaError_t launch_extrapolate(int64_t n, const double* phi_nm1, const double* phi_nm2, double* out,
                                cudaStream_t s);
 cudaError_t launch_active_delta(const Geom& g, const double* U, const double* phi_old,
@@ -211,4 +217,5 @@ namespace pff {
 // pff_launch_count).  Each launcher passes its cudaGetLastError() result through here.
 cudaError_t count_launch(cudaError_t e);
 long long launch_count();
+void add_launches(long long n);   // graph replays add their node count; a capture takes its own back
 }  // namespace pff

@@ -96,7 +96,9 @@ k_cell(CellArgs<T> a) {
         const int li = cell % C::TX, lj = (cell / C::TX) % C::TY, lk = cell / (C::TX * C::TY);
         const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
         if (valid) {
-            const T mu = T(a.ph.mu), lam = T(a.ph.lam), kap = T(a.ph.kappa), p = T(a.ph.p);
+            const double sE = g.es ? g.es[(int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) +
+                                                    (int64_t)g.nc[1] * (ck0 + lk))] : 1.0;
+            const T mu = T(a.ph.mu * sE), lam = T(a.ph.lam * sE), kap = T(a.ph.kappa), p = T(a.ph.p);
             const T Gc = T(a.ph.Gc), eps = T(a.ph.eps), ff = T(a.ph.f);
             const T one = T(1), two = T(2), half = T(0.5);
             T ih[3], vol = T(1);

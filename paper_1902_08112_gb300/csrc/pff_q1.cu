@@ -95,6 +95,8 @@ __global__ void k_q1_linearize(Geom g, Phys ph, const double* __restrict__ U, co
             const int i = ci[0] + (n & 1), j = ci[1] + ((n >> 1) & 1), k = DIM == 3 ? ci[2] + ((n >> 2) & 1) : 0;
             node[n] = (int64_t)i + (int64_t)g.nn[0] * ((int64_t)j + (int64_t)g.nn[1] * k);
         }
+        const double sE = g.es ? g.es[cell] : 1.0;
+        const double cmu = ph.mu * sE, clam = ph.lam * sE;
         double mu_[DIM][NV], mphi[NV], mpt[NV];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
@@ -138,16 +140,16 @@ __global__ void k_q1_linearize(Geom g, Phys ph, const double* __restrict__ U, co
             for (int i = 0; i < DIM; ++i)
 #pragma unroll
                 for (int j = 0; j < DIM; ++j) ee += e[i][j] * e[i][j];
-            const double Es = 0.5 * ph.lam * tr * tr + ph.mu * ee;
+            const double Es = 0.5 * clam * tr * tr + cmu * ee;
             const double gk = (1.0 - ph.kappa) * ptv * ptv + ph.kappa;
             double vals[NK];
-            vals[0] = w * gk;
+            vals[0] = w * gk * sE;
             const double a1 = 2.0 * ph.f * (1.0 - ph.kappa) * phi, b1 = 2.0 * ph.p * phi;
 #pragma unroll
             for (int i = 0; i < DIM; ++i)
 #pragma unroll
                 for (int j = i; j < DIM; ++j) {
-                    const double sig = 2.0 * ph.mu * e[i][j] + (i == j ? ph.lam * tr : 0.0);
+                    const double sig = 2.0 * cmu * e[i][j] + (i == j ? clam * tr : 0.0);
                     vals[1 + sidx<DIM>(i, j)] = w * (a1 * sig + (i == j ? b1 : 0.0));
                 }
             vals[NK - 1] = w * (2.0 * ph.f * (1.0 - ph.kappa) * Es + 2.0 * ph.p * tr + ph.Gc / ph.eps);
@@ -957,6 +959,8 @@ k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __rest
                 }
             }
         } else {
+            const double sE = g.es ? g.es[gid] : 1.0;
+            const double cmu = ph.mu * sE, clam = ph.lam * sE;
             const int tb = li + NTX * (lj + NTY * lk);
             double m_[NC + 1][NV];
 #pragma unroll
@@ -1010,7 +1014,7 @@ k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __rest
                 for (int i = 0; i < DIM; ++i)
 #pragma unroll
                     for (int j = 0; j < DIM; ++j) ee += e[i][j] * e[i][j];
-                const double Es = 0.5 * ph.lam * tr * tr + ph.mu * ee;
+                const double Es = 0.5 * clam * tr * tr + cmu * ee;
                 const double gk = (1.0 - ph.kappa) * ptv * ptv + ph.kappa;
                 // -A(U): u-rows g(phi~) sigma(u) + phi~^2 p I; phi-rows f g'(phi) E_s + 2 phi p div u
                 // - Gc/eps (1 - phi); gradient part Gc eps grad phi
@@ -1019,7 +1023,7 @@ k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __rest
                 for (int i = 0; i < DIM; ++i)
 #pragma unroll
                     for (int j = 0; j < DIM; ++j)
-                        fl[i][j] = -w * (gk * (2.0 * ph.mu * e[i][j] + (i == j ? ph.lam * tr : 0.0)) +
+                        fl[i][j] = -w * (gk * (2.0 * cmu * e[i][j] + (i == j ? clam * tr : 0.0)) +
                                          (i == j ? ptv * ptv * ph.p : 0.0));
 #pragma unroll
                 for (int j = 0; j < DIM; ++j) fl[DIM][j] = -w * ph.Gc * ph.eps * gphi[j];
@@ -1144,6 +1148,7 @@ __global__ void k_q1_energy(Geom g, Phys ph, const double* __restrict__ U, doubl
         int ci[3] = {0, 0, 0};
         int64_t r = cell;
         for (int a = 0; a < DIM; ++a) { ci[a] = (int)(r % g.nc[a]); r /= g.nc[a]; }
+        const double sE = g.es ? g.es[cell] : 1.0;
         double m_[DIM + 1][NV];
 #pragma unroll
         for (int n = 0; n < NV; ++n) {
@@ -1183,7 +1188,7 @@ __global__ void k_q1_energy(Geom g, Phys ph, const double* __restrict__ U, doubl
                 }
 #pragma unroll
             for (int d = 0; d < DIM; ++d) gg += gr[DIM][d] * gr[DIM][d];
-            const double Es = 0.5 * ph.lam * tr * tr + ph.mu * ee;
+            const double Es = sE * (0.5 * ph.lam * tr * tr + ph.mu * ee);
             const double gk = (1.0 - ph.kappa) * phi * phi + ph.kappa;
             eb += w * (gk * Es + phi * phi * ph.p * tr);
             ec += w * 0.5 * ph.Gc * ((1.0 - phi) * (1.0 - phi) / ph.eps + ph.eps * gg);

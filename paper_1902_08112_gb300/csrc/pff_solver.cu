@@ -131,13 +131,14 @@ cudaError_t residual_fine(pff_hierarchy* h, double* R) {
 }
 
 // Fine state -> all coarser levels (coincident nodes) and FP32 copies.
-cudaError_t propagate_state(pff_hierarchy* h) {
+cudaError_t propagate_state(pff_hierarchy* h, bool values) {
     for (int l = h->L - 2; l >= 0; --l) {
         Level& C = h->lv[l];
         Level& F = h->lv[l + 1];
         CK(launch_restrict_state(C.g, F.g, F.U64, F.pt64, F.mask, C.U64, C.pt64, C.mask, h->stream));
     }
     for (auto& L : h->lv) {
+        if (!values) break;     // only the masks changed: FP32 copies and Gauss-point data stay valid
         CK(launch_cast_f64_f32(L.U64, L.U32, n_dofs(L.g), h->stream));
         CK(launch_cast_f64_f32(L.pt64, L.pt32, L.g.n_nodes, h->stream));
         if (L.qpd64) CK(launch_q1_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
@@ -338,6 +339,9 @@ static int coarse_steps(double alpha, double beta, double rtol, int maxit) {
     return std::max(1, ki);
 }
 
+// Operator of the V-cycle residuals: G~ (P_full) or its block diagonal (P_diag, Sec. 3.3).
+static int mg_op(const pff_hierarchy* h) { return h->prm.preconditioner == 1 ? OP_APPLY_BLOCKDIAG : OP_APPLY; }
+
 // Run the recurrence on the residual r (modified in place) with the block-diagonal operator;
 // mode 1: x = correction, mode 2: x += correction.  ku/kp: steps per block (the longer block
 // keeps iterating; the other block's coefficients become zero-updates once finished).
@@ -369,7 +373,7 @@ cudaError_t smooth(pff_hierarchy* h, int l, const T* b, T* x, int zero_guess) {
         CK(cudaMemcpyAsync(r, b, sizeof(T) * nd, cudaMemcpyDeviceToDevice, h->stream));
     } else {
         T* t = work<T>(L, 4);
-        CK(apply_level<T>(h, l, OP_APPLY, x, t, PHI_BITS_ALL));
+        CK(apply_level<T>(h, l, mg_op(h), x, t, PHI_BITS_ALL));
         CK(launch_sub<T>(nd, b, t, r, h->stream));
     }
     const double sf = h->prm.cheb_safety, ra = h->prm.cheb_ratio;
@@ -381,7 +385,7 @@ template cudaError_t smooth<double>(pff_hierarchy*, int, const double*, double*,
 template cudaError_t smooth<float>(pff_hierarchy*, int, const float*, float*, int);
 
 // FP64 coarse solve on level 0: u block first, then phi block with the coupling G_phiu x_u
-// moved to the right-hand side.
+// moved to the right-hand side (P_full); both blocks at once without the coupling (P_diag).
 cudaError_t coarse_solve(pff_hierarchy* h, const double* b, double* x) {
     Level& L = h->lv[0];
     const int64_t nd = n_dofs(L.g);
@@ -396,6 +400,10 @@ cudaError_t coarse_solve(pff_hierarchy* h, const double* b, double* x) {
     ChebCoef none;
     none.c1.assign(1, 0.0);
     none.c2.assign(1, 0.0);
+    if (h->prm.preconditioner == 1) {
+        CK(cudaMemcpyAsync(r, b, sizeof(double) * nd, cudaMemcpyDeviceToDevice, h->stream));
+        return cheb_run<double>(h, 0, r, x, cu, cp, 1);
+    }
     // u block
     CK(launch_copy_block<double>(L.g, 0, b, r, h->stream));
     CK(cheb_run<double>(h, 0, r, x, cu, none, 1));
@@ -426,7 +434,7 @@ static cudaError_t vcycle_rec(pff_hierarchy* h, int l) {
     T* r = work<T>(L, 2);
     T* t = work<T>(L, 4);
     CK(smooth<T>(h, l, b, x, 1));
-    CK(apply_level<T>(h, l, OP_APPLY, x, t, PHI_BITS_ALL));
+    CK(apply_level<T>(h, l, mg_op(h), x, t, PHI_BITS_ALL));
     CK(launch_sub<T>(nd, b, t, r, h->stream));
     CK(launch_restrict<T>(C.g, L.g, r, work<T>(C, 0), C.mask, h->stream));
     CK(vcycle_rec<T>(h, l - 1));
@@ -464,6 +472,7 @@ static cudaError_t vcycle_body(pff_hierarchy* h) {
             return vcycle_rec<T>(h, h->L - 1);
         }
         h->vgraph_nodes = launch_count() - c0;
+        add_launches(-h->vgraph_nodes);       // captured kernels run only when replayed
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof_on) {
@@ -476,7 +485,7 @@ static cudaError_t vcycle_body(pff_hierarchy* h) {
         CK(cudaEventRecord(e1, h->stream));
         h->prof[PFF_PROF_VCYCLE].push_back({e0, e1});
     }
-    for (long long i = 0; i < h->vgraph_nodes; ++i) count_launch(cudaSuccess);
+    add_launches(h->vgraph_nodes);
     return cudaSuccess;
 }
 

@@ -12,7 +12,7 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
 template <typename T>
 cudaError_t diagonal_level(pff_hierarchy* h, int l, T* d);
 cudaError_t residual_fine(pff_hierarchy* h, double* R);
-cudaError_t propagate_state(pff_hierarchy* h);
+cudaError_t propagate_state(pff_hierarchy* h, bool values = true);   // values=false: masks only
 cudaError_t setup(pff_hierarchy* h);
 void drop_graph(pff_hierarchy* h);
 template <typename T>

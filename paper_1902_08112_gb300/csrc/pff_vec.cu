@@ -534,6 +534,70 @@ cudaError_t launch_active_delta(const Geom& g, const double* U, const double* ph
     return count_launch(cudaGetLastError());
 }
 
+// Sum of one component of R over the nodes of one boundary face (axis, side), one CTA of 256
+// threads, fixed summation order.  Sec. 5: L_y is the y-traction integrated over a boundary part,
+// which for the discrete solution is the sum of the residual A(U)(phi_i e_y) over the face nodes.
+__global__ void k_face_sum(Geom g, int axis, int side, int comp, const double* __restrict__ R,
+                           double* __restrict__ out) {
+    __shared__ double sm[256];
+    const int64_t nface = g.n_nodes / g.nn[axis];
+    const int b1 = axis == 0 ? 1 : 0, b2 = axis == 2 ? 1 : 2;
+    const int64_t fixed = side ? g.nn[axis] - 1 : 0;
+    const double* Rc = R + (int64_t)comp * g.n_nodes;
+    double acc = 0.0;
+    for (int64_t m = threadIdx.x; m < nface; m += blockDim.x) {
+        int64_t idx[3];
+        idx[axis] = fixed;
+        idx[b1] = m % g.nn[b1];
+        idx[b2] = m / g.nn[b1];
+        acc += Rc[idx[0] + (int64_t)g.nn[0] * (idx[1] + (int64_t)g.nn[1] * idx[2])];
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sm[0];
+}
+cudaError_t launch_face_sum(const Geom& g, int axis, int side, int comp, const double* R, double* out,
+                            cudaStream_t s) {
+    k_face_sum<<<1, 256, 0, s>>>(g, axis, side, comp, R, out);
+    return count_launch(cudaGetLastError());
+}
+
+// Per-cell modulus factor of the next coarser level: mean of the 2^d children, fixed order.
+__global__ void k_coarsen_cells(Geom gc, Geom gf, const double* __restrict__ sf, double* __restrict__ sc) {
+    GRID_STRIDE(c, gc.n_cells) {
+        const int i = (int)(c % gc.nc[0]), j = (int)((c / gc.nc[0]) % gc.nc[1]), k = (int)(c / ((int64_t)gc.nc[0] * gc.nc[1]));
+        double acc = 0.0;
+        const int kz = gc.dim == 3 ? 2 : 1;
+        for (int dk = 0; dk < kz; ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int di = 0; di < 2; ++di)
+                    acc += sf[(int64_t)(2 * i + di) + (int64_t)gf.nc[0] * ((int64_t)(2 * j + dj) + (int64_t)gf.nc[1] * (kz == 2 ? 2 * k + dk : 0))];
+        sc[c] = acc / (double)(kz * 4);
+    }
+}
+cudaError_t launch_coarsen_cells(const Geom& gc, const Geom& gf, const double* sf, double* sc, cudaStream_t s) {
+    k_coarsen_cells<<<grid_for(gc.n_cells), kThreads, 0, s>>>(gc, gf, sf, sc);
+    return count_launch(cudaGetLastError());
+}
+
+// counts entries that are not finite and positive
+__global__ void k_count_nonpositive(int64_t n, const double* __restrict__ v, int* __restrict__ bad) {
+    int local = 0;
+    GRID_STRIDE(i, n) {
+        const double x = v[i];
+        if (!(x > 0.0) || !isfinite(x)) ++local;
+    }
+    if (local) atomicAdd(bad, local);
+}
+cudaError_t launch_count_nonpositive(int64_t n, const double* v, int* bad, cudaStream_t s) {
+    k_count_nonpositive<<<grid_for(n), kThreads, 0, s>>>(n, v, bad);
+    return count_launch(cudaGetLastError());
+}
+
 // time-lagged phi~ of Sec. 2.3: clamp(2 phi^{n-1} - phi^{n-2}, 0, 1); phi^{n-1} without phi^{n-2}
 __global__ void k_extrapolate(int64_t n, const double* __restrict__ p1, const double* __restrict__ p2,
                               double* __restrict__ out) {

@@ -31,7 +31,7 @@ class Params(ctypes.Structure):
                 ("phi_elastic_factor", ctypes.c_double), ("mg_precision", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("cg_steps", ctypes.c_int), ("cheb_safety", ctypes.c_double),
                 ("cheb_ratio", ctypes.c_double), ("coarse_rtol", ctypes.c_double),
-                ("coarse_maxit", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("coarse_maxit", ctypes.c_int), ("seed", ctypes.c_uint64), ("preconditioner", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -49,6 +49,8 @@ class LoadInfo(ctypes.Structure):
                 ("last", NewtonInfo)]
 
 
+PRECOND_FULL, PRECOND_DIAG = 0, 1
+
 # C signatures: name -> (restype, argtypes)
 _VP, _I, _D, _I64P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
@@ -58,6 +60,7 @@ SIGNATURES = {
     "pff_hierarchy_bytes": (ctypes.c_int64, [ctypes.POINTER(Mesh), _I]),
     "pff_level_info": (_I, [_VP, _I, _I64P, _I64P, ctypes.POINTER(ctypes.c_int)]),
     "pff_set_params": (_I, [_VP, ctypes.POINTER(Params)]),
+    "pff_set_modulus": (_I, [_VP, _VP]),
     "pff_set_kernel_variant": (_I, [_VP, _I]),
     "pff_set_state": (_I, [_VP, _VP, _VP, _VP]),
     "pff_set_active_set": (_I, [_VP, _VP]),
@@ -65,6 +68,7 @@ SIGNATURES = {
     "pff_update_active_set": (_I, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pff_residual": (_I, [_VP, _VP]),
     "pff_energies": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "pff_boundary_load": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "pff_apply_jacobian": (_I, [_VP, _I, _VP, _VP]),
     "pff_apply_jacobian_f32": (_I, [_VP, _I, _VP, _VP]),
     "pff_diagonal": (_I, [_VP, _I, _I, _VP]),
@@ -214,6 +218,16 @@ def energies(h):
     out = (ctypes.c_double * 2)()
     _check(h, load().pff_energies(h, out), "pff_energies")
     return out[0], out[1]
+
+
+def boundary_load(h, face: int, component: int) -> float:
+    out = ctypes.c_double()
+    _check(h, load().pff_boundary_load(h, int(face), int(component), ctypes.byref(out)), "pff_boundary_load")
+    return out.value
+
+
+def set_modulus(h, escale):
+    return _check(h, load().pff_set_modulus(h, _ptr(escale)), "pff_set_modulus")
 
 
 def residual(h, R):

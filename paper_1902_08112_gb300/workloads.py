@@ -31,6 +31,7 @@ class Crack:
     center: tuple
     normal: tuple
     radius: float          # half length in 2D, disk radius in 3D
+    half_width: float = 1.0    # half thickness of the crack region in units of h
 
 
 @dataclass
@@ -86,6 +87,18 @@ class Workload:
 def config_2d_single_crack(n: int = 64, n_levels: int = 3, deg: int = 1) -> Workload:
     w = Workload("2d_single_crack", 2, deg, (n, n), n_levels, (-10.0, -10.0), (10.0, 10.0))
     w.cracks = [Crack((0.0, 0.0), (0.0, 1.0), 1.0)]
+    return w.finalize()
+
+
+def config_2d_two_cracks(n: int = 128, n_levels: int = 4, deg: int = 1) -> Workload:
+    """Sec. 5.1 (multiple fractures): (0,4)^2, a vertical crack {|x-2.5| <= h/2, 0.8 <= y <= 1.5}
+    and a horizontal one {0.5 <= x <= 1.5, |y-3| <= h/2}, E=1e4, nu=0.2, Gc=1, kappa=1e-10,
+    eps=h, pressure p(t) = 1e3 t with dt = 1e-2 (p_n = 10 n).  128^2 cells give h = 0.044,
+    the eps of the paper's parameter table."""
+    w = Workload("2d_two_cracks", 2, deg, (n, n), n_levels, (0.0, 0.0), (4.0, 4.0), E=1e4, nu=0.2, Gc=1.0,
+                 kappa=1e-10, pressure=10.0, eps_factor=1.0)
+    w.cracks = [Crack((2.5, 1.15), (1.0, 0.0), 0.35, half_width=0.5),
+                Crack((1.0, 3.0), (0.0, 1.0), 0.5, half_width=0.5)]
     return w.finalize()
 
 
@@ -146,8 +159,10 @@ def small(w: Workload, n, n_levels: int | None = None) -> Workload:
 
 def _cell_meets_crack(lo: np.ndarray, hi: np.ndarray, crack: Crack, h: float, dim: int) -> np.ndarray:
     """Vectorised test whether axis-aligned cells [lo, hi] meet the closed crack region
-    {|n.(x-c)| <= h, |x - c - (n.(x-c)) n| <= r}.  Exact for axis-aligned normals (interval
-    overlap plus nearest-point distance); otherwise sampled on a 5^dim lattice per cell."""
+    {|n.(x-c)| <= b h, |x - c - (n.(x-c)) n| <= r} (b = crack.half_width).  Exact for axis-aligned
+    normals (interval overlap plus nearest-point distance); otherwise sampled on a 5^dim lattice
+    per cell."""
+    h = crack.half_width * h
     c = np.asarray(crack.center[:dim], dtype=np.float64)
     nv = np.asarray(crack.normal[:dim], dtype=np.float64)
     nv = nv / np.linalg.norm(nv)
@@ -236,6 +251,34 @@ def random_state(w: Workload, seed: int | None = None):
     phi = rng.uniform(0.05, 1.0, w.n_nodes)
     ptil = np.clip(phi + 0.05 * rng.standard_normal(w.n_nodes), 0.0, 1.0)
     return np.concatenate([u, phi]), phi.copy(), ptil
+
+
+def modulus_field(w: Workload, lattice: int = 6, lo: float = 0.1, hi: float = 1.0,
+                  seed: int | None = None) -> np.ndarray:
+    """Smooth deterministic per-cell factor on E in [lo, hi] (value noise): seeded uniform values
+    on a (lattice+1)^dim grid spanning the box, blended with the smoothstep 3t^2 - 2t^3 and
+    sampled at the cell centres.  Returns n_cells values, cells lexicographic (x fastest)."""
+    rng = np.random.default_rng(w.seed + 77 if seed is None else seed)
+    vals = rng.uniform(lo, hi, size=(lattice + 1,) * w.dim)
+    centres = []
+    for a in range(w.dim):
+        t = (np.arange(w.n_cells[a]) + 0.5) / w.n_cells[a] * lattice
+        i0 = np.minimum(np.floor(t).astype(int), lattice - 1)
+        f = t - i0
+        centres.append((i0, f * f * (3.0 - 2.0 * f)))
+    grids = np.meshgrid(*[np.arange(w.n_cells[a]) for a in range(w.dim)][::-1], indexing="ij")[::-1]
+    out = np.zeros(grids[0].shape)
+    for corner in np.ndindex(*([2] * w.dim)):
+        wgt = np.ones(grids[0].shape)
+        idx = []
+        for a in range(w.dim):
+            i0, s_ = centres[a]
+            ia = i0[grids[a]]
+            sa = s_[grids[a]]
+            wgt = wgt * (sa if corner[a] else 1.0 - sa)
+            idx.append(ia + corner[a])
+        out += wgt * vals[tuple(idx)]
+    return out.ravel()
 
 
 def random_vector(n: int, seed: int = SEED) -> np.ndarray:

@@ -12,17 +12,19 @@ from paper_1902_08112_gb300 import pff, workloads as W  # noqa: E402
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
+# workload, final pressure of the three steps
 CASES = {
-    "2d_q1_64": lambda: W.config_2d_single_crack(),
-    "3d_q1_16": lambda: W.small(W.config_3d_penny(), 16, 3),
+    "2d_q1_64": (lambda: W.config_2d_single_crack(), 0.05),
+    "3d_q1_16": (lambda: W.small(W.config_3d_penny(), 16, 3), 0.05),
+    "2d_two_cracks_32": (lambda: W.config_2d_two_cracks(32, 3), 30.0),   # p_n = 10 n (Sec. 5.1)
 }
 
 
 @pytest.mark.parametrize("mgp", [32, 64])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_load_steps_match_oracle(name, mgp):
-    w = CASES[name]()
-    p_max = 50 * w.pressure
+    mk, p_max = CASES[name]
+    w = mk()
     U0, po, pt = W.initial_state(w)
     prm = pff.default_params(eps=w.eps, pressure=p_max / 3, kappa=w.kappa, E=w.E, nu=w.nu, Gc=w.Gc,
                              mg_precision=mgp)
@@ -42,6 +44,7 @@ def test_load_steps_match_oracle(name, mgp):
             gpu_act.append(a.cpu().numpy().astype(bool))
             prev = phi_nm1
         Ug = U.cpu().numpy()
+        qoi = (pff.energies(h), pff.boundary_load(h, 3, 1))
     finally:
         pff.destroy_hierarchy(h)
 
@@ -58,3 +61,7 @@ def test_load_steps_match_oracle(name, mgp):
         assert np.array_equal(gpu_act[n - 1], infos[-1].active)
     scale = np.abs(Uo).max()
     assert np.abs(Ug - Uo).max() <= 1e-6 * scale
+    ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=p_max)
+    ob, oc = fem.energy_parts(m, ph, Uo)
+    assert qoi[0][0] == pytest.approx(ob, rel=1e-5)
+    assert qoi[0][1] == pytest.approx(oc, rel=1e-5)

@@ -37,7 +37,7 @@ def rel(a, b):
 class Case:
     """A hierarchy on the GPU and the oracle's levels for the same inputs."""
 
-    def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0, variant=0):
+    def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0, variant=0, modulus=False):
         self.w = w
         if state == "random":
             U, po, pt = W.random_state(w)
@@ -48,11 +48,14 @@ class Case:
                                       Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f)
         self.h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), self.prm)
         pff.set_kernel_variant(self.h, variant)
+        es = W.modulus_field(w) if modulus else None
+        if modulus:
+            pff.set_modulus(self.h, t(es))
         pff.set_state(self.h, t(U), t(po), t(pt))
         act = W.random_active(w, active_fraction) if active_fraction > 0 else np.zeros(w.n_nodes, np.uint8)
         pff.set_active_set(self.h, t(act))
         self.mesh = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
-        self.phys = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, f=f)
+        self.phys = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, f=f, escale=es)
         self.mask = fem.dirichlet_face_mask(self.mesh, 0x3F) | (act * fem.BIT_ACTIVE).astype(np.uint8)
         self.levels = mg.build_levels(self.mesh, w.n_levels, self.phys, U, pt, self.mask)
 
@@ -73,13 +76,17 @@ CASES = {
     "2d_q1_lanes": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 2),
     "2d_q1_percell": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 3),
     "3d_q2": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1),
+    # spatially varying modulus (per-cell factor from a smooth seeded field)
+    "3d_q1_modulus": (lambda: W.small(W.config_3d_penny(), 20, 3), 0, True),
+    "3d_q1_lanes_modulus": (lambda: W.small(W.config_3d_penny(), 12, 2), 2, True),
+    "2d_q2_modulus": (lambda: W.small(W.config_2d_single_crack(deg=2), 12, 2), 1, True),
 }
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
 def case(request):
-    make_w, variant = CASES[request.param]
-    c = Case(make_w(), variant=variant)
+    make_w, variant, *rest = CASES[request.param]
+    c = Case(make_w(), variant=variant, modulus=bool(rest and rest[0]))
     yield c
     c.close()
 
@@ -204,3 +211,24 @@ def test_vcycle_fp64_matches_oracle(solver_case):
     pff.vcycle(c.h, t(v), z)
     ref = mg.precondition(c.levels, v, mg.MGParams())
     assert rel(z, ref) <= 1e-9
+
+
+def test_block_diagonal_vcycle_matches_oracle(solver_case):
+    """P_diag (Sec. 3.3): FP64 V-cycle and coarse solve without the coupling block."""
+    c = solver_case
+    prm = mg.MGParams(block_diagonal=True)
+    pd = pff.default_params(eps=c.w.eps, pressure=c.w.pressure, kappa=c.w.kappa, E=c.w.E, nu=c.w.nu,
+                            Gc=c.w.Gc, mg_precision=64, preconditioner=pff.PRECOND_DIAG)
+    pff.set_params(c.h, pd)
+    try:
+        lev = c.levels[0]
+        b = np.where(lev.free, W.random_vector(lev.mesh.n_dofs, 901), 0.0)
+        x = torch.zeros(lev.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        pff.coarse_solve(c.h, t(b), x)
+        assert rel(x, mg.coarse_solve(lev, b, prm)) <= 1e-9
+        v = W.random_vector(c.mesh.n_dofs, 1001)
+        z = torch.zeros(c.mesh.n_dofs, dtype=torch.float64, device=DEV)
+        pff.vcycle(c.h, t(v), z)
+        assert rel(z, mg.precondition(c.levels, v, prm)) <= 1e-9
+    finally:
+        pff.set_params(c.h, c.prm)

@@ -20,10 +20,10 @@ def t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def make(w, mg_precision, state="initial"):
+def make(w, mg_precision, state="initial", preconditioner=0):
     U, po, pt = W.initial_state(w, displacement="smooth") if state == "initial" else W.random_state(w)
     prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu, Gc=w.Gc,
-                             mg_precision=mg_precision)
+                             mg_precision=mg_precision, preconditioner=preconditioner)
     h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), prm)
     pff.set_state(h, t(U), t(po), t(pt))
     return h, U, po, pt
@@ -49,10 +49,11 @@ SOLVE_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(SOLVE_CASES))
-@pytest.mark.parametrize("mgp", [64, 32])
-def test_fgmres_iterations_match_oracle(name, mgp):
+@pytest.mark.parametrize("mgp,pc", [(64, 0), (32, 0), (64, 1), (32, 1)])
+def test_fgmres_iterations_match_oracle(name, mgp, pc):
+    """pc 0: P_full, pc 1: P_diag (Sec. 3.3)."""
     w = SOLVE_CASES[name]()
-    h, U, po, pt = make(w, mgp)
+    h, U, po, pt = make(w, mgp, preconditioner=pc)
     try:
         na, _ = pff.update_active_set(h)
         m, ph, act, Rt, lv = oracle_system(w, U, po, pt)
@@ -61,7 +62,7 @@ def test_fgmres_iterations_match_oracle(name, mgp):
         np.testing.assert_array_equal(active.cpu().numpy().astype(bool), act)
         G = lv[-1].G
         _, its_o, res_o, res0_o, _ = krylov.fgmres(lambda v: G @ v, Rt,
-                                                   lambda v: mg.precondition(lv, v, mg.MGParams()),
+                                                   lambda v: mg.precondition(lv, v, mg.MGParams(block_diagonal=pc == 1)),
                                                    rtol=1e-8, restart=30, maxit=200)
         x = torch.zeros(w.n_dofs, dtype=torch.float64, device=DEV)
         info = pff.gmres_solve(h, t(Rt), x, rtol=1e-8, restart=30, maxit=200)
@@ -130,5 +131,42 @@ def test_full_size_apply_sampled_rows():
         got = y.cpu().numpy()[rows]
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= 1e-12 * scale
+    finally:
+        pff.destroy_hierarchy(h)
+
+
+@pytest.mark.parametrize("mgp", [64, 32])
+def test_fgmres_with_varying_modulus(mgp):
+    """Spatially varying E (per-cell factor in [0.1, 1] from a smooth seeded field): the same
+    active set, iteration counts within 10% (+-1 for FP32) and the oracle's system solved."""
+    w = W.small(W.config_3d_penny(), 16, 3)
+    es = W.modulus_field(w)
+    U, po, pt = W.initial_state(w, displacement="smooth")
+    prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu, Gc=w.Gc,
+                             mg_precision=mgp)
+    h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), prm)
+    try:
+        pff.set_modulus(h, t(es))
+        pff.set_state(h, t(U), t(po), t(pt))
+        pff.update_active_set(h)
+        m = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, escale=es)
+        R = -fem.residual_A(m, ph, U, pt)
+        act = pdas.active_set(m, R, fem.lumped_mass(m), U, po, 100.0, 1e-10)
+        active = torch.empty(w.n_nodes, dtype=torch.uint8, device=DEV)
+        pff.get_active_set(h, active)
+        np.testing.assert_array_equal(active.cpu().numpy().astype(bool), act)
+        Rt, mask = pdas.eliminated_rhs(m, ph, U, pt, po, fem.dirichlet_face_mask(m, 0x3F), act, R)
+        lv = mg.build_levels(m, w.n_levels, ph, U, pt, mask)
+        mg.estimate_levels(lv, 12345, 10)
+        G = lv[-1].G
+        _, its_o, _, _, _ = krylov.fgmres(lambda v: G @ v, Rt, lambda v: mg.precondition(lv, v, mg.MGParams()),
+                                          rtol=1e-8, restart=30, maxit=200)
+        x = torch.zeros(w.n_dofs, dtype=torch.float64, device=DEV)
+        info = pff.gmres_solve(h, t(Rt), x, rtol=1e-8, restart=30, maxit=200)
+        assert info.converged
+        slack = max(1, math.floor(0.1 * its_o)) if mgp == 32 else math.floor(0.1 * its_o)
+        assert abs(info.iterations - its_o) <= slack, (info.iterations, its_o)
+        assert np.linalg.norm(Rt - G @ x.cpu().numpy()) <= 1.01e-8 * np.linalg.norm(Rt)
     finally:
         pff.destroy_hierarchy(h)

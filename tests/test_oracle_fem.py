@@ -213,3 +213,84 @@ def test_energy_parts_add_up_and_match_closed_forms(dim, deg):
     b0, c0 = fem.energy_parts(m, ph, U0)
     assert b0 == 0.0
     assert c0 == pytest.approx(0.5 * ph.Gc * (1 - cval) ** 2 / ph.eps * 2.0 ** dim, rel=1e-13)
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (3, 1), (3, 2)])
+def test_boundary_load_of_affine_field(dim, deg):
+    """L_c of Sec. 5 for u = diag(a) x (no shear) with constant phi~ = c: the effective stress on a
+    face is g(c) sigma + c^2 p I, so the upper face of axis y carries (g(c) sigma_yy + c^2 p) |face|
+    and the lower face the negative of it; sigma_yy = 2 mu a_y + lambda tr(a)."""
+    L = [1.0 + 0.25 * a for a in range(dim)]
+    m = fem.Mesh(dim, deg, (2,) * dim, (0.0,) * dim, tuple(L))
+    E, nu, p, kap, c = 2.0, 0.25, 3e-3, 1e-3, 0.5
+    ph = fem.Phys(E=E, nu=nu, p=p, eps=1.0, kappa=kap)
+    mu, lam = fem.lame(E, nu)
+    a = np.array([1e-2, -2e-2, 5e-3][:dim])
+    U = np.concatenate([_affine_u(m, np.diag(a)), np.ones(m.n_nodes)])
+    ptil = np.full(m.n_nodes, c)
+    area = np.prod([L[k] for k in range(dim) if k != 1])
+    syy = 2 * mu * a[1] + lam * a.sum()
+    want = ((1 - kap) * c * c + kap) * syy + c * c * p
+    assert fem.boundary_load(m, ph, U, ptil, 3, 1) == pytest.approx(want * area, rel=1e-12)
+    assert fem.boundary_load(m, ph, U, ptil, 2, 1) == pytest.approx(-want * area, rel=1e-12)
+    # no shear: the x-component of the load on a y-face vanishes
+    assert abs(fem.boundary_load(m, ph, U, ptil, 3, 0)) < 1e-14
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (3, 1), (2, 2)])
+def test_varying_modulus(dim, deg):
+    """Per-cell modulus E_K = s_K E: (a) a constant factor s is the same as the modulus s E
+    (residual, Jacobian, energy); (b) with a varying factor the residual is still the gradient of
+    the energy and the Jacobian the derivative of the residual (central differences); (c) a cell
+    whose factor changes alters only the rows of its own nodes."""
+    m = _mesh(dim, deg, 2)
+    rng = np.random.default_rng(11)
+    U = _rand_state(m, 12)
+    ptil = rng.uniform(0, 1, m.n_nodes)
+    zero = np.zeros(m.n_nodes, np.uint8)
+    s = 0.37
+    ph_s = fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, kappa=1e-3, escale=np.full(m.n_cells, s))
+    ph_e = fem.Phys(E=s, nu=0.2, p=0.05, eps=0.3, kappa=1e-3)
+    np.testing.assert_allclose(fem.residual_A(m, ph_s, U, ptil), fem.residual_A(m, ph_e, U, ptil), rtol=1e-13,
+                               atol=1e-15)
+    Gs = fem.assemble(m, ph_s, U, ptil, zero).toarray()
+    Ge = fem.assemble(m, ph_e, U, ptil, zero).toarray()
+    assert np.abs(Gs - Ge).max() <= 1e-13 * np.abs(Ge).max()
+    assert fem.energy(m, ph_s, U) == pytest.approx(fem.energy(m, ph_e, U), rel=1e-13)
+
+    es = rng.uniform(0.1, 1.0, m.n_cells)
+    ph = fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, kappa=1e-3, escale=es)
+    phi = U[dim * m.n_nodes:]
+    A = fem.residual_A(m, ph, U, phi)
+    G = fem.assemble(m, ph, U, ptil, zero)
+    for _ in range(2):
+        v = rng.standard_normal(U.size)
+        fd = (fem.energy(m, ph, U + 1e-5 * v) - fem.energy(m, ph, U - 1e-5 * v)) / 2e-5
+        assert fd == pytest.approx(A @ v, rel=1e-7)
+        fdj = (fem.residual_A(m, ph, U + 1e-6 * v, ptil) - fem.residual_A(m, ph, U - 1e-6 * v, ptil)) / 2e-6
+        assert np.linalg.norm(fdj - G @ v) <= 1e-7 * np.linalg.norm(G @ v)
+
+    es2 = es.copy()
+    es2[0] *= 3.0
+    dA = fem.residual_A(m, fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, kappa=1e-3, escale=es2), U, ptil) - \
+        fem.residual_A(m, fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, kappa=1e-3, escale=es), U, ptil)
+    npa = m.nodes_per_axis()
+    idx = np.indices(npa[::-1]).reshape(dim, -1)[::-1]
+    in_cell0 = np.all(idx <= deg, axis=0)
+    touched = np.abs(dA.reshape(dim + 1, -1)).max(axis=0) > 0
+    assert touched.any() and not np.any(touched & ~in_cell0)
+
+
+def test_coarsened_modulus_is_child_mean():
+    """The coarse-level factor is the mean of the 2^d children: constants are kept and the
+    integral of the factor is preserved."""
+    from oracle import multigrid as mg
+    m = fem.Mesh(3, 1, (4, 6, 2), (0.0,) * 3, (1.0, 1.5, 0.5))
+    es = np.random.default_rng(13).uniform(0.1, 1.0, m.n_cells)
+    c = mg.coarsen_cell_field(m, es)
+    assert c.size == m.n_cells // 8
+    assert c.sum() * 8 == pytest.approx(es.sum(), rel=1e-14)
+    assert np.allclose(mg.coarsen_cell_field(m, np.full(m.n_cells, 0.3)), 0.3, rtol=0, atol=1e-16)
+    # first coarse cell: children (0..1, 0..1, 0..1)
+    e3 = es.reshape(2, 6, 4)
+    assert c[0] == pytest.approx(e3[0:2, 0:2, 0:2].mean(), rel=1e-15)
