@@ -39,6 +39,11 @@ def _peaks():
         return {}
 
 
+# DRAM bytes per cell of the FP64-accurate apply, from one ncu capture at 64^3 (158.7 MB per launch
+# over 262,144 cells): the stored df64 Gauss-point data plus x, mask and y
+TRAFFIC_DF64_PER_CELL = 158.728448e6 / 262144
+
+
 def _nvtx(name: str, push: bool):
     """NVTX range around the timed region, so that a profiler can select exactly its launches."""
     try:
@@ -417,7 +422,9 @@ def main():
     fl32 = 1448.0 * cells
     roof = {"kernel": "k_q1_apply_lanes<3, df64> (FP64-accurate fine-level Jacobian apply)",
             "bound": "alu", "achieved": fl64 / (apply_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-            "traffic": None, "algorithmic_flops_per_launch": fl64,
+            "traffic": TRAFFIC_DF64_PER_CELL * cells, "algorithmic_flops_per_launch": fl64,
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 64^3 "
+                            "(158.7 MB), scaled by cells",
             "note": "peak: FP32 pipe derived from unit counts and 2.07 GHz; double-float arithmetic on FP32 pipes",
             "hbm": {"achieved": 105.0 * nn / (apply_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": 105.0 * nn / (apply_ms * 1e-3) / 1e9 / hbm,
