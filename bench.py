@@ -39,9 +39,9 @@ def _peaks():
         return {}
 
 
-# DRAM bytes per cell of the FP64-accurate apply, from one ncu capture at 64^3 (158.7 MB per launch
-# over 262,144 cells): the stored df64 Gauss-point data plus x, mask and y
-TRAFFIC_DF64_PER_CELL = 158.728448e6 / 262144
+# DRAM bytes per cell of the FP64-accurate apply k_q1_apply_direct<3, df64, 0> from one ncu capture
+# at 64^3 (bytes per launch / 262,144 cells); None until a capture of the current kernel exists
+TRAFFIC_DF64_PER_CELL = None
 
 
 def _nvtx(name: str, push: bool):
@@ -138,7 +138,8 @@ def cpu_baseline(n: int = 24, seconds: float = 3.0):
 def bench_batch(count: int, dev):
     """Batching pattern: 'count' instances of the batch recipe (N in {16,24,32,48,64}), one active-set
     step each (one linear solve to 1e-8).  Solves/s of the batched FP32-MG solver against the same
-    instances solved one after another by the plain FP64 single-instance solver (FP64 V-cycle)."""
+    instances solved one after another by the single-instance solver with the same FP32 V-cycle,
+    and with the FP64 V-cycle."""
     import torch
     from paper_1902_08112_gb300 import pff, workloads as W
     ws = W.batch_instances(count)
@@ -169,23 +170,89 @@ def bench_batch(count: int, dev):
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     pff.batch_destroy(b)
-    for h in hs:
-        pff.destroy_hierarchy(h)
-    hs, Us = build(64)
-    pff.newton_step(hs[0], Us[0].clone(), allow_noconv=True)   # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sinfos = [pff.newton_step(h, u, allow_noconv=True) for h, u in zip(hs, Us)]
-    torch.cuda.synchronize()
-    ts = time.perf_counter() - t0
+    single = {}
+    for mgp in (32, 64):
+        if mgp == 64:
+            for h in hs:
+                pff.destroy_hierarchy(h)
+            hs, _ = build(64)
+        for u, u0 in zip(Us, U0):
+            u.copy_(u0)
+        pff.newton_step(hs[0], Us[0].clone(), allow_noconv=True)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sinfos = [pff.newton_step(h, u, allow_noconv=True) for h, u in zip(hs, Us)]
+        torch.cuda.synchronize()
+        single[mgp] = (time.perf_counter() - t0, [i.solve.iterations for i in sinfos])
     for h in hs:
         pff.destroy_hierarchy(h)
     dofs = sum(w.n_dofs for w in ws)
     return {"instances": count, "dofs": dofs, "sizes": sorted({w.n_cells[0] for w in ws}),
-            "batched_fp32mg_solves_per_s": count / tb, "single_fp64mg_solves_per_s": count / ts,
-            "speedup": ts / tb, "gmres_its_batched": [i.solve.iterations for i in infos][:16],
-            "gmres_its_single": [i.solve.iterations for i in sinfos][:16],
+            "batched_fp32mg_solves_per_s": count / tb,
+            "single_fp32mg_solves_per_s": count / single[32][0],
+            "single_fp64mg_solves_per_s": count / single[64][0],
+            "speedup_vs_single_fp32mg": single[32][0] / tb,
+            "gmres_its_batched": [i.solve.iterations for i in infos],
+            "gmres_its_single_fp32mg": single[32][1], "gmres_its_single_fp64mg": single[64][1],
             "all_converged": all(i.solve.converged for i in infos)}
+
+
+def bench_multi(n: int, dev):
+    """3D multi-crack configuration (n^3 Q1, 8 penny cracks, 6 levels): FP64-accurate fine apply,
+    V-cycle and time to a 1e-8 FGMRES solve of the Newton right-hand side with the FP32 and the FP64
+    V-cycle, at the initial crack state with the active set of Algorithm 1."""
+    import torch
+    from paper_1902_08112_gb300 import pff, workloads as W
+    w = W.config_3d_multi(n=n, n_levels=6 if n >= 128 else 4)
+    U, po, pt = W.initial_state(w, displacement="smooth")
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": f"3d_multi_q1_{n}", "n_dofs": w.n_dofs, "levels": w.n_levels}
+
+    def timed(fn, reps=3):
+        fn()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for mgp in (32, 64):
+        prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
+                                 mg_precision=mgp)
+        h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm, stream)
+        try:
+            with torch.cuda.stream(stream):
+                Ud, pod, ptd = (torch.from_numpy(a).to(dev) for a in (U, po, pt))
+                x = torch.randn(w.n_dofs, dtype=torch.float64, device=dev)
+                y = torch.empty_like(x)
+                z = torch.empty_like(x)
+                R = torch.empty_like(x)
+                xs = torch.zeros_like(x)
+            stream.synchronize()
+            pff.set_state(h, Ud, pod, ptd)
+            na, _ = pff.update_active_set(h)
+            pff.setup(h)
+            if mgp == 32:
+                ms = timed(lambda: pff.apply_jacobian(h, -1, x, y), reps=5)
+                out["apply64_ms"] = ms
+                out["apply_gdofs"] = w.n_dofs / (ms * 1e-3) / 1e9
+                out["n_active"] = na
+            vc = timed(lambda: pff.vcycle(h, x, z))
+            pff.residual(h, R)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=300, allow_noconv=True)
+            stream.synchronize()
+            out[f"fp{mgp}_mg"] = {"vcycle_ms": vc, "solve_ms": (time.perf_counter() - t0) * 1e3,
+                                  "iterations": info.iterations, "rel_res": info.res_final / max(info.res0, 1e-300),
+                                  "converged": bool(info.converged)}
+        finally:
+            pff.destroy_hierarchy(h)
+    return out
 
 
 def bench_serve(count: int):
@@ -254,6 +321,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=32, help="instances in the batching measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving measurement (0: skip)")
+    ap.add_argument("--multi", type=int, default=256, help="cells per edge of the multi-crack measurement (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -291,7 +359,7 @@ def main():
     for n in (1, 2, 3):
         with torch.cuda.stream(stream):
             phi_nm1 = U[3 * nn:].clone()
-        li = pff.load_step(h, U, prev, w.pressure * n / 3, max_newton=30, allow_noconv=True)
+        li = pff.load_step(h, U, prev, w.pressure * n / 3, max_newton=12, allow_noconv=True)
         load_info.append({"newton_steps": li.newton_steps, "converged": li.converged,
                           "gmres_iterations": li.gmres_iterations})
         prev = phi_nm1
@@ -411,7 +479,8 @@ def main():
     # double-float on the FP32 pipes.  Peak = FP32 pipe from unit counts and the max clock:
     # 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  Algorithmic FP32 flops per cell of the
     # double-float lane apply: 8 lanes x (92 double-float adds x 8 + 131 multiplies x 7) = 13224;
-    # of the FP32 per-cell apply: 1448 (the modal algorithm's adds and multiplies).
+    # of the FP32 per-cell apply (butterfly form, counted from its operations): pass 1 756
+    # (transforms 180, Gauss-point work 8 x 45, integration 72 + 144), pass 2 176: 932.
     classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32),
                "vcycle_graph": (cntv, msv)}
     peaks = _peaks()
@@ -419,10 +488,11 @@ def main():
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     cells = w.n_cells_total
     fl64 = 13224.0 * cells
-    fl32 = 1448.0 * cells
-    roof = {"kernel": "k_q1_apply_lanes<3, df64> (FP64-accurate fine-level Jacobian apply)",
+    fl32 = 932.0 * cells
+    roof = {"kernel": "k_q1_apply_direct<3, df64, 0> (FP64-accurate fine-level Jacobian apply)",
             "bound": "alu", "achieved": fl64 / (apply_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-            "traffic": TRAFFIC_DF64_PER_CELL * cells, "algorithmic_flops_per_launch": fl64,
+            "traffic": TRAFFIC_DF64_PER_CELL * cells if TRAFFIC_DF64_PER_CELL else None,
+            "algorithmic_flops_per_launch": fl64,
             "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 64^3 "
                             "(158.7 MB), scaled by cells",
             "note": "peak: FP32 pipe derived from unit counts and 2.07 GHz; double-float arithmetic on FP32 pipes",
@@ -431,7 +501,7 @@ def main():
                     "algorithmic_bytes_per_launch": 105.0 * nn, "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "fp64_equivalent_tflops": 8 * 223.0 * cells / (apply_ms * 1e-3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof32 = {"kernel": "k_q1_apply<3, float> (FP32 fine-level V-cycle operator)", "ms": ms32_fine,
+    roof32 = {"kernel": "k_q1_apply<3, float, 0> (FP32 fine-level V-cycle operator)", "ms": ms32_fine,
               "bound": "alu", "achieved": fl32 / (ms32_fine * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
               "frac": fl32 / (ms32_fine * 1e-3) / 1e12 / fp32_peak,
               "hbm_frac": 53.0 * nn / (ms32_fine * 1e-3) / 1e9 / hbm, "gdofs": nd / (ms32_fine * 1e-3) / 1e9}
@@ -460,6 +530,8 @@ def main():
         line["batch"] = bench_batch(args.batch, dev)
     if args.serve > 0:
         line["serve"] = bench_serve(args.serve)
+    if args.multi > 0:
+        line["multi_crack"] = bench_multi(args.multi, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline()
         line["cpu_baseline"] = cb

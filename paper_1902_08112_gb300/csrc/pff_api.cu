@@ -337,10 +337,11 @@ extern "C" pff_status pff_set_modulus(pff_hierarchy* h, const double* escale) {
 
 extern "C" pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant) {
     if (!h) return PFF_EINVAL;
-    REQUIRE(h, variant >= 0 && variant <= 3, PFF_EINVAL, "variant must be 0, 1, 2 or 3");
+    REQUIRE(h, variant >= 0 && variant <= 5, PFF_EINVAL, "variant must be 0 .. 5");
     drop_graph(h);
     h->fast_q1 = variant != 1;
-    h->q1_style = variant == 2 ? 3 : (variant == 3 ? 0 : 1);
+    static const int style[6] = {4, 4, 3, 0, 1, 12};
+    h->q1_style = style[variant];
     h->stale = true;
     return PFF_OK;
 }
@@ -471,10 +472,10 @@ extern "C" pff_status pff_level_state(const pff_hierarchy* h, int level, double*
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return PFF_EINVAL;
     const Level& L = h->lv[l];
-    cudaError_t e = cudaSuccess;
-    if (U) e = cudaMemcpyAsync(U, L.U64, sizeof(double) * n_dofs(L.g), cudaMemcpyDeviceToDevice, h->stream);
+    cudaError_t e = refresh_state(const_cast<pff_hierarchy*>(h));   // logically const: derived data only
     if (e == cudaSuccess && phi_tilde)
         e = cudaMemcpyAsync(phi_tilde, L.pt64, sizeof(double) * L.g.n_nodes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && U) e = cudaMemcpyAsync(U, L.U64, sizeof(double) * n_dofs(L.g), cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess && mask) e = cudaMemcpyAsync(mask, L.mask, L.g.n_nodes, cudaMemcpyDeviceToDevice, h->stream);
     return e == cudaSuccess ? PFF_OK : PFF_ECUDA;
 }
@@ -633,13 +634,16 @@ pff_status pff_internal_newton_prepare(pff_hierarchy* h, double* U, int* n_act, 
     return PFF_OK;
 }
 
-// U += dU (tmp64[2]); the new U becomes the hierarchy's state.
+// U += dU (tmp64[2]); the new U becomes the hierarchy's state.  The coarse levels and the
+// Gauss-point data follow lazily (refresh_state), so that a following Newton step, which sets the
+// state again, computes them once.
 pff_status pff_internal_newton_finish(pff_hierarchy* h, double* U) {
     Level& F = h->lv[h->L - 1];
     const int64_t nd = n_dofs(F.g);
     CUDA_OR_FAIL(h, launch_axpby<double>(nd, 1.0, h->tmp64[2], 1.0, U, h->stream));
     CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    CUDA_OR_FAIL(h, propagate_state(h));
+    h->derived_dirty = true;
+    h->stale = true;
     return PFF_OK;
 }
 

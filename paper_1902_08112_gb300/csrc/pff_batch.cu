@@ -686,6 +686,7 @@ extern "C" pff_status pff_batch_setup(pff_batch* b) {
     if (!b) return PFF_EINVAL;
     for (auto* h : b->hs)
         if (!h->has_state) return b_fail(b, PFF_ESTATE, "batch setup before pff_set_state of every instance");
+    for (auto* h : b->hs) BCUDA_OR_FAIL(b, refresh_state(h));
     b->valid.assign(b->n, 1);
     BCUDA_OR_FAIL(b, upload(b));
     BCUDA_OR_FAIL(b, b_setup(b));

@@ -24,7 +24,7 @@ __global__ void kb_init_masked(const BLevel* __restrict__ L, int sx, int sy, int
     const T* x = sx >= 0 ? bvec<T>(d, sx) : nullptr;
     T* y = bvec<T>(d, sy);
     BSTRIDE(i, nd) {
-        const int c = (int)(i / nn);
+        const int c = dof_comp(i, nn);
         const bool e = belim(d.mask[i - c * nn], c, d.g.dim, phi_bits);
         y[i] = e ? (x ? x[i] : elim_val) : T(0);
     }
@@ -96,7 +96,7 @@ __global__ void kb_convert(const BLevel* __restrict__ L, int ss, int sd, int mod
     To* t = bvec<To>(d, sd);
     BSTRIDE(i, nd) {
         if (mode == 0) { t[i] = (To)s[i]; continue; }
-        const int c = (int)(i / nn);
+        const int c = dof_comp(i, nn);
         const bool e = belim(d.mask[i - c * nn], c, d.g.dim, PHI_BITS_ALL);
         if (mode == 1) t[i] = e ? To(0) : (To)s[i];
         else if (e) t[i] = (To)s[i];
@@ -377,7 +377,7 @@ __global__ void kb_start_vector(const BLevel* __restrict__ L, int sv, const uint
     T* v = bvec<T>(d, sv);
     const uint64_t seed = seeds[blockIdx.y];
     BSTRIDE(i, nd) {
-        const int c = (int)(i / nn);
+        const int c = dof_comp(i, nn);
         const uint64_t key = seed + (uint64_t)level * (1ull << 40) + (uint64_t)i;
         const double u = (double)(bsplitmix64(key) >> 11) * 0x1.0p-53;
         v[i] = belim(d.mask[i - c * nn], c, d.g.dim, PHI_BITS_ALL) ? T(0) : T(2.0 * u - 1.0);

@@ -41,6 +41,12 @@ struct Geom {
 
 __host__ __device__ inline int64_t n_dofs(const Geom& g) { return (int64_t)(g.dim + 1) * g.n_nodes; }
 
+// component of a DoF index in a component-blocked vector of up to 4 blocks of nn entries
+// (comparisons instead of a 64-bit division)
+__device__ __forceinline__ int dof_comp(int64_t i, int64_t nn) {
+    return (int)(i >= nn) + (int)(i >= 2 * nn) + (int)(i >= 3 * nn);
+}
+
 // Device arrays of one level.
 struct Level {
     Geom g;
@@ -108,7 +114,7 @@ cudaError_t launch_invert_diag(T* d, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cheb_update(const Geom& g, T* r, const T* t, T* d, const T* dinv, T* x,
                                double c1u, double c1p, double c2u, double c2p, int first,
-                               cudaStream_t s);
+                               cudaStream_t s, const uint8_t* mask = nullptr, T* tn = nullptr);
 // elementwise helpers
 template <typename T>
 cudaError_t launch_axpby(int64_t n, double a, const T* x, double b, T* y, cudaStream_t s);  // y = a x + b y
@@ -197,11 +203,12 @@ struct pff_hierarchy {
     double* kr_h = nullptr;          // device column of H (2 * (m + 1))
     bool has_state = false;
     bool fast_q1 = true;             // Q1 levels use the linearisation-data kernels of pff_q1.cu
-    int q1_style = 1;                // bit 0: df64 applies per Gauss-point lane; bit 1: FP32 likewise
+    int q1_style = 4;                // bit 0/1: lanes for FP64/FP32; bit 2/3: lanes with global atomics for FP64/FP32
     bool use_graphs = true;          // replay the V-cycle body from a captured CUDA graph
     cudaGraphExec_t vgraph = nullptr;   // captured V-cycle body (valid until the next setup)
     long long vgraph_nodes = 0;
     bool active_known = false;       // an active set has been computed or set
+    bool derived_dirty = false;      // fine U changed; coarse levels, FP32 copies, Gauss-point data not yet
     bool stale = true;               // preconditioner data out of date
     std::vector<void*> allocs;       // every device allocation, freed on destroy
     // kernel timing: event pairs per class, recorded while prof_on

@@ -359,7 +359,7 @@ __global__ void k_init_masked(int64_t nn, int dim, const uint8_t* __restrict__ m
                               int phi_bits, const T* __restrict__ x, T* __restrict__ y, T elim_val) {
     const int64_t nd = nn * (dim + 1);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i / nn);
+        const int c = dof_comp(i, nn);
         const uint8_t m = mask[i - c * nn];
         const bool e = c < dim ? (((m & u_bits) >> c) & 1) != 0 : (m & phi_bits) != 0;
         y[i] = e ? (x ? x[i] : elim_val) : T(0);

@@ -17,6 +17,8 @@
 // {-1,1}^d) values and gradients are sums of scaled m_k with sign patterns sigma^k, and the
 // transposed (integration) step is the same butterfly run backwards.  All sign patterns are
 // compile-time constants after unrolling.
+#include <cstring>
+
 #include "pff_df64.cuh"
 #include "pff_internal.cuh"
 #include "pff_q1.cuh"
@@ -71,107 +73,171 @@ __device__ __forceinline__ void inv(S* v) {
             }
 }
 
-// ------------------------------------------------------------------ linearisation data (FP64)
+// ------------------------------------------------------------------ linearisation data (df64)
+// Constants of the linearisation as (hi, lo) float pairs, computed once on the host.
+struct LinConsts {
+    float2 cv[4];        // g^j / 2^d: modal coefficient -> Gauss-point value
+    float2 cg[3][3];     // g^j 2 / (h_d 2^d): modal coefficient -> Gauss-point derivative along d
+    float2 w;            // Gauss weight x |K|
+    float2 omk, kap;     // 1 - kappa, kappa
+    float2 f2k;          // 2 f (1 - kappa)
+    float2 p2;           // 2 p
+    float2 gce;          // Gc / eps
+    float2 mu, lam;      // Lame coefficients (scaled per cell by a varying modulus)
+};
+
+__device__ __forceinline__ df64 dfc(float2 v) { return df_make(v.x, v.y); }
+// exact scaling by a power of two
+__device__ __forceinline__ df64 df_scale(df64 a, float s) { return df_make(a.hi * s, a.lo * s); }
+__device__ __forceinline__ float df_scale(float a, float s) { return a * s; }
+// hi + lo renormalised so that hi is the float nearest to the value
+__device__ __forceinline__ df64 df_renorm(df64 a) { return df_two_sum(a.hi, a.lo); }
+
+// For every cell and Gauss point q the state enters the Jacobian through c0, Sp and c1 (header
+// comment).  Values at the Gauss points come from the modal coefficients by one inverse butterfly
+// (v_q = sum_k sigma^k(q) cv[|k|] m_k); a Q1 derivative along d does not vary along d, so its 2^(d-1)
+// distinct values come from a butterfly over the other axes.  All arithmetic in df64.
 template <int DIM>
-__global__ void k_q1_linearize(Geom g, Phys ph, const double* __restrict__ U, const double* __restrict__ pt,
-                               float* __restrict__ q32, float2* __restrict__ q64, double gpt) {
+__global__ void __launch_bounds__(128) k_q1_linearize(Geom g, LinConsts k, const double* __restrict__ U,
+                                                      const double* __restrict__ pt, float* __restrict__ q32,
+                                                      float2* __restrict__ q64) {
     using D = Q1Dims<DIM>;
-    constexpr int NV = D::NV, NK = D::NK;
+    constexpr int NV = D::NV, NK = D::NK, NH = NV / 2;
     const int64_t nc = g.n_cells, nn = g.n_nodes;
-    double vol = 1.0;
-    for (int a = 0; a < DIM; ++a) vol *= g.h[a];
-    const double w = vol / NV;
-    double gp[DIM + 1];
-    gp[0] = 1.0;
-    for (int j = 1; j <= DIM; ++j) gp[j] = gp[j - 1] * gpt;
+    const df64 w = dfc(k.w), omk = dfc(k.omk), kap = dfc(k.kap), f2k = dfc(k.f2k), p2 = dfc(k.p2);
+    const df64 gce = dfc(k.gce);
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < nc;
          cell += (int64_t)gridDim.x * blockDim.x) {
         int ci[3] = {0, 0, 0};
         int64_t r = cell;
         for (int a = 0; a < DIM; ++a) { ci[a] = (int)(r % g.nc[a]); r /= g.nc[a]; }
-        int64_t node[NV];
+        const int64_t n0 = (int64_t)ci[0] + (int64_t)g.nn[0] * ((int64_t)ci[1] + (int64_t)g.nn[1] * ci[2]);
+        const df64 sE = g.es ? df_from_double(g.es[cell]) : df_make(1.f, 0.f);
+        const df64 cmu = dfc(k.mu) * sE, clam = dfc(k.lam) * sE;
+        // Gauss-point values of phi and phi~
+        df64 vphi[NV], vpt[NV];
 #pragma unroll
         for (int n = 0; n < NV; ++n) {
-            const int i = ci[0] + (n & 1), j = ci[1] + ((n >> 1) & 1), k = DIM == 3 ? ci[2] + ((n >> 2) & 1) : 0;
-            node[n] = (int64_t)i + (int64_t)g.nn[0] * ((int64_t)j + (int64_t)g.nn[1] * k);
+            const int64_t node = n0 + (n & 1) + (int64_t)g.nn[0] * (((n >> 1) & 1) + (DIM == 3 ? (int64_t)g.nn[1] * ((n >> 2) & 1) : 0));
+            vphi[n] = df_from_double(U[DIM * nn + node]);
+            vpt[n] = df_from_double(pt[node]);
         }
-        const double sE = g.es ? g.es[cell] : 1.0;
-        const double cmu = ph.mu * sE, clam = ph.lam * sE;
-        double mu_[DIM][NV], mphi[NV], mpt[NV];
+        fwd<DIM>(vphi);
+        fwd<DIM>(vpt);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            vphi[m] = vphi[m] * dfc(k.cv[popc(m)]);
+            vpt[m] = vpt[m] * dfc(k.cv[popc(m)]);
+        }
+        inv<DIM>(vphi);
+        inv<DIM>(vpt);
+        // displacement derivatives: gd[c][d][j], j = Gauss-point index without bit d
+        df64 gd[DIM][DIM][NH];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
+            df64 m_[NV];
 #pragma unroll
-            for (int n = 0; n < NV; ++n) mu_[c][n] = U[c * nn + node[n]];
-            fwd<DIM>(mu_[c]);
+            for (int n = 0; n < NV; ++n) {
+                const int64_t node = n0 + (n & 1) + (int64_t)g.nn[0] * (((n >> 1) & 1) + (DIM == 3 ? (int64_t)g.nn[1] * ((n >> 2) & 1) : 0));
+                m_[n] = df_from_double(U[c * nn + node]);
+            }
+            fwd<DIM>(m_);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                int j = 0;
+#pragma unroll
+                for (int kp = 0; kp < NV; ++kp) {
+                    if (kp & (1 << d)) continue;
+                    gd[c][d][j] = m_[kp | (1 << d)] * dfc(k.cg[d][popc(kp)]);
+                    ++j;
+                }
+                inv<DIM - 1>(gd[c][d]);
+#pragma unroll
+                for (int jj = 0; jj < NH; ++jj) gd[c][d][jj] = df_renorm(gd[c][d][jj]);
+            }
         }
 #pragma unroll
-        for (int n = 0; n < NV; ++n) { mphi[n] = U[DIM * nn + node[n]]; mpt[n] = pt[node[n]]; }
-        fwd<DIM>(mphi);
-        fwd<DIM>(mpt);
-#pragma unroll
         for (int q = 0; q < NV; ++q) {
-            double gu[DIM][DIM], phi = 0.0, ptv = 0.0;
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                const double s = sgn(k, q) * gp[popc(k)] / NV;
-                phi += s * mphi[k];
-                ptv += s * mpt[k];
-            }
+            df64 gu[DIM][DIM];
 #pragma unroll
             for (int c = 0; c < DIM; ++c)
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
-                    double acc = 0.0;
-#pragma unroll
-                    for (int kp = 0; kp < NV; ++kp) {
-                        if (kp & (1 << d)) continue;
-                        acc += sgn(kp, q) * gp[popc(kp)] * mu_[c][kp | (1 << d)];
-                    }
-                    gu[c][d] = acc * (2.0 / (g.h[d] * NV));
+                    const int jq = (q & ((1 << d) - 1)) | ((q >> (d + 1)) << d);   // q without bit d
+                    gu[c][d] = gd[c][d][jq];
                 }
-            double e[DIM][DIM], tr = 0.0, ee = 0.0;
+            df64 e[DIM][DIM], tr = gu[0][0], ee = gu[0][0] * gu[0][0];
 #pragma unroll
-            for (int i = 0; i < DIM; ++i)
+            for (int i = 0; i < DIM; ++i) {
+                e[i][i] = gu[i][i];
+                if (i > 0) { tr = tr + gu[i][i]; ee = ee + gu[i][i] * gu[i][i]; }
 #pragma unroll
-                for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
-#pragma unroll
-            for (int i = 0; i < DIM; ++i) tr += e[i][i];
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                for (int j = 0; j < DIM; ++j) ee += e[i][j] * e[i][j];
-            const double Es = 0.5 * clam * tr * tr + cmu * ee;
-            const double gk = (1.0 - ph.kappa) * ptv * ptv + ph.kappa;
-            double vals[NK];
-            vals[0] = w * gk * sE;
-            const double a1 = 2.0 * ph.f * (1.0 - ph.kappa) * phi, b1 = 2.0 * ph.p * phi;
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                for (int j = i; j < DIM; ++j) {
-                    const double sig = 2.0 * cmu * e[i][j] + (i == j ? clam * tr : 0.0);
-                    vals[1 + sidx<DIM>(i, j)] = w * (a1 * sig + (i == j ? b1 : 0.0));
+                for (int jx = i + 1; jx < DIM; ++jx) {
+                    e[i][jx] = df_scale(gu[i][jx] + gu[jx][i], 0.5f);
+                    e[jx][i] = e[i][jx];
+                    ee = ee + df_scale(e[i][jx] * e[i][jx], 2.f);
                 }
-            vals[NK - 1] = w * (2.0 * ph.f * (1.0 - ph.kappa) * Es + 2.0 * ph.p * tr + ph.Gc / ph.eps);
+            }
+            tr = df_renorm(tr);
+            const df64 Es = df_scale(clam * tr * tr, 0.5f) + cmu * ee;
+            const df64 phi = df_renorm(vphi[q]), ptv = df_renorm(vpt[q]);
+            df64 vals[NK];
+            vals[0] = w * (omk * ptv * ptv + kap) * sE;
+            const df64 a1 = f2k * phi, b1 = p2 * phi;
+            const df64 ltr = clam * tr;
 #pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                const int64_t idx = (int64_t)(q * NK + k) * nc + cell;
-                q32[idx] = (float)vals[k];
-                const float hi = __double2float_rn(vals[k]);
-                q64[idx] = make_float2(hi, __double2float_rn(vals[k] - (double)hi));
+            for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                for (int jx = i; jx < DIM; ++jx) {
+                    df64 sig = df_scale(cmu * e[i][jx], 2.f);
+                    if (i == jx) sig = sig + ltr;
+                    df64 v = a1 * sig;
+                    if (i == jx) v = v + b1;
+                    vals[1 + sidx<DIM>(i, jx)] = w * v;
+                }
+            vals[NK - 1] = w * (f2k * Es + p2 * tr + gce);
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) {
+                const df64 v = df_renorm(vals[kk]);
+                const int64_t idx = (int64_t)(q * NK + kk) * nc + cell;
+                q32[idx] = v.hi;
+                q64[idx] = make_float2(v.hi, v.lo);
             }
         }
     }
 }
 
+static float2 split_pair(double d);
+
+template <typename K>
+static void fill_lin_consts(const Geom& g, const Phys& ph, K& k) {
+    const int NV = 1 << g.dim;
+    const double gpt = 1.0 / sqrt(3.0);
+    const double gp[4] = {1.0, gpt, gpt * gpt, gpt * gpt * gpt};
+    for (int j = 0; j < 4; ++j) k.cv[j] = split_pair(gp[j] / NV);
+    for (int d = 0; d < 3; ++d)
+        for (int j = 0; j < 3; ++j) k.cg[d][j] = split_pair(d < g.dim ? gp[j] * 2.0 / (g.h[d] * NV) : 0.0);
+    double vol = 1.0;
+    for (int d = 0; d < g.dim; ++d) vol *= g.h[d];
+    k.w = split_pair(vol / NV);
+    k.omk = split_pair(1.0 - ph.kappa);
+    k.kap = split_pair(ph.kappa);
+    k.f2k = split_pair(2.0 * ph.f * (1.0 - ph.kappa));
+    k.p2 = split_pair(2.0 * ph.p);
+    k.gce = split_pair(ph.Gc / ph.eps);
+    k.mu = split_pair(ph.mu);
+    k.lam = split_pair(ph.lam);
+}
+
 cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, const double* pt, float* q32,
                                 float2* q64, cudaStream_t s) {
-    const double gpt = 1.0 / sqrt(3.0);
+    LinConsts k;
+    fill_lin_consts(g, ph, k);
     int64_t blocks = (g.n_cells + 127) / 128;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    if (g.dim == 3) k_q1_linearize<3><<<(int)blocks, 128, 0, s>>>(g, ph, U, pt, q32, q64, gpt);
-    else k_q1_linearize<2><<<(int)blocks, 128, 0, s>>>(g, ph, U, pt, q32, q64, gpt);
+    if (g.dim == 3) k_q1_linearize<3><<<(int)blocks, 128, 0, s>>>(g, k, U, pt, q32, q64);
+    else k_q1_linearize<2><<<(int)blocks, 128, 0, s>>>(g, k, U, pt, q32, q64);
     return count_launch(cudaGetLastError());
 }
 
@@ -282,10 +348,14 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
 
         const S mu = cpair<S>(a.k.mu);
 
-        // ======== pass 1: displacement rows (G_uu) and the coupling term of the phi rows
+        // ======== pass 1: displacement rows (G_uu) and the coupling term of the phi rows.
+        // A Q1 derivative along d does not vary along d: its 2^(d-1) Gauss-point values come from an
+        // inverse butterfly over the other axes; integration against the test-function derivatives
+        // is the transposed (forward) butterfly of the Gauss-point fluxes summed in pairs along d.
+        constexpr int NH = NV / 2;
         S cpl[NV];
         {
-            S G[DIM][DIM][NV / 2];     // G[c][d][j]: gradient-form coefficients, j = masks without bit d
+            S gd[DIM][DIM][NH];
 #pragma unroll
             for (int c = 0; c < DIM; ++c) {
                 S v[NV];
@@ -301,51 +371,31 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
 #pragma unroll
                     for (int kp = 0; kp < NV; ++kp) {
                         if (kp & (1 << d)) continue;
-                        G[c][d][j] = v[kp | (1 << d)] * cg[d][popc(kp)];
+                        gd[c][d][j] = v[kp | (1 << d)] * cg[d][popc(kp)];
                         ++j;
                     }
+                    inv<DIM - 1>(gd[c][d]);
                 }
             }
-            S H[DIM][DIM][NV / 2];
+            S ps[DIM][DIM][NH];
 #pragma unroll
             for (int c = 0; c < DIM; ++c)
 #pragma unroll
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll
-                    for (int j = 0; j < NV / 2; ++j) H[c][d][j] = Scalar<S>::zero();
+                    for (int j = 0; j < NH; ++j) ps[c][d][j] = Scalar<S>::zero();
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                S gd[DIM][DIM];
+                S g_[DIM][DIM];
 #pragma unroll
                 for (int c = 0; c < DIM; ++c)
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        S acc = Scalar<S>::zero();
-                        int j = 0;
-#pragma unroll
-                        for (int kp = 0; kp < NV; ++kp) {
-                            if (kp & (1 << d)) continue;
-                            acc = (sgn(kp, q) > 0) ? acc + G[c][d][j] : acc - G[c][d][j];
-                            ++j;
-                        }
-                        gd[c][d] = acc;
-                    }
+                    for (int d = 0; d < DIM; ++d) g_[c][d] = gd[c][d][(q & ((1 << d) - 1)) | ((q >> (d + 1)) << d)];
                 const S c0 = QData<S>::get(a.qd, (int64_t)(q * NK + 0) * g.n_cells + gid);
-                S tr = gd[0][0];
+                S tr = g_[0][0];
 #pragma unroll
-                for (int i = 1; i < DIM; ++i) tr = tr + gd[i][i];
+                for (int i = 1; i < DIM; ++i) tr = tr + g_[i][i];
                 const S ltr = lam * tr;
-                S fu[DIM][DIM];
-#pragma unroll
-                for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                    for (int j = i; j < DIM; ++j) {
-                        // c0 sigma(du)_ij with sigma = 2 mu e + lambda tr I and 2 e_ij = du_i,j + du_j,i
-                        const S sg = (i == j) ? mu2 * gd[i][i] + ltr : mu * (gd[i][j] + gd[j][i]);
-                        const S f = c0 * sg;
-                        fu[i][j] = f;
-                        fu[j][i] = f;
-                    }
                 S cp = Scalar<S>::zero();
                 if constexpr (!BLOCKDIAG) {
 #pragma unroll
@@ -353,25 +403,29 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
 #pragma unroll
                         for (int j = i; j < DIM; ++j) {
                             const S sp = QData<S>::get(a.qd, (int64_t)(q * NK + 1 + sidx<DIM>(i, j)) * g.n_cells + gid);
-                            cp = cp + sp * ((i == j) ? gd[i][i] : gd[i][j] + gd[j][i]);   // Sp : e(du)
+                            cp = cp + sp * ((i == j) ? g_[i][i] : g_[i][j] + g_[j][i]);   // Sp : e(du)
                         }
                 }
                 cpl[q] = cp;
 #pragma unroll
-                for (int c = 0; c < DIM; ++c)
+                for (int i = 0; i < DIM; ++i)
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        int j = 0;
-#pragma unroll
-                        for (int kp = 0; kp < NV; ++kp) {
-                            if (kp & (1 << d)) continue;
-                            H[c][d][j] = (sgn(kp, q) > 0) ? H[c][d][j] + fu[c][d] : H[c][d][j] - fu[c][d];
-                            ++j;
+                    for (int j = i; j < DIM; ++j) {
+                        // c0 sigma(du)_ij with sigma = 2 mu e + lambda tr I and 2 e_ij = du_i,j + du_j,i
+                        const S sg = (i == j) ? mu2 * g_[i][i] + ltr : mu * (g_[i][j] + g_[j][i]);
+                        const S f = c0 * sg;
+                        const int ji = (q & ((1 << j) - 1)) | ((q >> (j + 1)) << j);
+                        ps[i][j][ji] = ps[i][j][ji] + f;
+                        if (i != j) {
+                            const int jj = (q & ((1 << i) - 1)) | ((q >> (i + 1)) << i);
+                            ps[j][i][jj] = ps[j][i][jj] + f;
                         }
                     }
             }
 #pragma unroll
             for (int c = 0; c < DIM; ++c) {
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) fwd<DIM - 1>(ps[c][d]);
                 S Y[NV];
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
@@ -381,7 +435,7 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                         if (!(k & (1 << d))) continue;
                         const int kp = k & ~(1 << d);
                         const int j = (kp & ((1 << d) - 1)) | ((kp >> (d + 1)) << d);   // kp without bit d
-                        acc = acc + H[c][d][j] * cg[d][popc(kp)];
+                        acc = acc + ps[c][d][j] * cg[d][popc(kp)];
                     }
                     Y[k] = acc;
                 }
@@ -390,7 +444,8 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                 for (int n = 0; n < NV; ++n) sel[(n * NC + c) * NCELL + cell] = Y[n];
             }
         }
-        // ======== pass 2: phase-field rows (G_phiphi and the stored coupling)
+        // ======== pass 2: phase-field rows.  Values at the Gauss points by an inverse butterfly;
+        // the gradient-gradient term is diagonal in modal coefficients (factor 2^d).
         {
             S v[NV];
 #pragma unroll
@@ -399,55 +454,16 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                 v[n] = sx[DIM * NT + tb + off];
             }
             fwd<DIM>(v);
-            S Mp[NV], Gp[DIM][NV / 2];
+            S F[NV];
 #pragma unroll
-            for (int k = 0; k < NV; ++k) Mp[k] = v[k] * cv[popc(k)];
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                int j = 0;
-#pragma unroll
-                for (int kp = 0; kp < NV; ++kp) {
-                    if (kp & (1 << d)) continue;
-                    Gp[d][j] = v[kp | (1 << d)] * cg[d][popc(kp)];
-                    ++j;
-                }
-            }
-            S F[NV], Hp[DIM][NV / 2];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) F[k] = Scalar<S>::zero();
-#pragma unroll
-            for (int d = 0; d < DIM; ++d)
-#pragma unroll
-                for (int j = 0; j < NV / 2; ++j) Hp[d][j] = Scalar<S>::zero();
+            for (int k = 0; k < NV; ++k) F[k] = v[k] * cv[popc(k)];
+            inv<DIM>(F);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                S dphi = Scalar<S>::zero();
-#pragma unroll
-                for (int k = 0; k < NV; ++k) dphi = (sgn(k, q) > 0) ? dphi + Mp[k] : dphi - Mp[k];
                 const S c1 = QData<S>::get(a.qd, (int64_t)(q * NK + NK - 1) * g.n_cells + gid);
-                const S fp = c1 * dphi + cpl[q];
-#pragma unroll
-                for (int k = 0; k < NV; ++k) F[k] = (sgn(k, q) > 0) ? F[k] + fp : F[k] - fp;
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) {
-                    S gph = Scalar<S>::zero();
-                    int j = 0;
-#pragma unroll
-                    for (int kp = 0; kp < NV; ++kp) {
-                        if (kp & (1 << d)) continue;
-                        gph = (sgn(kp, q) > 0) ? gph + Gp[d][j] : gph - Gp[d][j];
-                        ++j;
-                    }
-                    const S fg = gcew * gph;
-                    j = 0;
-#pragma unroll
-                    for (int kp = 0; kp < NV; ++kp) {
-                        if (kp & (1 << d)) continue;
-                        Hp[d][j] = (sgn(kp, q) > 0) ? Hp[d][j] + fg : Hp[d][j] - fg;
-                        ++j;
-                    }
-                }
+                F[q] = c1 * F[q] + cpl[q];
             }
+            fwd<DIM>(F);
             S Y[NV];
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
@@ -456,8 +472,8 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                 for (int d = 0; d < DIM; ++d) {
                     if (!(k & (1 << d))) continue;
                     const int kp = k & ~(1 << d);
-                    const int j = (kp & ((1 << d) - 1)) | ((kp >> (d + 1)) << d);
-                    acc = acc + Hp[d][j] * cg[d][popc(kp)];
+                    // gradient term: 2^d Gc eps w cg^2 times the modal coefficient k
+                    acc = acc + df_scale((gcew * v[k]) * (cg[d][popc(kp)] * cg[d][popc(kp)]), float(NV));
                 }
                 Y[k] = acc;
             }
@@ -708,6 +724,89 @@ __device__ __forceinline__ void q1_apply_lanes_tile(
     }
 }
 
+// Lane apply without shared memory: every lane reads its node's x from global memory (neighbour
+// cells hit the caches) and adds its contribution to y with one atomic per component; no CTA
+// barrier.  Same arithmetic as q1_apply_lanes_tile.
+template <int DIM, typename S, bool BLOCKDIAG>
+__global__ void __launch_bounds__(256) k_q1_apply_direct(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
+    using T = LaneTile<DIM>;
+    using D = Q1Dims<DIM>;
+    constexpr int NV = D::NV, NC = D::NC, NK = D::NK;
+    const Geom& g = a.g;
+    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = DIM == 3 ? blockIdx.z * T::TZ : 0;
+    const int64_t nn = g.n_nodes;
+    const int cell = threadIdx.x / NV, n = threadIdx.x % NV;
+    const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
+    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+    const int gi = ci0 + li + (n & 1), gj = cj0 + lj + ((n >> 1) & 1), gk = DIM == 3 ? ck0 + lk + ((n >> 2) & 1) : 0;
+    const int64_t gn = valid ? (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk) : 0;
+    const int64_t gid = valid ? (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)) : 0;
+    const uint8_t m = valid ? a.mask[gn] : 0;
+    bool el[NC];
+    S xv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        el[c] = c < DIM ? ((m >> c) & 1) != 0 : (m & a.phi_bits) != 0;
+        xv[c] = (valid && !el[c]) ? Scalar<S>::load(a.x[c * nn + gn]) : Scalar<S>::zero();
+    }
+    LaneConst<DIM, S> k;
+    k.g2 = cpair<S>(a.k.g2);
+    k.al = cpair<S>(a.k.al);
+    k.be = cpair<S>(a.k.be);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) k.ih[d] = cpair<S>(a.k.ih[d]);
+    const S mu = cpair<S>(a.k.mu), mu2 = cpair<S>(a.k.mu2);
+    const S lam = cpair<S>(a.k.lam), gcew = cpair<S>(a.k.gcew);
+    S gd[DIM][DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        S dummy;
+        lane_eval<DIM, S, false>(xv[c], n, k, dummy, gd[c]);
+    }
+    S dphi, gphi[DIM];
+    lane_eval<DIM, S, true>(xv[DIM], n, k, dphi, gphi);
+    const int64_t qbase = (int64_t)(n * NK) * g.n_cells + gid;
+    const S c0 = valid ? QData<S>::get(a.qd, qbase) : Scalar<S>::zero();
+    const S c1 = valid ? QData<S>::get(a.qd, qbase + (int64_t)(NK - 1) * g.n_cells) : Scalar<S>::zero();
+    S tr = gd[0][0];
+#pragma unroll
+    for (int i = 1; i < DIM; ++i) tr = tr + gd[i][i];
+    const S ltr = lam * tr;
+    S fu[DIM][DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = i; j < DIM; ++j) {
+            const S sg = (i == j) ? mu2 * gd[i][i] + ltr : mu * (gd[i][j] + gd[j][i]);
+            const S f = c0 * sg;
+            fu[i][j] = f;
+            fu[j][i] = f;
+        }
+    S fp = c1 * dphi;
+    if constexpr (!BLOCKDIAG) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = i; j < DIM; ++j) {
+                const S sp = valid ? QData<S>::get(a.qd, qbase + (int64_t)(1 + sidx<DIM>(i, j)) * g.n_cells)
+                                   : Scalar<S>::zero();
+                fp = fp + sp * ((i == j) ? gd[i][i] : gd[i][j] + gd[j][i]);
+            }
+    }
+    S out[NC];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) out[c] = lane_integrate<DIM, S, false>(Scalar<S>::zero(), fu[c], n, k);
+    S fg[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) fg[d] = gcew * gphi[d];
+    out[DIM] = lane_integrate<DIM, S, true>(fp, fg, n, k);
+    if (valid) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (!el[c]) atomicAdd(&a.y[c * nn + gn], Scalar<S>::store(out[c]));
+    }
+}
+
 template <int DIM, typename S, bool BLOCKDIAG>
 __global__ void __launch_bounds__(Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ, Q1Tile<DIM, S>::MINB)
 k_q1_apply(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
@@ -807,15 +906,17 @@ cudaError_t launch_q1_apply_batched(int dim, bool fp64, bool blockdiag, bool lan
 
 template <typename S, bool BD>
 static cudaError_t launch_lanes_dim(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, bool direct) {
     if (a.g.dim == 3) {
         using T = LaneTile<3>;
         dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, (a.g.nc[2] + T::TZ - 1) / T::TZ);
-        k_q1_apply_lanes<3, S, BD><<<grid, 256, 0, s>>>(a);
+        if (direct) k_q1_apply_direct<3, S, BD><<<grid, 256, 0, s>>>(a);
+        else k_q1_apply_lanes<3, S, BD><<<grid, 256, 0, s>>>(a);
     } else {
         using T = LaneTile<2>;
         dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, 1);
-        k_q1_apply_lanes<2, S, BD><<<grid, 256, 0, s>>>(a);
+        if (direct) k_q1_apply_direct<2, S, BD><<<grid, 256, 0, s>>>(a);
+        else k_q1_apply_lanes<2, S, BD><<<grid, 256, 0, s>>>(a);
     }
     return count_launch(cudaGetLastError());
 }
@@ -841,7 +942,8 @@ static void fill_consts(Q1ApplyArgs<St, QT>& a, const Phys& ph) {
 }
 
 cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s) {
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
+                              bool direct) {
     Q1ApplyArgs<double, float2> a;
     a.g = g;
     a.qd = qd;
@@ -850,12 +952,14 @@ cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, c
     a.mask = mask;
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
-    if (lanes) return blockdiag ? launch_lanes_dim<df64, true>(a, s) : launch_lanes_dim<df64, false>(a, s);
+    if (lanes || direct)
+        return blockdiag ? launch_lanes_dim<df64, true>(a, s, direct) : launch_lanes_dim<df64, false>(a, s, direct);
     return blockdiag ? launch_apply_dim<df64, true>(a, s) : launch_apply_dim<df64, false>(a, s);
 }
 
 cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s) {
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
+                              bool direct) {
     Q1ApplyArgs<float, float> a;
     a.g = g;
     a.qd = qd;
@@ -864,7 +968,8 @@ cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, co
     a.mask = mask;
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
-    if (lanes) return blockdiag ? launch_lanes_dim<float, true>(a, s) : launch_lanes_dim<float, false>(a, s);
+    if (lanes || direct)
+        return blockdiag ? launch_lanes_dim<float, true>(a, s, direct) : launch_lanes_dim<float, false>(a, s, direct);
     return blockdiag ? launch_apply_dim<float, true>(a, s) : launch_apply_dim<float, false>(a, s);
 }
 
@@ -876,6 +981,24 @@ cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, co
 // (d_d N_n(q))^2 = h_d^-2 prod_{e != d} A(n,q,e), N_n(q)^2 = prod_e A(n,q,e), with
 // A = ((1 + g)/2)^2 if node n and Gauss point q lie on the same side in direction e, else
 // ((1 - g)/2)^2.
+// Diagonal weights per m = n xor q (node n, Gauss point q), Q1, as (hi, lo) pairs:
+//   A[c][m] = mu Ws + (mu + lambda) W_c,  P[m] = prod_e a_e,  Wg[m] = Gc eps w Ws,
+// with a_e = ((1 + g)/2)^2 if bit e of m is clear else ((1 - g)/2)^2, W_d = a-product over e != d
+// divided by h_d^2 and Ws = sum_d W_d.  (Phi_n at q is prod_e ((1 +- g)/2); its derivative along d is
+// +-1/h_d times the product over the other axes.)
+struct DiagConsts {
+    float2 A[3][8];
+    float2 P[8];
+    float2 Wg[8];
+};
+
+// Residual constants: the linearisation constants plus p and 2 w Gc eps (pair sum of a gradient flux).
+struct ResConsts {
+    float2 cv[4], cg[3][3];
+    float2 w, omk, kap, f2k, p2, gce, mu, lam;
+    float2 p, wgce2;
+};
+
 namespace {
 template <int DIM>
 struct RDTile;
@@ -885,11 +1008,11 @@ template <> struct RDTile<2> { static constexpr int TX = 16, TY = 8, TZ = 1; };
 
 template <int DIM, int OP>
 __global__ void __launch_bounds__(RDTile<DIM>::TX * RDTile<DIM>::TY * RDTile<DIM>::TZ)
-k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __restrict__ pt,
-             const float2* __restrict__ q64, const uint8_t* __restrict__ mask, double* __restrict__ y, double gpt) {
+k_q1_resdiag(Geom g, ResConsts rk, DiagConsts dk, const double* __restrict__ U, const double* __restrict__ pt,
+             const float2* __restrict__ q64, const uint8_t* __restrict__ mask, double* __restrict__ y) {
     using T = RDTile<DIM>;
     using D = Q1Dims<DIM>;
-    constexpr int NV = D::NV, NC = D::NC, NK = D::NK;
+    constexpr int NV = D::NV, NC = D::NC, NK = D::NK, NH = NV / 2;
     constexpr int NCELL = T::TX * T::TY * T::TZ;
     constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = DIM == 3 ? T::TZ + 1 : 1;
     constexpr int NT = NTX * NTY * NTZ;
@@ -911,15 +1034,6 @@ k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __rest
         }
         __syncthreads();
     }
-    double vol = 1.0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) vol *= g.h[a];
-    const double w = vol / NV;
-    double gp[DIM + 1];
-    gp[0] = 1.0;
-#pragma unroll
-    for (int j = 1; j <= DIM; ++j) gp[j] = gp[j - 1] * gpt;
-
     const int cell = threadIdx.x;
     const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
     const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
@@ -931,137 +1045,162 @@ k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __rest
     if (valid) {
         const int64_t gid = (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk));
         if constexpr (OP == 1) {
-            const double Ap = 0.25 * (1.0 + gpt) * (1.0 + gpt), Am = 0.25 * (1.0 - gpt) * (1.0 - gpt);
-            const double gcew = ph.Gc * ph.eps * w;
+            // diag G~: for node n and Gauss point q the element weights depend on m = n xor q only
+            // (host tables); c0 and c1 are the stored df64 coefficients.
+            df64 acc[NV][NC];
+#pragma unroll
+            for (int n = 0; n < NV; ++n)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[n][c] = df_make(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 const float2 a0 = q64[(int64_t)(q * NK + 0) * g.n_cells + gid];
                 const float2 a1 = q64[(int64_t)(q * NK + NK - 1) * g.n_cells + gid];
-                const double c0 = (double)a0.x + (double)a0.y, c1 = (double)a1.x + (double)a1.y;
+                const df64 c0 = df_make(a0.x, a0.y), c1 = df_make(a1.x, a1.y);
 #pragma unroll
                 for (int n = 0; n < NV; ++n) {
                     const int m = n ^ q;
-                    double P = 1.0, Wd[DIM], Ws = 0.0;
 #pragma unroll
-                    for (int e = 0; e < DIM; ++e) P *= (m >> e) & 1 ? Am : Ap;
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        double f = 1.0 / (g.h[d] * g.h[d]);
-#pragma unroll
-                        for (int e = 0; e < DIM; ++e)
-                            if (e != d) f *= (m >> e) & 1 ? Am : Ap;
-                        Wd[d] = f;
-                        Ws += f;
-                    }
-#pragma unroll
-                    for (int c = 0; c < DIM; ++c) el[n][c] += c0 * (ph.mu * Ws + (ph.mu + ph.lam) * Wd[c]);
-                    el[n][DIM] += c1 * P + gcew * Ws;
+                    for (int c = 0; c < DIM; ++c) acc[n][c] = acc[n][c] + c0 * dfc(dk.A[c][m]);
+                    acc[n][DIM] = acc[n][DIM] + c1 * dfc(dk.P[m]) + dfc(dk.Wg[m]);
                 }
             }
+#pragma unroll
+            for (int n = 0; n < NV; ++n)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) el[n][c] = df_to_double(acc[n][c]);
         } else {
-            const double sE = g.es ? g.es[gid] : 1.0;
-            const double cmu = ph.mu * sE, clam = ph.lam * sE;
+            // -A(U) in df64 (Eq. (semilinear)): u-rows (g(phi~) sigma(u) + phi~^2 p I) : grad Phi,
+            // phi-rows (f g'(phi) E_s + 2 phi p div u - Gc/eps (1 - phi)) Phi + Gc eps grad phi . grad Phi.
+            // Gauss-point values by inverse butterflies; integration by the transposed (forward)
+            // butterflies; a Q1 derivative is constant along its own axis.
+            const df64 sE = g.es ? df_from_double(g.es[gid]) : df_make(1.f, 0.f);
+            const df64 cmu = dfc(rk.mu) * sE, clam = dfc(rk.lam) * sE;
+            const df64 w = dfc(rk.w), omk = dfc(rk.omk), kap = dfc(rk.kap), f2k = dfc(rk.f2k), p2 = dfc(rk.p2);
             const int tb = li + NTX * (lj + NTY * lk);
-            double m_[NC + 1][NV];
+            auto off = [](int n) { return (n & 1) + NTX * (((n >> 1) & 1) + NTY * (DIM == 3 ? (n >> 2) & 1 : 0)); };
+            df64 vphi[NV], vpt[NV];
 #pragma unroll
-            for (int c = 0; c <= NC; ++c) {
-#pragma unroll
-                for (int n = 0; n < NV; ++n) {
-                    const int off = (n & 1) + NTX * (((n >> 1) & 1) + NTY * (DIM == 3 ? (n >> 2) & 1 : 0));
-                    m_[c][n] = sv[c * NT + tb + off];
-                }
-                fwd<DIM>(m_[c]);
+            for (int n = 0; n < NV; ++n) {
+                vphi[n] = df_from_double(sv[DIM * NT + tb + off(n)]);
+                vpt[n] = df_from_double(sv[NC * NT + tb + off(n)]);
             }
-            double H[NC][DIM][NV / 2], F[NV];
+            fwd<DIM>(vphi);
+            fwd<DIM>(vpt);
+            df64 Hp[DIM][NH];       // phi-row gradient part, already integrated
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
+            for (int d = 0; d < DIM; ++d) {
+                int jj = 0;
+#pragma unroll
+                for (int kp = 0; kp < NV; ++kp) {
+                    if (kp & (1 << d)) continue;
+                    Hp[d][jj] = vphi[kp | (1 << d)] * dfc(rk.cg[d][popc(kp)]);
+                    ++jj;
+                }
+                // the flux -w Gc eps dphi/dx_d is constant along d (the pair sum over q doubles it,
+                // wgce2 = 2 w Gc eps); integrating it over the other axes is the forward butterfly of
+                // the inverse one, i.e. a factor 2^(d-1)
+#pragma unroll
+                for (int t = 0; t < NH; ++t) Hp[d][t] = df_scale(Hp[d][t] * dfc(rk.wgce2), -(float)NH);
+            }
+#pragma unroll
+            for (int m = 0; m < NV; ++m) {
+                vphi[m] = vphi[m] * dfc(rk.cv[popc(m)]);
+                vpt[m] = vpt[m] * dfc(rk.cv[popc(m)]);
+            }
+            inv<DIM>(vphi);
+            inv<DIM>(vpt);
+            df64 gd[DIM][DIM][NH];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                df64 m_[NV];
+#pragma unroll
+                for (int n = 0; n < NV; ++n) m_[n] = df_from_double(sv[c * NT + tb + off(n)]);
+                fwd<DIM>(m_);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    int jj = 0;
+#pragma unroll
+                    for (int kp = 0; kp < NV; ++kp) {
+                        if (kp & (1 << d)) continue;
+                        gd[c][d][jj] = m_[kp | (1 << d)] * dfc(rk.cg[d][popc(kp)]);
+                        ++jj;
+                    }
+                    inv<DIM - 1>(gd[c][d]);
+#pragma unroll
+                    for (int t = 0; t < NH; ++t) gd[c][d][t] = df_renorm(gd[c][d][t]);
+                }
+            }
+            df64 ps[DIM][DIM][NH], fv[NV];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c)
 #pragma unroll
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll
-                    for (int j = 0; j < NV / 2; ++j) H[c][d][j] = 0.0;
-#pragma unroll
-            for (int k = 0; k < NV; ++k) F[k] = 0.0;
+                    for (int t = 0; t < NH; ++t) ps[c][d][t] = df_make(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                double gu[DIM][DIM], gphi[DIM], phi = 0.0, ptv = 0.0;
+                df64 gu[DIM][DIM];
 #pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    const double sc = sgn(k, q) * gp[popc(k)] / NV;
-                    phi += sc * m_[DIM][k];
-                    ptv += sc * m_[NC][k];
+                for (int c = 0; c < DIM; ++c)
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) gu[c][d] = gd[c][d][(q & ((1 << d) - 1)) | ((q >> (d + 1)) << d)];
+                df64 e[DIM][DIM], tr = gu[0][0], ee = gu[0][0] * gu[0][0];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    e[a][a] = gu[a][a];
+                    if (a > 0) { tr = tr + gu[a][a]; ee = ee + gu[a][a] * gu[a][a]; }
+#pragma unroll
+                    for (int b = a + 1; b < DIM; ++b) {
+                        e[a][b] = df_scale(gu[a][b] + gu[b][a], 0.5f);
+                        e[b][a] = e[a][b];
+                        ee = ee + df_scale(e[a][b] * e[a][b], 2.f);
+                    }
                 }
+                tr = df_renorm(tr);
+                const df64 Es = df_scale(clam * tr * tr, 0.5f) + cmu * ee;
+                const df64 phi = df_renorm(vphi[q]), ptv = df_renorm(vpt[q]);
+                const df64 gk = omk * ptv * ptv + kap;
+                const df64 wg = w * gk, wp = w * ptv * ptv * dfc(rk.p);
+                const df64 ltr = clam * tr;
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
+                for (int a = 0; a < DIM; ++a)
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        double acc = 0.0;
-#pragma unroll
-                        for (int kp = 0; kp < NV; ++kp) {
-                            if (kp & (1 << d)) continue;
-                            acc += sgn(kp, q) * gp[popc(kp)] * m_[c][kp | (1 << d)];
-                        }
-                        acc *= 2.0 / (g.h[d] * NV);
-                        if (c < DIM) gu[c][d] = acc; else gphi[d] = acc;
+                    for (int b = 0; b < DIM; ++b) {
+                        df64 sg = df_scale(cmu * e[a][b], 2.f);
+                        if (a == b) sg = sg + ltr;
+                        df64 f = wg * sg;
+                        if (a == b) f = f + wp;
+                        const int jq = (q & ((1 << b) - 1)) | ((q >> (b + 1)) << b);
+                        ps[a][b][jq] = ps[a][b][jq] - f;
                     }
-                double e[DIM][DIM], tr = 0.0, ee = 0.0;
-#pragma unroll
-                for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                    for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
-#pragma unroll
-                for (int i = 0; i < DIM; ++i) tr += e[i][i];
-#pragma unroll
-                for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                    for (int j = 0; j < DIM; ++j) ee += e[i][j] * e[i][j];
-                const double Es = 0.5 * clam * tr * tr + cmu * ee;
-                const double gk = (1.0 - ph.kappa) * ptv * ptv + ph.kappa;
-                // -A(U): u-rows g(phi~) sigma(u) + phi~^2 p I; phi-rows f g'(phi) E_s + 2 phi p div u
-                // - Gc/eps (1 - phi); gradient part Gc eps grad phi
-                double fl[NC][DIM];
-#pragma unroll
-                for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                    for (int j = 0; j < DIM; ++j)
-                        fl[i][j] = -w * (gk * (2.0 * cmu * e[i][j] + (i == j ? clam * tr : 0.0)) +
-                                         (i == j ? ptv * ptv * ph.p : 0.0));
-#pragma unroll
-                for (int j = 0; j < DIM; ++j) fl[DIM][j] = -w * ph.Gc * ph.eps * gphi[j];
-                const double fv = -w * (ph.f * 2.0 * (1.0 - ph.kappa) * phi * Es + 2.0 * phi * ph.p * tr -
-                                        ph.Gc / ph.eps * (1.0 - phi));
-#pragma unroll
-                for (int k = 0; k < NV; ++k) F[k] += sgn(k, q) * fv;
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        int j = 0;
-#pragma unroll
-                        for (int kp = 0; kp < NV; ++kp) {
-                            if (kp & (1 << d)) continue;
-                            H[c][d][j] += sgn(kp, q) * fl[c][d];
-                            ++j;
-                        }
-                    }
+                // value part of the phi rows: -w (f g'(phi) E_s + 2 p phi tr - Gc/eps (1 - phi))
+                const df64 one_m = df_make(1.f, 0.f) - phi;
+                fv[q] = w * (dfc(rk.gce) * one_m - f2k * phi * Es - p2 * phi * tr);
             }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                double Y[NV];
+            for (int c = 0; c < DIM; ++c)
 #pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    double acc = (c == DIM) ? F[k] * gp[popc(k)] / NV : 0.0;
+                for (int d = 0; d < DIM; ++d) fwd<DIM - 1>(ps[c][d]);
+            fwd<DIM>(fv);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                df64 Y[NV];
+#pragma unroll
+                for (int kk = 0; kk < NV; ++kk) {
+                    df64 acc = (c == DIM) ? fv[kk] * dfc(rk.cv[popc(kk)]) : df_make(0.f, 0.f);
 #pragma unroll
                     for (int d = 0; d < DIM; ++d) {
-                        if (!(k & (1 << d))) continue;
-                        const int kp = k & ~(1 << d);
-                        const int j = (kp & ((1 << d) - 1)) | ((kp >> (d + 1)) << d);
-                        acc += H[c][d][j] * gp[popc(kp)] * (2.0 / (g.h[d] * NV));
+                        if (!(kk & (1 << d))) continue;
+                        const int kp = kk & ~(1 << d);
+                        const int jj = (kp & ((1 << d) - 1)) | ((kp >> (d + 1)) << d);
+                        acc = acc + (c < DIM ? ps[c][d][jj] : Hp[d][jj]) * dfc(rk.cg[d][popc(kp)]);
                     }
-                    Y[k] = acc;
+                    Y[kk] = acc;
                 }
                 inv<DIM>(Y);
 #pragma unroll
-                for (int n = 0; n < NV; ++n) el[n][c] = Y[n];
+                for (int n = 0; n < NV; ++n) el[n][c] = df_to_double(Y[n]);
             }
         }
     }
@@ -1102,18 +1241,55 @@ k_q1_resdiag(Geom g, Phys ph, const double* __restrict__ U, const double* __rest
     }
 }
 
+static ResConsts make_res_consts(const Geom& g, const Phys& ph) {
+    ResConsts k;
+    fill_lin_consts(g, ph, k);
+    double vol = 1.0;
+    for (int d = 0; d < g.dim; ++d) vol *= g.h[d];
+    k.p = split_pair(ph.p);
+    k.wgce2 = split_pair(2.0 * ph.Gc * ph.eps * vol / (1 << g.dim));
+    return k;
+}
+
+static DiagConsts make_diag_consts(const Geom& g, const Phys& ph) {
+    DiagConsts k;
+    memset(&k, 0, sizeof(k));
+    const int dim = g.dim, NV = 1 << dim;
+    const double gpt = 1.0 / sqrt(3.0);
+    const double Ap = 0.25 * (1.0 + gpt) * (1.0 + gpt), Am = 0.25 * (1.0 - gpt) * (1.0 - gpt);
+    double vol = 1.0;
+    for (int d = 0; d < dim; ++d) vol *= g.h[d];
+    const double gcew = ph.Gc * ph.eps * vol / NV;
+    for (int m = 0; m < NV; ++m) {
+        double P = 1.0, Wd[3] = {0.0, 0.0, 0.0}, Ws = 0.0;
+        for (int e = 0; e < dim; ++e) P *= (m >> e) & 1 ? Am : Ap;
+        for (int d = 0; d < dim; ++d) {
+            double f = 1.0 / (g.h[d] * g.h[d]);
+            for (int e = 0; e < dim; ++e)
+                if (e != d) f *= (m >> e) & 1 ? Am : Ap;
+            Wd[d] = f;
+            Ws += f;
+        }
+        for (int c = 0; c < dim; ++c) k.A[c][m] = split_pair(ph.mu * Ws + (ph.mu + ph.lam) * Wd[c]);
+        k.P[m] = split_pair(P);
+        k.Wg[m] = split_pair(gcew * Ws);
+    }
+    return k;
+}
+
 template <int OP>
 static cudaError_t launch_resdiag(const Geom& g, const Phys& ph, const double* U, const double* pt,
                                   const float2* q64, const uint8_t* mask, double* y, cudaStream_t s) {
-    const double gpt = 1.0 / sqrt(3.0);
+    const DiagConsts dk = make_diag_consts(g, ph);
+    const ResConsts rk = make_res_consts(g, ph);
     if (g.dim == 3) {
         using T = RDTile<3>;
         dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
-        k_q1_resdiag<3, OP><<<grid, T::TX * T::TY * T::TZ, 0, s>>>(g, ph, U, pt, q64, mask, y, gpt);
+        k_q1_resdiag<3, OP><<<grid, T::TX * T::TY * T::TZ, 0, s>>>(g, rk, dk, U, pt, q64, mask, y);
     } else {
         using T = RDTile<2>;
         dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, 1);
-        k_q1_resdiag<2, OP><<<grid, T::TX * T::TY, 0, s>>>(g, ph, U, pt, q64, mask, y, gpt);
+        k_q1_resdiag<2, OP><<<grid, T::TX * T::TY, 0, s>>>(g, rk, dk, U, pt, q64, mask, y);
     }
     return count_launch(cudaGetLastError());
 }

@@ -39,9 +39,11 @@ cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, 
 // lanes = true: one thread per (cell, Gauss point) with shuffle butterflies; false: one thread
 // per cell with the modal form in registers
 cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s);
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
+                              bool direct = false);
 cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
-                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s);
+                              const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
+                              bool direct = false);
 
 // -A(U) on a Q1 level (R zeroed by the caller) and diag(G~) on free rows (eliminated rows preset)
 cudaError_t launch_q1_residual(const Geom& g, const Phys& ph, const double* U, const double* pt, double* R,

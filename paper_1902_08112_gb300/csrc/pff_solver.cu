@@ -48,7 +48,8 @@ static cudaEvent_t next_event(pff_hierarchy* h) {
 }
 
 template <typename T>
-cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int phi_bits) {
+cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int phi_bits, bool preset) {
+    CK(refresh_state(h));
     Level& L = h->lv[l];
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof_on) {
@@ -56,15 +57,15 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
         e1 = next_event(h);
         if (e0 && e1) CK(cudaEventRecord(e0, h->stream));
     }
-    CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, phi_bits, x, y, T(0), h->stream));
+    if (preset) CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, phi_bits, x, y, T(0), h->stream));
     if (h->fast_q1 && L.g.deg == 1 && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
         const bool bd = op == OP_APPLY_BLOCKDIAG;
         if constexpr (sizeof(T) == 8)
             CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd,
-                                 (h->q1_style & 1) != 0, h->stream));
+                                 (h->q1_style & 1) != 0, h->stream, (h->q1_style & 4) != 0));
         else
             CK(launch_q1_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd,
-                                 (h->q1_style & 2) != 0, h->stream));
+                                 (h->q1_style & 2) != 0, h->stream, (h->q1_style & 8) != 0));
     } else {
         CellArgs<T> a;
         a.g = L.g;
@@ -86,11 +87,12 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
     }
     return cudaSuccess;
 }
-template cudaError_t apply_level<double>(pff_hierarchy*, int, int, const double*, double*, int);
-template cudaError_t apply_level<float>(pff_hierarchy*, int, int, const float*, float*, int);
+template cudaError_t apply_level<double>(pff_hierarchy*, int, int, const double*, double*, int, bool);
+template cudaError_t apply_level<float>(pff_hierarchy*, int, int, const float*, float*, int, bool);
 
 template <typename T>
 cudaError_t diagonal_level(pff_hierarchy* h, int l, T* d) {
+    CK(refresh_state(h));
     Level& L = h->lv[l];
     CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, PHI_BITS_ALL, (const T*)nullptr, d, T(1), h->stream));
     if constexpr (sizeof(T) == 8) {
@@ -131,7 +133,12 @@ cudaError_t residual_fine(pff_hierarchy* h, double* R) {
 }
 
 // Fine state -> all coarser levels (coincident nodes) and FP32 copies.
+cudaError_t refresh_state(pff_hierarchy* h) {
+    return h->derived_dirty ? propagate_state(h, true) : cudaSuccess;
+}
+
 cudaError_t propagate_state(pff_hierarchy* h, bool values) {
+    if (values) h->derived_dirty = false;
     for (int l = h->L - 2; l >= 0; --l) {
         Level& C = h->lv[l];
         Level& F = h->lv[l + 1];
@@ -284,6 +291,7 @@ void drop_graph(pff_hierarchy* h) {
 }
 
 cudaError_t setup(pff_hierarchy* h) {
+    CK(refresh_state(h));
     cudaStream_t s = h->stream;
     drop_graph(h);
     const bool f32 = h->prm.mg_precision == 32;
@@ -352,14 +360,15 @@ static cudaError_t cheb_run(pff_hierarchy* h, int l, T* r, T* x, const ChebCoef&
     T* d = work<T>(L, 3);
     T* t = work<T>(L, 4);
     const int k = (int)std::max(cu.c2.size(), cp.c2.size());
-    // first step
+    // first step; every update except the last also presets t for the next apply
     CK(launch_cheb_update<T>(L.g, r, (const T*)nullptr, d, dinv<T>(L), x, 0.0, 0.0, cu.c2[0], cp.c2[0], mode,
-                             h->stream));
+                             h->stream, L.mask, k > 1 ? t : (T*)nullptr));
     for (int st = 1; st < k; ++st) {
-        CK(apply_level<T>(h, l, OP_APPLY_BLOCKDIAG, d, t, PHI_BITS_ALL));
+        CK(apply_level<T>(h, l, OP_APPLY_BLOCKDIAG, d, t, PHI_BITS_ALL, false));
         const bool uon = st < (int)cu.c2.size(), pon = st < (int)cp.c2.size();
         CK(launch_cheb_update<T>(L.g, r, t, d, dinv<T>(L), x, uon ? cu.c1[st] : 0.0, pon ? cp.c1[st] : 0.0,
-                                 uon ? cu.c2[st] : 0.0, pon ? cp.c2[st] : 0.0, 0, h->stream));
+                                 uon ? cu.c2[st] : 0.0, pon ? cp.c2[st] : 0.0, 0, h->stream, L.mask,
+                                 st + 1 < k ? t : (T*)nullptr));
     }
     return cudaSuccess;
 }
@@ -490,6 +499,7 @@ static cudaError_t vcycle_body(pff_hierarchy* h) {
 }
 
 cudaError_t vcycle(pff_hierarchy* h, const double* r, double* z) {
+    CK(refresh_state(h));
     Level& F = h->lv[h->L - 1];
     const int64_t nd = n_dofs(F.g);
     if (h->prm.mg_precision == 32) {

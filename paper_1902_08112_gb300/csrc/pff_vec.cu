@@ -237,38 +237,47 @@ template cudaError_t launch_invert_diag<float>(float*, int64_t, cudaStream_t);
 //   first = 1:  d = c2[b] * dinv * r,  x = d                 (d_0 = z_0 / theta)
 //   first = 2:  d = c2[b] * dinv * r,  x += d
 //   first = 0:  r -= t;  d = c1[b] d + c2[b] dinv r;  x += d
+// With tn != nullptr the update also writes the preset of the next operator apply t = G d into tn
+// (d on eliminated rows, 0 elsewhere), so that apply need not launch its own preset.
 template <typename T>
-__global__ void k_cheb_update(int64_t nn, int dim, T* __restrict__ r, const T* __restrict__ t, T* __restrict__ d,
-                              const T* __restrict__ dinv, T* __restrict__ x, T c1u, T c1p, T c2u, T c2p, int first) {
+__global__ void k_cheb_update(int64_t nn, int dim, T* __restrict__ r, const T* t, T* __restrict__ d,
+                              const T* __restrict__ dinv, T* __restrict__ x, T c1u, T c1p, T c2u, T c2p, int first,
+                              const uint8_t* __restrict__ mask, T* tn) {
     const int64_t nd = nn * (dim + 1);
     const int64_t nu = nn * dim;
     GRID_STRIDE(i, nd) {
         const bool u = i < nu;
         const T c1 = u ? c1u : c1p, c2 = u ? c2u : c2p;
+        T di;
         if (first) {
-            const T di = c2 * dinv[i] * r[i];
-            d[i] = di;
+            di = c2 * dinv[i] * r[i];
             x[i] = first == 1 ? di : x[i] + di;
         } else {
             const T ri = r[i] - t[i];
             r[i] = ri;
-            const T di = c1 * d[i] + c2 * dinv[i] * ri;
-            d[i] = di;
+            di = c1 * d[i] + c2 * dinv[i] * ri;
             x[i] += di;
+        }
+        d[i] = di;
+        if (tn) {
+            const int c = dof_comp(i, nn);
+            tn[i] = elim_dof(mask[i - c * nn], c, dim) ? di : T(0);
         }
     }
 }
 template <typename T>
 cudaError_t launch_cheb_update(const Geom& g, T* r, const T* t, T* d, const T* dinv, T* x, double c1u, double c1p,
-                               double c2u, double c2p, int first, cudaStream_t s) {
+                               double c2u, double c2p, int first, cudaStream_t s, const uint8_t* mask, T* tn) {
     k_cheb_update<T><<<grid_for(n_dofs(g)), kThreads, 0, s>>>(g.n_nodes, g.dim, r, t, d, dinv, x, (T)c1u, (T)c1p,
-                                                              (T)c2u, (T)c2p, first);
+                                                              (T)c2u, (T)c2p, first, mask, tn);
     return count_launch(cudaGetLastError());
 }
 template cudaError_t launch_cheb_update<double>(const Geom&, double*, const double*, double*, const double*, double*,
-                                                double, double, double, double, int, cudaStream_t);
+                                                double, double, double, double, int, cudaStream_t, const uint8_t*,
+                                                double*);
 template cudaError_t launch_cheb_update<float>(const Geom&, float*, const float*, float*, const float*, float*,
-                                               double, double, double, double, int, cudaStream_t);
+                                               double, double, double, double, int, cudaStream_t, const uint8_t*,
+                                               float*);
 
 template <typename T>
 __global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
@@ -316,7 +325,7 @@ __global__ void k_mask_copy(int64_t nn, int dim, const uint8_t* __restrict__ mas
                             T* __restrict__ dst, int free_only) {
     const int64_t nd = nn * (dim + 1);
     GRID_STRIDE(i, nd) {
-        const int c = (int)(i / nn);
+        const int c = dof_comp(i, nn);
         const bool e = elim_dof(mask[i - c * nn], c, dim);
         if (free_only) dst[i] = e ? T(0) : src[i];
         else if (e) dst[i] = src[i];
@@ -405,7 +414,7 @@ __global__ void k_start_vector(int64_t nn, int dim, const uint8_t* __restrict__ 
                                T* __restrict__ v) {
     const int64_t nd = nn * (dim + 1);
     GRID_STRIDE(i, nd) {
-        const int c = (int)(i / nn);
+        const int c = dof_comp(i, nn);
         const uint64_t key = seed + (uint64_t)level * (1ull << 40) + (uint64_t)i;
         const double u = (double)(splitmix64(key) >> 11) * 0x1.0p-53;
         v[i] = elim_dof(mask[i - c * nn], c, dim) ? T(0) : T(2.0 * u - 1.0);
@@ -620,7 +629,7 @@ __global__ void k_newton_rhs(Geom g, const double* __restrict__ R, const double*
                              const uint8_t* __restrict__ mask, double* __restrict__ Rt) {
     const int64_t nn = g.n_nodes, nd = nn * (g.dim + 1);
     GRID_STRIDE(i, nd) {
-        const int c = (int)(i / nn);
+        const int c = dof_comp(i, nn);
         const int64_t n = i - c * nn;
         const uint8_t m = mask[n];
         double v;

@@ -193,15 +193,22 @@ def initial_phase_field(w: Workload) -> np.ndarray:
     dim = w.dim
     n = np.array(w.n_cells)
     edge = (np.array(w.hi) - np.array(w.lo)) / n
-    cidx = np.indices(tuple(n[::-1])).reshape(dim, -1)[::-1].T     # (ncell, dim), x fastest
-    lo = np.array(w.lo)[None, :] + cidx * edge[None, :]
-    hi = lo + edge[None, :]
-    hit = np.zeros(cidx.shape[0], dtype=bool)
+    hits = []
     for cr in w.cracks:
-        hit |= _cell_meets_crack(lo, hi, cr, w.h, dim)
+        # only cells inside the crack region's bounding box (centre +- (radius + half-thickness))
+        reach = cr.radius + cr.half_width * w.h
+        c = np.asarray(cr.center[:dim], dtype=np.float64)
+        i0 = np.clip(np.floor((c - reach - np.array(w.lo)) / edge).astype(int) - 1, 0, n - 1)
+        i1 = np.clip(np.floor((c + reach - np.array(w.lo)) / edge).astype(int) + 1, 0, n - 1)
+        axes = [np.arange(i0[a], i1[a] + 1) for a in range(dim)]
+        grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+        cidx = np.stack([g.ravel() for g in grids], axis=1)
+        lo = np.array(w.lo)[None, :] + cidx * edge[None, :]
+        hi = lo + edge[None, :]
+        hits.append(cidx[_cell_meets_crack(lo, hi, cr, w.h, dim)])
     phi = np.ones(w.n_nodes)
     npa = np.array(w.nodes_per_axis())
-    hc = cidx[hit]
+    hc = np.concatenate(hits, axis=0) if hits else np.zeros((0, dim), dtype=int)
     strides = np.cumprod(np.concatenate([[1], npa[:-1]]))
     for off in np.ndindex(*([w.deg + 1] * dim)):
         node = ((hc * w.deg + np.array(off)[None, :]) * strides[None, :]).sum(axis=1)

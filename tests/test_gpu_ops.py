@@ -64,7 +64,8 @@ class Case:
 
 
 # (workload, kernel variant): 0 = Q1 fast path (df64 / FP32 with stored linearisation data),
-# 1 = generic kernels.  Sizes span several tiles with ragged edges.
+# 1 = generic kernels, 2 = one thread per Gauss point, 3 = one thread per cell, 5 = Gauss-point
+# lanes adding to y with global atomics.  Sizes span several tiles with ragged edges.
 CASES = {
     "2d_q1": (lambda: W.small(W.config_2d_single_crack(), 40, 3), 0),
     "2d_q1_generic": (lambda: W.small(W.config_2d_single_crack(), 24, 3), 1),
@@ -76,6 +77,8 @@ CASES = {
     "2d_q1_lanes": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 2),
     "2d_q1_percell": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 3),
     "3d_q2": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1),
+    "3d_q1_direct": (lambda: W.small(W.config_3d_penny(), 12, 2), 5),
+    "2d_q1_direct": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 5),
     # spatially varying modulus (per-cell factor from a smooth seeded field)
     "3d_q1_modulus": (lambda: W.small(W.config_3d_penny(), 20, 3), 0, True),
     "3d_q1_lanes_modulus": (lambda: W.small(W.config_3d_penny(), 12, 2), 2, True),
