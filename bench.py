@@ -40,8 +40,8 @@ def _peaks():
 
 
 # DRAM bytes per cell of the FP64-accurate apply k_q1_apply_direct<3, df64, 0> from one ncu capture
-# at 64^3 (bytes per launch / 262,144 cells); None until a capture of the current kernel exists
-TRAFFIC_DF64_PER_CELL = None
+# at 64^3 (158.6 MB per launch over 262,144 cells): the df64 Gauss-point data plus x, mask and y
+TRAFFIC_DF64_PER_CELL = 158.613248e6 / 262144
 
 
 def _nvtx(name: str, push: bool):

@@ -90,6 +90,10 @@ typedef struct {
  *  coarse_rtol, coarse_maxit  Chebyshev coarse solver: steps from the Chebyshev error bound
  *                 for this reduction, capped (Sec. 3.2.2 gives neither).
  *  seed           seed of the SplitMix64 start vector of the CG eigenvalue estimate.
+ *  split          0: no split of the elastic energy (E_s^+ = E_s, default); 1: Miehe split (Sec. 2.1):
+ *                 E_s^+ = lambda/2 <tr e>_+^2 + mu tr(e_+^2) over the strain eigenvalues, sigma^+ its
+ *                 derivative; g(phi) degrades only the + part.  Operators then run in the generic
+ *                 kernels (any degree); batches require 0.
  *  preconditioner 0: P_full = MG(G~), the monolithic V-cycle (Sec. 3.3, default);
  *                 1: P_diag = blockdiag(MG(U~), MG(P~)) (Sec. 3.3): the coupling G_phiu is
  *                 left out of every V-cycle residual and of the coarse solve.  Batches
@@ -107,6 +111,7 @@ typedef struct {
     int coarse_maxit;
     uint64_t seed;
     int preconditioner;
+    int split;
 } pff_params;
 
 typedef struct {
@@ -126,7 +131,7 @@ typedef struct {
 
 /* Fill *p with the defaults quoted above (E=1, nu=0.2, Gc=1, kappa=1e-10, eps=1, p=1e-3,
  * c=100, eps_as=1e-10, f=1, FP32 V-cycle, degree 4, 10 CG steps, 1.2, 0.2, 1e-6, 200, 12345,
- * P_full). */
+ * P_full, no split). */
 void pff_default_params(pff_params* p);
 
 /* Create the level hierarchy (Sec. 3.2 and 4.2) on the current CUDA device.  cuda_stream is a
@@ -194,9 +199,9 @@ pff_status pff_update_active_set(pff_hierarchy* h, int* n_active, int* n_changed
  * (FP64, device output of n_dofs). */
 pff_status pff_residual(pff_hierarchy* h, double* R);
 
-/* Bulk energy int g(phi) E_s(e(u)) + phi^2 p div u and crack energy
- * int Gc/2 ((1 - phi)^2 / eps + eps |grad phi|^2) of Sec. 5 (no stress split) at the current fine
- * state, FP64, Q1 meshes.  out (host): [bulk, crack].  Synchronises. */
+/* Bulk energy int g(phi) E_s^+(e(u)) + E_s^-(e(u)) + phi^2 p div u and crack energy
+ * int Gc/2 ((1 - phi)^2 / eps + eps |grad phi|^2) of Sec. 5 at the current fine state (E_s^+ = E_s
+ * without split), FP64, Q1 meshes.  out (host): [bulk, crack].  Synchronises. */
 pff_status pff_energies(pff_hierarchy* h, double out[2]);
 
 /* Boundary load of Sec. 5, L_c = int_Gamma (sigma n)_c ds over one face of the box, evaluated as
@@ -290,7 +295,7 @@ pff_status pff_load_step(pff_hierarchy* h, double* U, const double* phi_prev, do
 
 /* ---- Batches of independent instances (one launch per level and operation across instances).
  * A batch is a view over n existing hierarchies created on the same stream, all Q1 with the same
- * dimension, mg_precision 32, preconditioner 0 and cheb_degree; instances may differ in mesh size, number of levels
+ * dimension, mg_precision 32, preconditioner 0, split 0 and cheb_degree; instances may differ in mesh size, number of levels
  * and physical parameters.  The batch owns only descriptor tables and reduction scratch; the
  * hierarchies keep their data (a hierarchy may belong to several batches, but batches that share a
  * hierarchy must not run concurrently).  Per-instance results equal those of the single-instance

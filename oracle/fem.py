@@ -43,7 +43,7 @@ class _Mesh(ctypes.Structure):
 class _Phys(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("lam", ctypes.c_double), ("Gc", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_double),
-                ("f", ctypes.c_double), ("escale", ctypes.POINTER(ctypes.c_double))]
+                ("f", ctypes.c_double), ("escale", ctypes.POINTER(ctypes.c_double)), ("split", ctypes.c_int)]
 
 
 _lib = None
@@ -141,11 +141,12 @@ class Phys:
     p: float = 1e-3
     f: float = 1.0            # factor on the phi-equation elastic term (1 = energy consistent)
     escale: np.ndarray | None = None   # per cell factor on E (n_cells, x fastest), None = uniform
+    split: int = 0            # 0: E_s^+ = E_s (no split); 1: Miehe split (Sec. 2.1)
     extra: dict = field(default_factory=dict)
 
     def c(self) -> _Phys:
         mu, lam = lame(self.E, self.nu)
-        ph = _Phys(mu, lam, self.Gc, self.kappa, self.eps, self.p, self.f, None)
+        ph = _Phys(mu, lam, self.Gc, self.kappa, self.eps, self.p, self.f, None, int(self.split))
         if self.escale is not None:
             arr = np.ascontiguousarray(self.escale, dtype=np.float64)
             ph.escale = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

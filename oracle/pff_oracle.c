@@ -18,7 +18,10 @@
  *     energy), used only as a finite-difference pin,
  *   - the Gauss-Lobatto lumped mass of the remark after Algorithm 1,
  *   - optionally a Young's modulus that varies per cell (E = s_cell E_0, Sec. 5.2 uses a
- *     spatially varying E): mu and lambda of a cell are scaled by s_cell.
+ *     spatially varying E): mu and lambda of a cell are scaled by s_cell,
+ *   - optionally the Miehe split of the elastic energy (Sec. 2.1): E_s^+ from the positive parts
+ *     of tr(e) and of the strain eigenvalues, sigma^+ = dE_s^+/de, degraded by g while
+ *     E_s^- = E_s - E_s^+ and sigma^- = sigma - sigma^+ are not.
  *
  * Notation: d = dim, comps 0..d-1 = displacement u, comp d = phase field phi.
  * DoF index = comp * n_nodes + node, node lexicographic with x fastest.
@@ -41,6 +44,7 @@ typedef struct {
     double Gc, kappa, eps, p;
     double f;          /* factor on the phi-equation elastic term: 1 = energy consistent */
     const double *escale;  /* per cell factor on mu and lam (n_cells), NULL = uniform */
+    int split;             /* 0: no split (E_s^+ = E_s); 1: Miehe split */
 } om_phys;
 
 /* The physics of one cell: mu and lam scaled by the cell's modulus factor. */
@@ -211,6 +215,98 @@ static double elastic_energy(const om_phys *ph, int d, double e[3][3]) {
     return 0.5 * ph->lam * tr * tr + ph->mu * ee;
 }
 
+/* ---------------------------------------------------------------- Miehe split (Sec. 2.1) */
+
+/* Eigen-decomposition a = V diag(l) V^T of a symmetric 3x3 matrix by cyclic Jacobi rotations
+ * (Golub and Van Loan, Matrix Computations, Sec. 8.5); the columns of V are the eigenvectors. */
+static void sym_eig3(double a_in[3][3], double l[3], double V[3][3]) {
+    double a[3][3];
+    memcpy(a, a_in, sizeof(a));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off == 0.0 || off <= 1e-36 * dia) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                /* rotation J in the (p, q) plane that zeroes a[p][q] in J^T a J */
+                double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 3; ++k) {      /* a <- a J */
+                    double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - sn * akq;
+                    a[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {      /* a <- J^T a */
+                    double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - sn * aqk;
+                    a[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {      /* V <- V J */
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i) l[i] = a[i][i];
+}
+
+/* <x>_+ = max(0, x) and its derivative, taken as 0 at x = 0. */
+static double posp(double x) { return x > 0.0 ? x : 0.0; }
+static double heav(double x) { return x > 0.0 ? 1.0 : 0.0; }
+
+typedef struct {
+    double l[3], V[3][3];   /* eigenvalues and eigenvectors (columns) of e */
+    double tr;              /* tr(e) */
+} om_eig;
+
+/* sigma^+ = lambda <tr e>_+ I + 2 mu e_+ and E_s^+ = lambda/2 <tr e>_+^2 + mu tr(e_+^2), with
+ * e_+ = sum_a <l_a>_+ n_a n_a^T.  In 2D (plane strain) e is the 3x3 strain with e_zz = 0. */
+static void miehe_split(const om_phys *ph, int d, double e[3][3], double sp[3][3], double *Esp, om_eig *E) {
+    sym_eig3(e, E->l, E->V);
+    E->tr = 0.0;
+    for (int i = 0; i < d; ++i) E->tr += e[i][i];
+    double trp = posp(E->tr), ep2 = 0.0;
+    for (int a = 0; a < 3; ++a) ep2 += posp(E->l[a]) * posp(E->l[a]);
+    *Esp = 0.5 * ph->lam * trp * trp + ph->mu * ep2;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double epij = 0.0;
+            for (int a = 0; a < 3; ++a) epij += posp(E->l[a]) * E->V[i][a] * E->V[j][a];
+            sp[i][j] = (i < d && j < d) ? 2.0 * ph->mu * epij + (i == j ? ph->lam * trp : 0.0) : 0.0;
+        }
+}
+
+/* Directional derivative of sigma^+ at e in the direction de:
+ *   C^+ de = lambda H(tr e) tr(de) I + 2 mu P^+(de),
+ *   P^+(de) = sum_{a,b} theta_ab (n_a . de n_b) n_a n_b^T,
+ * theta_aa = H(l_a), theta_ab = (<l_a>_+ - <l_b>_+) / (l_a - l_b) for l_a != l_b (H(l_a) if equal);
+ * the derivative of the isotropic tensor function e -> e_+. */
+static void miehe_tangent(const om_phys *ph, int d, const om_eig *E, double de[3][3], double out[3][3]) {
+    double dtr = 0.0;
+    for (int i = 0; i < d; ++i) dtr += de[i][i];
+    double dp[3][3] = {{0}};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double th;
+            if (a == b || E->l[a] == E->l[b]) th = heav(E->l[a]);
+            else th = (posp(E->l[a]) - posp(E->l[b])) / (E->l[a] - E->l[b]);
+            if (th == 0.0) continue;
+            double proj = 0.0;   /* n_a . de n_b */
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) proj += E->V[i][a] * de[i][j] * E->V[j][b];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) dp[i][j] += th * proj * E->V[i][a] * E->V[j][b];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            out[i][j] = (i < d && j < d) ? 2.0 * ph->mu * dp[i][j] + (i == j ? ph->lam * heav(E->tr) * dtr : 0.0) : 0.0;
+}
+
 static double ddot(int d, double a[3][3], double b[3][3]) {
     double s = 0.0;
     for (int i = 0; i < d; ++i)
@@ -262,10 +358,12 @@ static void element_jacobian(const om_mesh *m, const om_phys *ph, const om_qpdat
     for (int q = 0; q < qd->nq; ++q) {
         om_state s;
         state_at_qp(m, qd, q, nodes, nn, U, ptil, &s);
-        double eu[3][3], su[3][3];
+        double eu[3][3], su[3][3], sp[3][3], Esp;
+        om_eig E;
         strain(d, s.gu, eu);
         stress(ph, d, eu, su);
-        double Es = elastic_energy(ph, d, eu);
+        if (ph->split) miehe_split(ph, d, eu, sp, &Esp, &E);
+        else { memcpy(sp, su, sizeof(sp)); Esp = elastic_energy(ph, d, eu); }
         double divu = 0.0;
         for (int i = 0; i < d; ++i) divu += s.gu[i][i];
         double gt = degr(ph, s.pt);
@@ -288,7 +386,14 @@ static void element_jacobian(const om_mesh *m, const om_phys *ph, const om_qpdat
                             strain(d, gi, ei);
                             strain(d, gj, ej);
                             stress(ph, d, ej, sj);
-                            val = gt * ddot(d, sj, ei);
+                            if (ph->split) {
+                                /* g C^+ de + C^- de with C^- = C - C^+ */
+                                double cp[3][3];
+                                miehe_tangent(ph, d, &E, ej, cp);
+                                val = gt * ddot(d, cp, ei) + ddot(d, sj, ei) - ddot(d, cp, ei);
+                            } else {
+                                val = gt * ddot(d, sj, ei);
+                            }
                         } else if (ci < d && cj == d) {
                             val = 0.0; /* phi~ frozen in the displacement equation */
                         } else if (ci == d && cj < d) {
@@ -296,12 +401,12 @@ static void element_jacobian(const om_mesh *m, const om_phys *ph, const om_qpdat
                             vec_shape_grad(d, cj, gNj, gj);
                             strain(d, gj, ej);
                             double divj = gNj[cj];
-                            val = (2.0 * ph->f * (1.0 - ph->kappa) * s.phi * ddot(d, su, ej)
+                            val = (2.0 * ph->f * (1.0 - ph->kappa) * s.phi * ddot(d, sp, ej)
                                    + 2.0 * ph->p * s.phi * divj) * Ni;
                         } else {
                             double gg = 0.0;
                             for (int a = 0; a < d; ++a) gg += gNi[a] * gNj[a];
-                            val = (2.0 * ph->f * (1.0 - ph->kappa) * Es + 2.0 * ph->p * divu + ph->Gc / ph->eps) * Nj * Ni
+                            val = (2.0 * ph->f * (1.0 - ph->kappa) * Esp + 2.0 * ph->p * divu + ph->Gc / ph->eps) * Nj * Ni
                                   + ph->Gc * ph->eps * gg;
                         }
                         Ke[row * ne + col] += W * val;
@@ -322,13 +427,19 @@ static void element_residual(const om_mesh *m, const om_phys *ph, const om_qpdat
     for (int q = 0; q < qd->nq; ++q) {
         om_state s;
         state_at_qp(m, qd, q, nodes, nn, U, ptil, &s);
-        double eu[3][3], su[3][3];
+        double eu[3][3], su[3][3], sp[3][3], Esp;
+        om_eig E;
         strain(d, s.gu, eu);
         stress(ph, d, eu, su);
-        double Es = elastic_energy(ph, d, eu);
+        if (ph->split) miehe_split(ph, d, eu, sp, &Esp, &E);
+        else { memcpy(sp, su, sizeof(sp)); Esp = elastic_energy(ph, d, eu); }
+        /* g(phi~) sigma^+ + sigma^- */
+        double gt = degr(ph, s.pt);
+        double seff[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) seff[i][j] = gt * sp[i][j] + (su[i][j] - sp[i][j]);
         double divu = 0.0;
         for (int i = 0; i < d; ++i) divu += s.gu[i][i];
-        double gt = degr(ph, s.pt);
         double W = qd->W[q];
         for (int ni = 0; ni < nl; ++ni) {
             const double *gNi = qd->G[q][ni];
@@ -337,12 +448,12 @@ static void element_residual(const om_mesh *m, const om_phys *ph, const om_qpdat
                 double gi[3][3], ei[3][3];
                 vec_shape_grad(d, ci, gNi, gi);
                 strain(d, gi, ei);
-                double v = gt * ddot(d, su, ei) + s.pt * s.pt * ph->p * gNi[ci];
+                double v = ddot(d, seff, ei) + s.pt * s.pt * ph->p * gNi[ci];
                 Re[ni * nc + ci] += W * v;
             }
             double gg = 0.0;
             for (int a = 0; a < d; ++a) gg += s.gphi[a] * gNi[a];
-            double v = ph->f * 2.0 * (1.0 - ph->kappa) * s.phi * Es * Ni
+            double v = ph->f * 2.0 * (1.0 - ph->kappa) * s.phi * Esp * Ni
                        + 2.0 * s.phi * ph->p * divu * Ni
                        + ph->Gc * (-(1.0 / ph->eps) * (1.0 - s.phi) * Ni + ph->eps * gg);
             Re[ni * nc + d] += W * v;
@@ -374,8 +485,15 @@ static double element_energy(const om_mesh *m, const om_phys *ph, const om_qpdat
             }
         for (int j = 0; j < d; ++j) gp2 += gphi[j] * gphi[j];
         double Es = 0.5 * ph->lam * tr * tr + ph->mu * ee;
+        double Esp = Es;
+        if (ph->split) {
+            double e[3][3], sp[3][3];
+            om_eig E;
+            strain(d, gu, e);
+            miehe_split(ph, d, e, sp, &Esp, &E);
+        }
         double g = (1.0 - ph->kappa) * phi * phi + ph->kappa;
-        double dens = g * Es + phi * phi * ph->p * tr
+        double dens = g * Esp + (Es - Esp) + phi * phi * ph->p * tr
                       + 0.5 * ph->Gc * ((1.0 - phi) * (1.0 - phi) / ph->eps + ph->eps * gp2);
         E += qd->W[q] * dens;
     }

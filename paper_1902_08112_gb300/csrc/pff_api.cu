@@ -46,6 +46,7 @@ extern "C" void pff_default_params(pff_params* p) {
     p->coarse_maxit = 200;
     p->seed = 12345;
     p->preconditioner = 0;
+    p->split = 0;
 }
 
 // Gauss-Legendre rule with deg+1 points mapped to [0,1] and the Lagrange basis on the
@@ -95,6 +96,7 @@ static Phys make_phys(const pff_params& p) {
     ph.eps = p.eps;
     ph.p = p.pressure;
     ph.f = p.phi_elastic_factor;
+    ph.split = p.split;
     return ph;
 }
 
@@ -108,6 +110,7 @@ static const char* check_params(const pff_params* p) {
     if (!(p->cheb_safety > 0) || !(p->cheb_ratio > 0 && p->cheb_ratio < 1)) return "need cheb_safety > 0, 0 < cheb_ratio < 1";
     if (!(p->coarse_rtol > 0 && p->coarse_rtol < 1) || p->coarse_maxit < 1) return "need 0 < coarse_rtol < 1, coarse_maxit >= 1";
     if (p->preconditioner != 0 && p->preconditioner != 1) return "preconditioner must be 0 (P_full) or 1 (P_diag)";
+    if (p->split != 0 && p->split != 1) return "split must be 0 (none) or 1 (Miehe)";
     return nullptr;
 }
 

@@ -134,11 +134,13 @@ cudaError_t upload(pff_batch* b) {
 const BLevel* tab(pff_batch* b, int l) { return l == b->Lmax ? b->d_fine : b->d_lv + (size_t)l * b->n; }
 
 // y(sy) = G~ x(sx) on level l (l == Lmax: each instance's finest level), precision by fp64
-cudaError_t b_apply(pff_batch* b, int l, bool fp64, bool blockdiag, int sx, int sy, int phi_bits) {
+cudaError_t b_apply(pff_batch* b, int l, bool fp64, bool blockdiag, int sx, int sy, int phi_bits, bool preset = true) {
     const BLevel* L = tab(b, l);
     const int st = fp64 ? kStyleF64 : kStyleF32;
-    if (fp64) BCK(bl_init_masked<double>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.0, b->stream));
-    else BCK(bl_init_masked<float>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.f, b->stream));
+    if (preset) {
+        if (fp64) BCK(bl_init_masked<double>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.0, b->stream));
+        else BCK(bl_init_masked<float>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.f, b->stream));
+    }
     return launch_q1_apply_batched(b->dim, fp64, blockdiag, fp64, L, b->n,
                                    b->d_tiles + ((size_t)l * 2 + st) * (b->n + 1), b->tot[(size_t)l * 2 + st], sx, sy,
                                    phi_bits, b->stream);
@@ -155,12 +157,13 @@ cudaError_t b_cheb_run(pff_batch* b, int l, int K, bool coarse, int phase, int s
     const BLevel* L = tab(b, l);
     const int W = sizeof(T) == 8 ? BV_W64 : BV_W32;
     const int r = bsel(W + 2), d = bsel(W + 3), t = bsel(W + 4);
+    // every update except the last also presets t for the next apply
     BCK(bl_cheb<T>(L, b->n, b->blocks[l], r, -1, d, sx, coarse ? coarse_coef(b, phase, 0) : smooth_coef(b, l, 0), mode,
-                   b->stream));
+                   b->stream, K > 1 ? t : -1));
     for (int s = 1; s < K; ++s) {
-        BCK(b_apply(b, l, sizeof(T) == 8, true, d, t, PHI_BITS_ALL));
+        BCK(b_apply(b, l, sizeof(T) == 8, true, d, t, PHI_BITS_ALL, false));
         BCK(bl_cheb<T>(L, b->n, b->blocks[l], r, t, d, sx, coarse ? coarse_coef(b, phase, s) : smooth_coef(b, l, s), 0,
-                       b->stream));
+                       b->stream, s + 1 < K ? t : -1));
     }
     return cudaSuccess;
 }
@@ -628,7 +631,7 @@ extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int rest
         if (!hs[i]) return PFF_EINVAL;
         if (hs[i]->mesh.degree != 1 || hs[i]->mesh.dim != hs[0]->mesh.dim) return PFF_EINVAL;
         if (hs[i]->stream != hs[0]->stream) return PFF_EINVAL;
-        if (hs[i]->prm.mg_precision != 32 || hs[i]->prm.preconditioner != 0 || hs[i]->prm.cheb_degree != hs[0]->prm.cheb_degree) return PFF_EINVAL;
+        if (hs[i]->prm.mg_precision != 32 || hs[i]->prm.preconditioner != 0 || hs[i]->prm.split != 0 || hs[i]->prm.cheb_degree != hs[0]->prm.cheb_degree) return PFF_EINVAL;
         if (!hs[i]->fast_q1) return PFF_EINVAL;
     }
     pff_batch* b = new (std::nothrow) pff_batch();

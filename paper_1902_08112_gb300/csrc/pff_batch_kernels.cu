@@ -30,10 +30,11 @@ __global__ void kb_init_masked(const BLevel* __restrict__ L, int sx, int sy, int
     }
 }
 
-// Chebyshev step with per-instance coefficients coef[inst * 4 + (c1u, c1p, c2u, c2p)]
+// Chebyshev step with per-instance coefficients coef[inst * 4 + (c1u, c1p, c2u, c2p)]; with
+// stn >= 0 it also writes the preset of the next apply into stn (d on eliminated rows, else 0)
 template <typename T>
 __global__ void kb_cheb(const BLevel* __restrict__ L, int sr, int st, int sd, int sx, const double* __restrict__ coef,
-                        int first) {
+                        int first, int stn) {
     const BLevel& d = L[blockIdx.y];
     if (!d.valid) return;
     const int64_t nd = n_dofs(d.g), nu = d.g.n_nodes * d.g.dim;
@@ -43,20 +44,26 @@ __global__ void kb_cheb(const BLevel* __restrict__ L, int sr, int st, int sd, in
     const T* t = st >= 0 ? bvec<T>(d, st) : nullptr;
     T* dd = bvec<T>(d, sd);
     T* x = bvec<T>(d, sx);
+    T* tn = stn >= 0 ? bvec<T>(d, stn) : nullptr;
+    const int64_t nn = d.g.n_nodes;
     const T* dinv = sizeof(T) == 8 ? (const T*)d.dinv64 : (const T*)d.dinv32;
     BSTRIDE(i, nd) {
         const bool u = i < nu;
         const T c1 = u ? c1u : c1p, c2 = u ? c2u : c2p;
+        T di;
         if (first) {
-            const T di = c2 * dinv[i] * r[i];
-            dd[i] = di;
+            di = c2 * dinv[i] * r[i];
             x[i] = first == 1 ? di : x[i] + di;
         } else {
             const T ri = r[i] - t[i];
             r[i] = ri;
-            const T di = c1 * dd[i] + c2 * dinv[i] * ri;
-            dd[i] = di;
+            di = c1 * dd[i] + c2 * dinv[i] * ri;
             x[i] += di;
+        }
+        dd[i] = di;
+        if (tn) {
+            const int c = dof_comp(i, nn);
+            tn[i] = belim(d.mask[i - c * nn], c, d.g.dim, PHI_BITS_ALL) ? di : T(0);
         }
     }
 }
@@ -394,8 +401,8 @@ cudaError_t bl_init_masked(const BLevel* L, int n, int blocks, int sx, int sy, i
 }
 template <typename T>
 cudaError_t bl_cheb(const BLevel* L, int n, int blocks, int sr, int st, int sd, int sx, const double* coef, int first,
-                    cudaStream_t s) {
-    kb_cheb<T><<<bgrid(blocks, n), kT, 0, s>>>(L, sr, st, sd, sx, coef, first);
+                    cudaStream_t s, int stn) {
+    kb_cheb<T><<<bgrid(blocks, n), kT, 0, s>>>(L, sr, st, sd, sx, coef, first, stn);
     return count_launch(cudaGetLastError());
 }
 template <typename T>
@@ -475,7 +482,7 @@ cudaError_t bl_start_vector(const BLevel* L, int n, int blocks, int sv, const ui
 
 #define PFF_INST(T)                                                                                              \
     template cudaError_t bl_init_masked<T>(const BLevel*, int, int, int, int, int, T, cudaStream_t);             \
-    template cudaError_t bl_cheb<T>(const BLevel*, int, int, int, int, int, int, const double*, int, cudaStream_t); \
+    template cudaError_t bl_cheb<T>(const BLevel*, int, int, int, int, int, int, const double*, int, cudaStream_t, int); \
     template cudaError_t bl_sub<T>(const BLevel*, int, int, int, int, int, cudaStream_t);                        \
     template cudaError_t bl_copy<T>(const BLevel*, int, int, int, int, int, cudaStream_t);                       \
     template cudaError_t bl_restrict<T>(const BLevel*, const BLevel*, int, int, int, int, cudaStream_t);         \

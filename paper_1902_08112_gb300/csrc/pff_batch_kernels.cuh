@@ -11,7 +11,7 @@ template <typename T>
 cudaError_t bl_init_masked(const BLevel* L, int n, int blocks, int sx, int sy, int phi_bits, T v, cudaStream_t s);
 template <typename T>
 cudaError_t bl_cheb(const BLevel* L, int n, int blocks, int sr, int st, int sd, int sx, const double* coef, int first,
-                    cudaStream_t s);
+                    cudaStream_t s, int stn = -1);
 template <typename T>
 cudaError_t bl_sub(const BLevel* L, int n, int blocks, int sa, int sb, int sc, cudaStream_t s);
 template <typename T>

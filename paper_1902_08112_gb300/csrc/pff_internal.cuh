@@ -19,6 +19,7 @@ struct Phys {
     double mu, lam;      // Lame coefficients
     double Gc, kappa, eps, p;
     double f;            // factor on the phi-equation elastic term
+    int split;           // 0: no split; 1: Miehe split of E_s (Sec. 2.1)
 };
 
 // 1D Lagrange shape functions on [0,1] at the (deg+1)-point Gauss rule: value N1[a][q],

@@ -12,6 +12,7 @@
 // Eliminated columns are zeroed while staging; eliminated rows are preset by
 // launch_init_masked (y = x for the apply, 1 for the diagonal) and skipped here.
 #include "pff_internal.cuh"
+#include "pff_split.cuh"
 
 namespace pff {
 
@@ -51,7 +52,7 @@ struct CellKernel {
     }
 };
 
-template <int DIM, int DEG, typename T, int OP>
+template <int DIM, int DEG, typename T, int OP, bool SPLIT>
 __global__ void __launch_bounds__(TileCfg<DIM, DEG>::TX * TileCfg<DIM, DEG>::TY * TileCfg<DIM, DEG>::TZ)
 k_cell(CellArgs<T> a) {
     using K = CellKernel<DIM, DEG, T, OP>;
@@ -181,6 +182,17 @@ k_cell(CellArgs<T> a) {
                     for (int j = 0; j < DIM; ++j) ee += eu[i][j] * eu[i][j];
                 const T Es = half * lam * tru * tru + mu * ee;
                 const T gt = (one - kap) * ptv * ptv + kap;   // g_kappa(phi~)
+                // Miehe split (Sec. 2.1): sigma^+(u), E_s^+ and the eigen data of the tangent
+                T sp3[3][3], Esp = Es;
+                SplitEig<T> se;
+                if constexpr (SPLIT) {
+                    T e3[3][3];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) e3[i][j] = (i < DIM && j < DIM) ? eu[i][j] : T(0);
+                    split_stress(mu, lam, DIM, e3, sp3, Esp, se);
+                }
 
                 // ---- pointwise coefficients of the test functions: fu (tensor on grad w),
                 //      fphi (on psi), fgphi (on grad psi)
@@ -193,22 +205,36 @@ k_cell(CellArgs<T> a) {
                         for (int j = 0; j < DIM; ++j) ed[i][j] = half * (gdu[i][j] + gdu[j][i]);
 #pragma unroll
                     for (int i = 0; i < DIM; ++i) trd += ed[i][i];
-                    // G_uu: g(phi~) sigma(du) : e(w)
+                    // G_uu: g(phi~) sigma(du) : e(w); with the split g C^+ de + (C - C^+) de
+                    T cpd[3][3];
+                    if constexpr (SPLIT) {
+                        T d3[3][3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) d3[i][j] = (i < DIM && j < DIM) ? ed[i][j] : T(0);
+                        split_tangent(mu, lam, DIM, se, d3, cpd);
+                    }
 #pragma unroll
                     for (int i = 0; i < DIM; ++i)
 #pragma unroll
-                        for (int j = 0; j < DIM; ++j)
-                            fu[i][j] = wq * gt * (two * mu * ed[i][j] + (i == j ? lam * trd : T(0)));
-                    // G_phiphi: [2 f (1-k) E_s + 2 p div u + Gc/eps] dphi psi + Gc eps grad dphi . grad psi
-                    fphi = (two * ff * (one - kap) * Es + two * p * tru + Gc / eps) * dphi;
+                        for (int j = 0; j < DIM; ++j) {
+                            const T sd = two * mu * ed[i][j] + (i == j ? lam * trd : T(0));
+                            if constexpr (SPLIT) fu[i][j] = wq * (sd - (one - gt) * cpd[i][j]);
+                            else fu[i][j] = wq * gt * sd;
+                        }
+                    // G_phiphi: [2 f (1-k) E_s^+ + 2 p div u + Gc/eps] dphi psi + Gc eps grad dphi . grad psi
+                    fphi = (two * ff * (one - kap) * Esp + two * p * tru + Gc / eps) * dphi;
                     if constexpr (OP == OP_APPLY) {
-                        // G_phiu: 2 f (1-k) phi sigma(u):e(du) + 2 p phi div du
+                        // G_phiu: 2 f (1-k) phi sigma^+(u):e(du) + 2 p phi div du
                         T su_ed = 0;
 #pragma unroll
                         for (int i = 0; i < DIM; ++i)
 #pragma unroll
-                            for (int j = 0; j < DIM; ++j)
-                                su_ed += (two * mu * eu[i][j] + (i == j ? lam * tru : T(0))) * ed[i][j];
+                            for (int j = 0; j < DIM; ++j) {
+                                const T sij = SPLIT ? sp3[i][j] : two * mu * eu[i][j] + (i == j ? lam * tru : T(0));
+                                su_ed += sij * ed[i][j];
+                            }
                         fphi += two * ff * (one - kap) * phi * su_ed + two * p * phi * trd;
                     }
                     fphi *= wq;
@@ -220,15 +246,18 @@ k_cell(CellArgs<T> a) {
 #pragma unroll
                     for (int i = 0; i < DIM; ++i)
 #pragma unroll
-                        for (int j = 0; j < DIM; ++j)
-                            fu[i][j] = -wq * (gt * (two * mu * eu[i][j] + (i == j ? lam * tru : T(0))) +
-                                              (i == j ? ptv * ptv * p : T(0)));
-                    fphi = -wq * (ff * two * (one - kap) * phi * Es + two * phi * p * tru - Gc / eps * (one - phi));
+                        for (int j = 0; j < DIM; ++j) {
+                            const T sij = two * mu * eu[i][j] + (i == j ? lam * tru : T(0));
+                            // g(phi~) sigma^+ + sigma^- = sigma - (1 - g) sigma^+
+                            const T seff = SPLIT ? sij - (one - gt) * sp3[i][j] : gt * sij;
+                            fu[i][j] = -wq * (seff + (i == j ? ptv * ptv * p : T(0)));
+                        }
+                    fphi = -wq * (ff * two * (one - kap) * phi * Esp + two * phi * p * tru - Gc / eps * (one - phi));
 #pragma unroll
                     for (int j = 0; j < DIM; ++j) fgphi[j] = -wq * Gc * eps * gphi[j];
                 } else {
                     // diagonal: coefficients reused below
-                    fphi = wq * (two * ff * (one - kap) * Es + two * p * tru + Gc / eps);
+                    fphi = wq * (two * ff * (one - kap) * Esp + two * p * tru + Gc / eps);
 #pragma unroll
                     for (int j = 0; j < DIM; ++j) fgphi[j] = wq * Gc * eps;
 #pragma unroll
@@ -251,8 +280,31 @@ k_cell(CellArgs<T> a) {
 #pragma unroll
                         for (int j = 0; j < DIM; ++j) gg += G[j] * G[j];
 #pragma unroll
-                        for (int c = 0; c < DIM; ++c)
-                            sel[(n * NC + c) * NCELL + cell] += fu[0][0] * (mu * (gg + G[c] * G[c]) + lam * G[c] * G[c]);
+                        for (int c = 0; c < DIM; ++c) {
+                            if constexpr (SPLIT) {
+                                // de = sym(e_c (x) grad N): sigma(de) : de - (1 - g) C^+ de : de
+                                T d3[3][3], cp3[3][3];
+#pragma unroll
+                                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                                    for (int j = 0; j < 3; ++j) {
+                                        T v = T(0);
+                                        if (i == c && j < DIM) v += half * G[j];
+                                        if (j == c && i < DIM) v += half * G[i];
+                                        d3[i][j] = v;
+                                    }
+                                split_tangent(mu, lam, DIM, se, d3, cp3);
+                                T cpdd = 0;
+#pragma unroll
+                                for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                                    for (int j = 0; j < DIM; ++j) cpdd += cp3[i][j] * d3[i][j];
+                                const T full = mu * (gg + G[c] * G[c]) + lam * G[c] * G[c];
+                                sel[(n * NC + c) * NCELL + cell] += wq * (full - (one - gt) * cpdd);
+                            } else {
+                                sel[(n * NC + c) * NCELL + cell] += fu[0][0] * (mu * (gg + G[c] * G[c]) + lam * G[c] * G[c]);
+                            }
+                        }
                         sel[(n * NC + DIM) * NCELL + cell] += fphi * N * N + fgphi[0] * gg;
                     } else {
 #pragma unroll
@@ -311,31 +363,40 @@ k_cell(CellArgs<T> a) {
     }
 }
 
-template <int DIM, int DEG, typename T, int OP>
+template <int DIM, int DEG, typename T, int OP, bool SPLIT>
 static cudaError_t launch_one(const CellArgs<T>& a, cudaStream_t s) {
     using K = CellKernel<DIM, DEG, T, OP>;
     using C = typename K::C;
     const size_t smem = K::smem_bytes();
     static bool attr_set = false;  // per instantiation; the attribute is per device function
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_cell<DIM, DEG, T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_cell<DIM, DEG, T, OP, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((a.g.nc[0] + C::TX - 1) / C::TX, (a.g.nc[1] + C::TY - 1) / C::TY,
               DIM == 3 ? (a.g.nc[2] + C::TZ - 1) / C::TZ : 1);
-    k_cell<DIM, DEG, T, OP><<<grid, K::NCELL, smem, s>>>(a);
+    k_cell<DIM, DEG, T, OP, SPLIT><<<grid, K::NCELL, smem, s>>>(a);
     return count_launch(cudaGetLastError());
 }
 
 template <int DIM, int DEG, typename T>
 static cudaError_t dispatch_op(int op, const CellArgs<T>& a, cudaStream_t s) {
+    if (a.ph.split) {
+        switch (op) {
+            case OP_APPLY: return launch_one<DIM, DEG, T, OP_APPLY, true>(a, s);
+            case OP_APPLY_BLOCKDIAG: return launch_one<DIM, DEG, T, OP_APPLY_BLOCKDIAG, true>(a, s);
+            case OP_RESIDUAL: return launch_one<DIM, DEG, T, OP_RESIDUAL, true>(a, s);
+            case OP_DIAGONAL: return launch_one<DIM, DEG, T, OP_DIAGONAL, true>(a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (op) {
-        case OP_APPLY: return launch_one<DIM, DEG, T, OP_APPLY>(a, s);
-        case OP_APPLY_BLOCKDIAG: return launch_one<DIM, DEG, T, OP_APPLY_BLOCKDIAG>(a, s);
-        case OP_RESIDUAL: return launch_one<DIM, DEG, T, OP_RESIDUAL>(a, s);
-        case OP_DIAGONAL: return launch_one<DIM, DEG, T, OP_DIAGONAL>(a, s);
+        case OP_APPLY: return launch_one<DIM, DEG, T, OP_APPLY, false>(a, s);
+        case OP_APPLY_BLOCKDIAG: return launch_one<DIM, DEG, T, OP_APPLY_BLOCKDIAG, false>(a, s);
+        case OP_RESIDUAL: return launch_one<DIM, DEG, T, OP_RESIDUAL, false>(a, s);
+        case OP_DIAGONAL: return launch_one<DIM, DEG, T, OP_DIAGONAL, false>(a, s);
     }
     return cudaErrorInvalidValue;
 }

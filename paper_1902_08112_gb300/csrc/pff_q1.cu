@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include "pff_df64.cuh"
+#include "pff_split.cuh"
 #include "pff_internal.cuh"
 #include "pff_q1.cuh"
 #include "pff_batch.cuh"
@@ -1365,8 +1366,18 @@ __global__ void k_q1_energy(Geom g, Phys ph, const double* __restrict__ U, doubl
 #pragma unroll
             for (int d = 0; d < DIM; ++d) gg += gr[DIM][d] * gr[DIM][d];
             const double Es = sE * (0.5 * ph.lam * tr * tr + ph.mu * ee);
+            double Esp = Es;
+            if (ph.split) {   // Miehe split: g(phi) E_s^+ + (E_s - E_s^+)
+                double e3[3][3], sp[3][3];
+                SplitEig<double> se;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) e3[i][j] = (i < DIM && j < DIM) ? 0.5 * (gr[i][j] + gr[j][i]) : 0.0;
+                split_stress(sE * ph.mu, sE * ph.lam, DIM, e3, sp, Esp, se);
+            }
             const double gk = (1.0 - ph.kappa) * phi * phi + ph.kappa;
-            eb += w * (gk * Es + phi * phi * ph.p * tr);
+            eb += w * (gk * Esp + (Es - Esp) + phi * phi * ph.p * tr);
             ec += w * 0.5 * ph.Gc * ((1.0 - phi) * (1.0 - phi) / ph.eps + ph.eps * gg);
         }
     }

@@ -58,7 +58,7 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
         if (e0 && e1) CK(cudaEventRecord(e0, h->stream));
     }
     if (preset) CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, phi_bits, x, y, T(0), h->stream));
-    if (h->fast_q1 && L.g.deg == 1 && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
+    if (h->fast_q1 && L.g.deg == 1 && !h->ph.split && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
         const bool bd = op == OP_APPLY_BLOCKDIAG;
         if constexpr (sizeof(T) == 8)
             CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd,
@@ -96,7 +96,8 @@ cudaError_t diagonal_level(pff_hierarchy* h, int l, T* d) {
     Level& L = h->lv[l];
     CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, PHI_BITS_ALL, (const T*)nullptr, d, T(1), h->stream));
     if constexpr (sizeof(T) == 8) {
-        if (h->fast_q1 && L.g.deg == 1) return launch_q1_diagonal(L.g, h->ph, L.qpd64, L.mask, (double*)d, h->stream);
+        if (h->fast_q1 && L.g.deg == 1 && !h->ph.split)
+            return launch_q1_diagonal(L.g, h->ph, L.qpd64, L.mask, (double*)d, h->stream);
     }
     CellArgs<T> a;
     a.g = L.g;
@@ -117,7 +118,7 @@ template cudaError_t diagonal_level<float>(pff_hierarchy*, int, float*);
 cudaError_t residual_fine(pff_hierarchy* h, double* R) {
     Level& L = h->lv[h->L - 1];
     CK(cudaMemsetAsync(R, 0, sizeof(double) * n_dofs(L.g), h->stream));
-    if (h->fast_q1 && L.g.deg == 1) return launch_q1_residual(L.g, h->ph, L.U64, L.pt64, R, h->stream);
+    if (h->fast_q1 && L.g.deg == 1 && !h->ph.split) return launch_q1_residual(L.g, h->ph, L.U64, L.pt64, R, h->stream);
     CellArgs<double> a;
     a.g = L.g;
     a.ph = h->ph;
@@ -148,7 +149,7 @@ cudaError_t propagate_state(pff_hierarchy* h, bool values) {
         if (!values) break;     // only the masks changed: FP32 copies and Gauss-point data stay valid
         CK(launch_cast_f64_f32(L.U64, L.U32, n_dofs(L.g), h->stream));
         CK(launch_cast_f64_f32(L.pt64, L.pt32, L.g.n_nodes, h->stream));
-        if (L.qpd64) CK(launch_q1_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
+        if (L.qpd64 && !h->ph.split) CK(launch_q1_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
     }
     h->stale = true;
     return cudaSuccess;

@@ -37,7 +37,8 @@ def rel(a, b):
 class Case:
     """A hierarchy on the GPU and the oracle's levels for the same inputs."""
 
-    def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0, variant=0, modulus=False):
+    def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0, variant=0, modulus=False,
+                 split=0):
         self.w = w
         if state == "random":
             U, po, pt = W.random_state(w)
@@ -45,7 +46,7 @@ class Case:
             U, po, pt = W.initial_state(w, displacement="smooth")
         self.U, self.po, self.pt = U, po, pt
         self.prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu,
-                                      Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f)
+                                      Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f, split=split)
         self.h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), self.prm)
         pff.set_kernel_variant(self.h, variant)
         es = W.modulus_field(w) if modulus else None
@@ -55,7 +56,8 @@ class Case:
         act = W.random_active(w, active_fraction) if active_fraction > 0 else np.zeros(w.n_nodes, np.uint8)
         pff.set_active_set(self.h, t(act))
         self.mesh = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
-        self.phys = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, f=f, escale=es)
+        self.phys = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, f=f, escale=es,
+                             split=split)
         self.mask = fem.dirichlet_face_mask(self.mesh, 0x3F) | (act * fem.BIT_ACTIVE).astype(np.uint8)
         self.levels = mg.build_levels(self.mesh, w.n_levels, self.phys, U, pt, self.mask)
 
@@ -83,13 +85,17 @@ CASES = {
     "3d_q1_modulus": (lambda: W.small(W.config_3d_penny(), 20, 3), 0, True),
     "3d_q1_lanes_modulus": (lambda: W.small(W.config_3d_penny(), 12, 2), 2, True),
     "2d_q2_modulus": (lambda: W.small(W.config_2d_single_crack(deg=2), 12, 2), 1, True),
+    # Miehe split (generic kernels); random states mix tension and compression
+    "3d_q1_split": (lambda: W.small(W.config_3d_penny(), 12, 2), 0, False, 1),
+    "2d_q1_split": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 0, False, 1),
+    "3d_q2_split": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1, False, 1),
 }
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
 def case(request):
     make_w, variant, *rest = CASES[request.param]
-    c = Case(make_w(), variant=variant, modulus=bool(rest and rest[0]))
+    c = Case(make_w(), variant=variant, modulus=bool(rest and rest[0]), split=rest[1] if len(rest) > 1 else 0)
     yield c
     c.close()
 
@@ -165,9 +171,12 @@ def test_transfers_match_oracle(case):
         assert rel(xf, x0 + corr) <= 1e-14
 
 
-@pytest.fixture(scope="module")
-def solver_case():
-    c = Case(W.small(W.config_3d_penny(), 8, 2), active_fraction=0.05, state="initial")
+# (kernel variant, split): the Q1 fast path, the generic kernels, the Miehe split
+@pytest.fixture(scope="module", params=[(0, 0), (1, 0), (0, 1)], ids=["fast", "generic", "split"])
+def solver_case(request):
+    variant, split = request.param
+    c = Case(W.small(W.config_3d_penny(), 8, 2), active_fraction=0.05, state="initial", variant=variant,
+             split=split)
     mg.estimate_levels(c.levels, 12345, 10)
     yield c
     c.close()
@@ -221,7 +230,7 @@ def test_block_diagonal_vcycle_matches_oracle(solver_case):
     c = solver_case
     prm = mg.MGParams(block_diagonal=True)
     pd = pff.default_params(eps=c.w.eps, pressure=c.w.pressure, kappa=c.w.kappa, E=c.w.E, nu=c.w.nu,
-                            Gc=c.w.Gc, mg_precision=64, preconditioner=pff.PRECOND_DIAG)
+                            Gc=c.w.Gc, mg_precision=64, preconditioner=pff.PRECOND_DIAG, split=c.prm.split)
     pff.set_params(c.h, pd)
     try:
         lev = c.levels[0]

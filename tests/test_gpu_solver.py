@@ -170,3 +170,52 @@ def test_fgmres_with_varying_modulus(mgp):
         assert np.linalg.norm(Rt - G @ x.cpu().numpy()) <= 1.01e-8 * np.linalg.norm(Rt)
     finally:
         pff.destroy_hierarchy(h)
+
+
+@pytest.mark.parametrize("mgp", [64, 32])
+def test_fgmres_with_miehe_split(mgp):
+    """Miehe split (Sec. 2.1) on a loaded state (three load steps of the 2D single crack at 50x
+    pressure, run by the oracle): the same active set, iteration counts within 10% (+-1 for FP32)
+    and the oracle's system solved to the tolerance."""
+    w = W.config_2d_single_crack()
+    m = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
+    dmask = fem.dirichlet_face_mask(m, 0x3F)
+    U, _, _ = W.initial_state(w)
+    nn = m.n_nodes
+    prev_phi, prev_act = None, None
+    for n in (1, 2):
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=50 * w.pressure * n / 2, split=1)
+        phi_nm1 = U[w.dim * nn:].copy()
+        U, infos = pdas.load_step(m, ph, w.n_levels, U, prev_phi, dmask, prev_act, max_newton=6)
+        prev_phi, prev_act = phi_nm1, infos[-1].active
+    po = U[w.dim * nn:].copy()
+    pt = pdas.extrapolate(po, prev_phi)
+    prm = pff.default_params(eps=w.eps, pressure=ph.p, kappa=w.kappa, E=w.E, nu=w.nu, Gc=w.Gc,
+                             mg_precision=mgp, split=1)
+    h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), prm)
+    try:
+        pff.set_state(h, t(U), t(po), t(pt))
+        pff.update_active_set(h)
+        R = -fem.residual_A(m, ph, U, pt)
+        act = pdas.active_set(m, R, fem.lumped_mass(m), U, po, 100.0, 1e-10)
+        active = torch.empty(w.n_nodes, dtype=torch.uint8, device=DEV)
+        pff.get_active_set(h, active)
+        np.testing.assert_array_equal(active.cpu().numpy().astype(bool), act)
+        Rt, mask = pdas.eliminated_rhs(m, ph, U, pt, po, dmask, act, R)
+        lv = mg.build_levels(m, w.n_levels, ph, U, pt, mask)
+        mg.estimate_levels(lv, 12345, 10)
+        G = lv[-1].G
+        _, its_o, _, _, _ = krylov.fgmres(lambda v: G @ v, Rt, lambda v: mg.precondition(lv, v, mg.MGParams()),
+                                          rtol=1e-8, restart=30, maxit=200)
+        x = torch.zeros(w.n_dofs, dtype=torch.float64, device=DEV)
+        info = pff.gmres_solve(h, t(Rt), x, rtol=1e-8, restart=30, maxit=200)
+        assert info.converged
+        slack = max(1, math.floor(0.1 * its_o)) if mgp == 32 else math.floor(0.1 * its_o)
+        assert abs(info.iterations - its_o) <= slack, (info.iterations, its_o)
+        assert np.linalg.norm(Rt - G @ x.cpu().numpy()) <= 1.01e-8 * np.linalg.norm(Rt)
+        bulk, crack = pff.energies(h)
+        ob, oc = fem.energy_parts(m, ph, U)
+        assert bulk == pytest.approx(ob, rel=1e-11)
+        assert crack == pytest.approx(oc, rel=1e-11)
+    finally:
+        pff.destroy_hierarchy(h)

@@ -294,3 +294,75 @@ def test_coarsened_modulus_is_child_mean():
     # first coarse cell: children (0..1, 0..1, 0..1)
     e3 = es.reshape(2, 6, 4)
     assert c[0] == pytest.approx(e3[0:2, 0:2, 0:2].mean(), rel=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_miehe_split_closed_forms(dim):
+    """Miehe split (Sec. 2.1) on uniform strains with constant phi = c, p = 0: the bulk energy is
+    (g(c) E_s^+ + E_s - E_s^+)|D|, with E_s^+ = E_s for volumetric expansion and uniaxial tension,
+    E_s^+ = 0 for volumetric compression, and E_s^+ = E_s / 2 for pure shear (eigenvalues +-gamma,
+    tr e = 0); a rotated strain has the same E_s^+."""
+    m = _mesh(dim, 1, 2, 0.0, 2.0)
+    vol = 2.0 ** dim
+    kap, c = 1e-3, 0.4
+    ph = fem.Phys(E=1.5, nu=0.2, p=0.0, eps=0.4, Gc=0.0, kappa=kap, split=1)
+    mu, lam = fem.lame(1.5, 0.2)
+    g = (1 - kap) * c * c + kap
+
+    def bulk(A):
+        U = np.concatenate([_affine_u(m, A), np.full(m.n_nodes, c)])
+        return fem.energy(m, ph, U)
+
+    def Es_of(A):
+        e = 0.5 * (A + A.T)
+        return 0.5 * lam * np.trace(e) ** 2 + mu * np.sum(e * e)
+
+    eps_ = 0.01
+    cases = [(eps_ * np.eye(dim), 1.0), (-eps_ * np.eye(dim), 0.0)]
+    A = np.zeros((dim, dim)); A[0, 0] = eps_
+    cases.append((A, 1.0))
+    A = np.zeros((dim, dim)); A[0, 1] = A[1, 0] = eps_
+    cases.append((A, 0.5))
+    for A, frac in cases:
+        Es = Es_of(A)
+        Esp = frac * Es
+        assert bulk(A) == pytest.approx((g * Esp + Es - Esp) * vol, rel=1e-12, abs=1e-18)
+    # rotation invariance of E_s^+ (and of E_s) for a generic strain
+    rng = np.random.default_rng(3)
+    S = rng.standard_normal((dim, dim)) * 0.01
+    S = 0.5 * (S + S.T)
+    Q, _ = np.linalg.qr(rng.standard_normal((dim, dim)))
+    assert bulk(Q @ S @ Q.T) == pytest.approx(bulk(S), rel=1e-11)
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (3, 1), (3, 2)])
+def test_miehe_split_derivatives(dim, deg):
+    """With the Miehe split the residual is still the energy gradient (phi~ = phi, f = 1) and the
+    Jacobian the derivative of the residual (phi~ frozen), by central differences on random states
+    with tension and compression at the quadrature points."""
+    m = _mesh(dim, deg, 2)
+    ph = fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, Gc=1.0, kappa=1e-3, split=1)
+    U = _rand_state(m, 31)
+    phi = U[dim * m.n_nodes:]
+    A = fem.residual_A(m, ph, U, phi)
+    rng = np.random.default_rng(32)
+    for _ in range(3):
+        v = rng.standard_normal(U.size)
+        dlt = 1e-6
+        fd = (fem.energy(m, ph, U + dlt * v) - fem.energy(m, ph, U - dlt * v)) / (2 * dlt)
+        assert fd == pytest.approx(A @ v, rel=1e-6)
+    ptil = rng.uniform(0, 1, m.n_nodes)
+    G = fem.assemble(m, ph, U, ptil, np.zeros(m.n_nodes, np.uint8))
+    for _ in range(3):
+        v = rng.standard_normal(U.size)
+        dlt = 1e-7
+        fd = (fem.residual_A(m, ph, U + dlt * v, ptil) - fem.residual_A(m, ph, U - dlt * v, ptil)) / (2 * dlt)
+        Gv = G @ v
+        assert np.linalg.norm(fd - Gv) <= 1e-6 * np.linalg.norm(Gv)
+    # the split changes the operator: it differs from the unsplit Jacobian
+    G0 = fem.assemble(m, fem.Phys(E=1.0, nu=0.2, p=0.05, eps=0.3, Gc=1.0, kappa=1e-3), U, ptil,
+                      np.zeros(m.n_nodes, np.uint8))
+    assert abs(G - G0).max() > 1e-3 * abs(G0).max()
+    # symmetric displacement block
+    Guu = G.toarray()[:dim * m.n_nodes, :dim * m.n_nodes]
+    assert np.abs(Guu - Guu.T).max() <= 1e-13 * np.abs(Guu).max()
