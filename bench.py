@@ -256,24 +256,26 @@ def bench_multi(n: int, dev):
 
 
 def bench_serve(count: int):
-    """Serving pattern: Poisson arrivals of random pressurised-crack requests (N in {16,24,32},
-    2 load steps each) served by the continuous-batching loop; rate = 80% of the measured
-    closed-loop capacity."""
+    """Serving pattern: Poisson arrivals of random pressurised-crack requests (N in {16,24,32}) mixed
+    with 3D L-shaped panels (every 4th request), 2 load steps each, served by the
+    continuous-batching loop at 50, 80 and 95 % of the measured closed-loop capacity."""
     from paper_1902_08112_gb300 import serve
     # capacity: all requests queued at once
-    cal = serve.poisson_requests(max(4, count // 4), 1.0, seed=99)
+    cal = serve.poisson_requests(max(4, count // 4), 1.0, seed=99, lshape_every=4)
     srv = serve.Server(serve.PffBackend(), hbm_budget=64 << 30)
     t0 = srv.now()
     srv.run(cal, realtime=False)
     cap = len(cal) / (srv.now() - t0)       # requests per second
-    rate = 0.8 * cap
-    reqs = serve.poisson_requests(count, rate, seed=12345)
-    srv = serve.Server(serve.PffBackend(), hbm_budget=64 << 30)
-    t0 = srv.now()
-    srv.run(reqs, realtime=True)
-    wall = srv.now() - t0
-    out = serve.summarize(srv.results, wall)
-    out.update({"arrival_rate_per_s": rate, "capacity_requests_per_s": cap, "load_steps": 2, "ticks": srv.ticks})
+    out = {"capacity_requests_per_s": cap, "load_steps": 2, "mix": "batch recipe + 3D L-shape every 4th"}
+    for frac in (0.5, 0.8, 0.95):
+        reqs = serve.poisson_requests(count, frac * cap, seed=12345, lshape_every=4)
+        srv = serve.Server(serve.PffBackend(), hbm_budget=64 << 30)
+        t0 = srv.now()
+        srv.run(reqs, realtime=True)
+        wall = srv.now() - t0
+        res = serve.summarize(srv.results, wall)
+        res.update({"arrival_rate_per_s": frac * cap, "ticks": srv.ticks})
+        out[f"load_{int(frac * 100)}"] = res
     return out
 
 

@@ -59,7 +59,11 @@ enum {
  * dirichlet_faces: bit 2a clamps all displacement components on the lower face of axis a,
  * bit 2a+1 on the upper face (0x3F = every face, the pressurised-crack setting of Sec. 2.1).
  * dirichlet_mask: optional HOST array of fine-level node masks (PFF_MASK_U* bits) OR-ed into
- * the face mask; NULL for none.  Coarse levels inherit masks from the coincident fine nodes. */
+ * the face mask; NULL for none.  Coarse levels inherit masks from the coincident fine nodes.
+ * cell_mask: optional HOST array of fine-level cells (x fastest), nonzero = in the domain, for
+ * domains cut from the box such as the L-shaped panels of Sec. 5.2/5.3; NULL = the whole box.
+ * Cells outside contribute nothing; nodes on no cell of the domain are fixed in every component
+ * (identity rows).  A coarse cell is in the domain if any of its children is. */
 typedef struct {
     int dim;
     int degree;
@@ -69,6 +73,7 @@ typedef struct {
     double hi[3];
     unsigned dirichlet_faces;
     const uint8_t* dirichlet_mask;
+    const uint8_t* cell_mask;
 } pff_mesh;
 
 /* Problem and solver parameters.

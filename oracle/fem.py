@@ -37,7 +37,8 @@ def build_oracle(force: bool = False) -> str:
 
 class _Mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("deg", ctypes.c_int), ("n", ctypes.c_int * 3),
-                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("cell_mask", ctypes.POINTER(ctypes.c_uint8))]
 
 
 class _Phys(ctypes.Structure):
@@ -88,6 +89,7 @@ class Mesh:
     n: tuple            # cells per axis (len dim)
     lo: tuple
     hi: tuple
+    cell_mask: np.ndarray | None = None   # uint8 per cell (x fastest), 1 = in the domain; None = box
 
     def nodes_per_axis(self):
         return tuple(self.deg * self.n[a] + 1 for a in range(self.dim))
@@ -112,8 +114,31 @@ class Mesh:
         return tuple((self.hi[a] - self.lo[a]) / self.n[a] for a in range(self.dim))
 
     def coarsen(self) -> "Mesh":
+        """Next coarser nested mesh; a coarse cell is in the domain if any of its children is."""
         assert all(c % 2 == 0 for c in self.n)
-        return Mesh(self.dim, self.deg, tuple(c // 2 for c in self.n), self.lo, self.hi)
+        cm = None
+        if self.cell_mask is not None:
+            a = (np.asarray(self.cell_mask).reshape(tuple(self.n[::-1])) != 0)
+            for ax in range(self.dim):
+                sl0 = [slice(None)] * self.dim
+                sl1 = [slice(None)] * self.dim
+                sl0[ax] = slice(0, None, 2)
+                sl1[ax] = slice(1, None, 2)
+                a = a[tuple(sl0)] | a[tuple(sl1)]
+            cm = a.ravel().astype(np.uint8)
+        return Mesh(self.dim, self.deg, tuple(c // 2 for c in self.n), self.lo, self.hi, cm)
+
+    def node_touches_domain(self) -> np.ndarray:
+        """bool per node: the node belongs to at least one cell of the domain."""
+        npa = self.nodes_per_axis()
+        if self.cell_mask is None:
+            return np.ones(self.n_nodes, dtype=bool)
+        cm = (np.asarray(self.cell_mask).reshape(tuple(self.n[::-1])) != 0)
+        out = np.zeros(tuple(npa[::-1]), dtype=bool)
+        for off in np.ndindex(*([self.deg + 1] * self.dim)):
+            sl = tuple(slice(o, o + self.deg * nc, self.deg) for o, nc in zip(off[::-1], self.n[::-1]))
+            out[sl] |= cm
+        return out.ravel()
 
     def node_coords(self):
         """(n_nodes, dim) coordinates, x fastest."""
@@ -128,6 +153,10 @@ class Mesh:
             m.n[a] = self.n[a] if a < self.dim else 1
             m.lo[a] = self.lo[a] if a < self.dim else 0.0
             m.hi[a] = self.hi[a] if a < self.dim else 1.0
+        if self.cell_mask is not None:
+            arr = np.ascontiguousarray(self.cell_mask, dtype=np.uint8)
+            m.cell_mask = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+            m._keep = arr           # the C side reads the array during the call
         return m
 
 
@@ -253,7 +282,8 @@ def constrained_dofs(mesh: Mesh, mask, phi_bits: int = PHI_ALL) -> np.ndarray:
 
 def dirichlet_face_mask(mesh: Mesh, faces: int) -> np.ndarray:
     """uint8 per node: all u components clamped on the faces in 'faces'
-    (bit 2a = lower face of axis a, bit 2a+1 = upper face)."""
+    (bit 2a = lower face of axis a, bit 2a+1 = upper face).  Nodes that belong to no cell of the
+    domain (mesh.cell_mask) are fixed in every component (identity rows)."""
     npa = mesh.nodes_per_axis()
     idx = np.indices(npa[::-1]).reshape(mesh.dim, -1)[::-1]   # idx[a] = index along axis a
     on = np.zeros(mesh.n_nodes, dtype=bool)
@@ -263,4 +293,7 @@ def dirichlet_face_mask(mesh: Mesh, faces: int) -> np.ndarray:
         if faces >> (2 * a + 1) & 1:
             on |= idx[a] == npa[a] - 1
     ubits = sum(BIT_U[c] for c in range(mesh.dim))
-    return np.where(on, ubits, 0).astype(np.uint8)
+    out = np.where(on, ubits, 0).astype(np.uint8)
+    outside = ~mesh.node_touches_domain()
+    out[outside] = ubits | BIT_PHI_DIR
+    return out

@@ -42,11 +42,13 @@ class StepInfo:
 
 
 def active_set(mesh: fem.Mesh, R: np.ndarray, M: np.ndarray, U: np.ndarray, phi_old: np.ndarray,
-               c: float, threshold: float = 1e-10) -> np.ndarray:
+               c: float, threshold: float = 1e-10, fixed: np.ndarray | None = None) -> np.ndarray:
+    """fixed: bool per node whose phi is prescribed (phi Dirichlet, outside the domain): never active."""
     nn = mesh.n_nodes
     phi = U[mesh.dim * nn:]
-    lam = R[mesh.dim * nn:] / M
-    return lam + c * (phi - phi_old) > threshold
+    free = M > 0 if fixed is None else (M > 0) & ~fixed
+    lam = np.divide(R[mesh.dim * nn:], M, out=np.zeros(nn), where=free)
+    return free & (lam + c * (phi - phi_old) > threshold)
 
 
 def eliminated_rhs(mesh, phys, U, ptil, phi_old, dir_mask, active, R):
@@ -72,7 +74,7 @@ def newton_step(mesh, phys, n_levels, U, phi_old, ptil, dir_mask, prev_active, c
     U = np.asarray(U, dtype=np.float64)
     R = -fem.residual_A(mesh, phys, U, ptil)
     M = fem.lumped_mass(mesh)
-    act = active_set(mesh, R, M, U, phi_old, c_as, tol_as)
+    act = active_set(mesh, R, M, U, phi_old, c_as, tol_as, fixed=(dir_mask & fem.BIT_PHI_DIR) != 0)
     Rt, mask = eliminated_rhs(mesh, phys, U, ptil, phi_old, dir_mask, act, R)
     levels = multigrid.build_levels(mesh, n_levels, phys, U, ptil, mask)
     multigrid.estimate_levels(levels, seed, cg_steps)

@@ -37,7 +37,11 @@ typedef struct {
     int dim, deg;
     int n[3];          /* cells per axis */
     double lo[3], hi[3];
+    const uint8_t *cell_mask;  /* per cell: nonzero = in the domain (n_cells), NULL = the whole box */
 } om_mesh;
+
+/* Cells outside the domain (an L-shaped panel cut from its bounding box) contribute nothing. */
+static int cell_in(const om_mesh *m, int64_t cell) { return !m->cell_mask || m->cell_mask[cell] != 0; }
 
 typedef struct {
     double mu, lam;    /* Lame coefficients */
@@ -518,6 +522,7 @@ void om_residual(const om_mesh *m, const om_phys *ph, const double *U, const dou
     double Re[MAXN * MAXC];
     int64_t nodes[MAXN];
     for (int64_t cell = 0; cell < ncell; ++cell) {
+        if (!cell_in(m, cell)) continue;
         int nl = cell_nodes(m, cell, nodes);
         om_phys pc;
         element_residual(m, cell_phys(ph, cell, &pc), qd, nodes, nn, U, ptil, Re);
@@ -541,6 +546,7 @@ void om_energy_parts(const om_mesh *m, const om_phys *ph, const double *U, doubl
     out[0] = 0.0;
     out[1] = 0.0;
     for (int64_t cell = 0; cell < ncell; ++cell) {
+        if (!cell_in(m, cell)) continue;
         cell_nodes(m, cell, nodes);
         om_phys pc;
         out[0] += element_energy(m, cell_phys(&bulk, cell, &pc), qd, nodes, nn, U);
@@ -556,6 +562,7 @@ double om_energy(const om_mesh *m, const om_phys *ph, const double *U) {
     int64_t nodes[MAXN];
     double E = 0.0;
     for (int64_t cell = 0; cell < ncell; ++cell) {
+        if (!cell_in(m, cell)) continue;
         cell_nodes(m, cell, nodes);
         om_phys pc;
         E += element_energy(m, cell_phys(ph, cell, &pc), qd, nodes, nn, U);
@@ -579,6 +586,7 @@ void om_lumped_mass(const om_mesh *m, double *M) {
     int p = m->deg + 1, kz = (m->dim == 3) ? p : 1;
     int64_t nodes[MAXN];
     for (int64_t cell = 0; cell < ncell; ++cell) {
+        if (!cell_in(m, cell)) continue;
         cell_nodes(m, cell, nodes);
         int n = 0;
         for (int k = 0; k < kz; ++k)
@@ -667,6 +675,7 @@ void om_assemble(const om_mesh *m, const om_phys *ph, const double *U, const dou
     double *Ke = malloc(sizeof(double) * ne * ne);
     int64_t nodes[MAXN];
     for (int64_t cell = 0; cell < ncell; ++cell) {
+        if (!cell_in(m, cell)) continue;
         cell_nodes(m, cell, nodes);
         om_phys pc;
         element_jacobian(m, cell_phys(ph, cell, &pc), qd, nodes, nn, U, ptil, Ke);
@@ -732,6 +741,7 @@ void om_apply_rows(const om_mesh *m, const om_phys *ph, const double *U, const d
             for (int64_t cj = clo[1]; cj <= chi[1]; ++cj)
                 for (int64_t ci = clo[0]; ci <= chi[0]; ++ci) {
                     int64_t cell = ci + m->n[0] * (cj + (d == 3 ? (int64_t)m->n[1] * ck : 0));
+                    if (!cell_in(m, cell)) continue;
                     cell_nodes(m, cell, nodes);
                     int li = -1;
                     for (int n = 0; n < nl; ++n) if (nodes[n] == node) li = n;

@@ -161,6 +161,7 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
         g.dim = mesh->dim;
         g.deg = mesh->degree;
         g.es = nullptr;
+        g.cm = nullptr;
         const int f = 1 << (h->L - 1 - l);
         g.n_nodes = 1;
         g.n_cells = 1;
@@ -217,6 +218,21 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
         delete h;
         return st;
     }
+    // domain masks (cells outside an L-shaped or otherwise cut domain), finest from the host
+    if (mesh->cell_mask) {
+        for (int l = 0; l < h->L && e == cudaSuccess; ++l) e = dalloc(h, &h->lv[l].cm_buf, (size_t)h->lv[l].g.n_cells);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(F.cm_buf, mesh->cell_mask, (size_t)F.g.n_cells, cudaMemcpyHostToDevice, h->stream);
+        for (int l = h->L - 2; l >= 0 && e == cudaSuccess; --l)
+            e = launch_coarsen_cell_mask(h->lv[l].g, h->lv[l + 1].g, h->lv[l + 1].cm_buf, h->lv[l].cm_buf, h->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_all(h);
+            delete h;
+            return PFF_ECUDA;
+        }
+        for (auto& L : h->lv) L.g.cm = L.cm_buf;
+    }
     // Dirichlet mask of the finest level (faces + optional host mask), copied to every level
     uint8_t* extra = nullptr;
     if (mesh->dirichlet_mask) {
@@ -228,6 +244,7 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
         }
     }
     e = launch_face_mask(F.g, mesh->dirichlet_faces, extra, h->dir_mask, h->stream);
+    if (e == cudaSuccess && mesh->cell_mask) e = launch_outside_nodes(F.g, h->dir_mask, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(F.mask, h->dir_mask, nnf, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) e = propagate_state(h);
     if (e == cudaSuccess) e = launch_lumped_mass(F.g, h->lumped, h->stream);
@@ -277,6 +294,7 @@ extern "C" int64_t pff_hierarchy_bytes(const pff_mesh* mesh, int restart) {
             const int64_t nq = (int64_t)(mesh->dim == 3 ? 8 : 5) * (1 << mesh->dim) * nc;
             total += (nq * 4 + pad) + (nq * 8 + pad);
         }
+        if (mesh->cell_mask) total += nc + pad;
         nn_f = nn;
         nd_f = nd;
     }

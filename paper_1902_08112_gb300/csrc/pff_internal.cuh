@@ -38,7 +38,10 @@ struct Geom {
     int64_t n_nodes, n_cells;
     double h[3];         // cell edge lengths (1 beyond dim)
     const double* es;    // per-cell factor on E (n_cells, device), nullptr = uniform modulus
+    const uint8_t* cm;   // per-cell domain mask (n_cells, device, nonzero = in), nullptr = box
 };
+
+__host__ __device__ inline bool cell_in(const Geom& g, int64_t cell) { return !g.cm || g.cm[cell] != 0; }
 
 __host__ __device__ inline int64_t n_dofs(const Geom& g) { return (int64_t)(g.dim + 1) * g.n_nodes; }
 
@@ -62,6 +65,7 @@ struct Level {
     float* qpd32 = nullptr;      // Q1: Gauss-point linearisation coefficients, FP32
     float2* qpd64 = nullptr;     // Q1: the same as df64 pairs (hi, lo)
     double* es_buf = nullptr;    // storage of g.es once a varying modulus is set
+    uint8_t* cm_buf = nullptr;   // storage of g.cm (domains cut from the box)
     double lam_min[2] = {1, 1};  // eigenvalue estimates of D^-1 G_bb, blocks u / phi
     double lam_max[2] = {1, 1};
 };
@@ -158,6 +162,8 @@ cudaError_t launch_newton_rhs(const Geom& g, const double* R, const double* t, c
                               const double* phi_old, const uint8_t* mask, double* Rt, cudaStream_t s);
 cudaError_t launch_coarsen_cells(const Geom& gc, const Geom& gf, const double* sf, double* sc, cudaStream_t s);
 cudaError_t launch_count_nonpositive(int64_t n, const double* v, int* bad, cudaStream_t s);
+cudaError_t launch_coarsen_cell_mask(const Geom& gc, const Geom& gf, const uint8_t* mf, uint8_t* mc, cudaStream_t s);
+cudaError_t launch_outside_nodes(const Geom& g, uint8_t* mask, cudaStream_t s);
 cudaError_t launch_face_sum(const Geom& g, int axis, int side, int comp, const double* R, double* out,
                             cudaStream_t s);
 cudaError_t launch_extrapolate(int64_t n, const double* phi_nm1, const double* phi_nm2, double* out,

@@ -104,6 +104,7 @@ extern "C" pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_par
     if (mesh->degree != 1 && mesh->degree != 2) return PFF_EINVAL;
     pff::Geom g;
     g.es = nullptr;
+    g.cm = nullptr;
     g.dim = mesh->dim;
     g.deg = mesh->degree;
     g.n_nodes = 1;

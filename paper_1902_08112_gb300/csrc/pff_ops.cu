@@ -95,7 +95,8 @@ k_cell(CellArgs<T> a) {
     const int cell = threadIdx.x;
     if (cell < NCELL) {
         const int li = cell % C::TX, lj = (cell / C::TX) % C::TY, lk = cell / (C::TX * C::TY);
-        const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+        const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]) &&
+                           cell_in(g, (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)));
         if (valid) {
             const double sE = g.es ? g.es[(int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) +
                                                     (int64_t)g.nc[1] * (ck0 + lk))] : 1.0;

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(128) k_q1_linearize(Geom g, LinConsts k, const
     const df64 gce = dfc(k.gce);
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < nc;
          cell += (int64_t)gridDim.x * blockDim.x) {
+        if (!cell_in(g, cell)) continue;
         int ci[3] = {0, 0, 0};
         int64_t r = cell;
         for (int a = 0; a < DIM; ++a) { ci[a] = (int)(r % g.nc[a]); r /= g.nc[a]; }
@@ -245,7 +246,7 @@ cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, 
 // ------------------------------------------------------------------ modal apply
 template <int DIM, typename S>
 struct Q1Tile;
-template <> struct Q1Tile<3, float> { static constexpr int TX = 8, TY = 8, TZ = 4, MINB = 2; };
+template <> struct Q1Tile<3, float> { static constexpr int TX = 16, TY = 4, TZ = 2, MINB = 4; };
 template <> struct Q1Tile<3, df64> { static constexpr int TX = 8, TY = 4, TZ = 4, MINB = 1; };
 template <> struct Q1Tile<2, float> { static constexpr int TX = 16, TY = 16, TZ = 1, MINB = 2; };
 template <> struct Q1Tile<2, df64> { static constexpr int TX = 16, TY = 8, TZ = 1, MINB = 1; };
@@ -297,9 +298,11 @@ template <> struct QData<df64> {
     }
 };
 
+// kg: the Gauss-point scalings in global memory (batched launches), nullptr to read them from the
+// kernel parameters (a.k)
 template <int DIM, typename S, bool BLOCKDIAG>
 __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
-                                              int bx, int by, int bz) {
+                                              int bx, int by, int bz, const Q1Consts* __restrict__ kg = nullptr) {
     using T = Q1Tile<DIM, S>;
     using D = Q1Dims<DIM>;
     using St = typename Scalar<S>::storage;
@@ -333,17 +336,15 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
 
     const int cell = threadIdx.x;
     const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
-    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]) &&
+                       cell_in(g, (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)));
     if (valid) {
         const int64_t gid = (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk));
         const int tb = li + NTX * (lj + NTY * lk);
-        S cv[DIM + 1], cg[DIM][DIM];
-#pragma unroll
-        for (int j = 0; j <= DIM; ++j) cv[j] = cpair<S>(a.k.cv[j]);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-#pragma unroll
-            for (int j = 0; j < DIM; ++j) cg[d][j] = cpair<S>(a.k.cg[d][j]);
+        // Gauss-point scalings read straight from the kernel parameters or global memory (a local
+        // copy indexed in the unrolled loops ended up in local memory)
+        auto cv = [&](int j) { return cpair<S>(kg ? kg->cv[j] : a.k.cv[j]); };
+        auto cg = [&](int d, int j) { return cpair<S>(kg ? kg->cg[d][j] : a.k.cg[d][j]); };
         const S mu2 = cpair<S>(a.k.mu2), lam = cpair<S>(a.k.lam);
         const S gcew = cpair<S>(a.k.gcew);
 
@@ -372,7 +373,7 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
 #pragma unroll
                     for (int kp = 0; kp < NV; ++kp) {
                         if (kp & (1 << d)) continue;
-                        gd[c][d][j] = v[kp | (1 << d)] * cg[d][popc(kp)];
+                        gd[c][d][j] = v[kp | (1 << d)] * cg(d, popc(kp));
                         ++j;
                     }
                     inv<DIM - 1>(gd[c][d]);
@@ -436,7 +437,7 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                         if (!(k & (1 << d))) continue;
                         const int kp = k & ~(1 << d);
                         const int j = (kp & ((1 << d) - 1)) | ((kp >> (d + 1)) << d);   // kp without bit d
-                        acc = acc + ps[c][d][j] * cg[d][popc(kp)];
+                        acc = acc + ps[c][d][j] * cg(d, popc(kp));
                     }
                     Y[k] = acc;
                 }
@@ -457,7 +458,7 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
             fwd<DIM>(v);
             S F[NV];
 #pragma unroll
-            for (int k = 0; k < NV; ++k) F[k] = v[k] * cv[popc(k)];
+            for (int k = 0; k < NV; ++k) F[k] = v[k] * cv(popc(k));
             inv<DIM>(F);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
@@ -468,13 +469,13 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
             S Y[NV];
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                S acc = F[k] * cv[popc(k)];
+                S acc = F[k] * cv(popc(k));
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
                     if (!(k & (1 << d))) continue;
                     const int kp = k & ~(1 << d);
                     // gradient term: 2^d Gc eps w cg^2 times the modal coefficient k
-                    acc = acc + df_scale((gcew * v[k]) * (cg[d][popc(kp)] * cg[d][popc(kp)]), float(NV));
+                    acc = acc + df_scale((gcew * v[k]) * (cg(d, popc(kp)) * cg(d, popc(kp))), float(NV));
                 }
                 Y[k] = acc;
             }
@@ -631,7 +632,8 @@ __device__ __forceinline__ void q1_apply_lanes_tile(
 
     const int cell = threadIdx.x / NV, n = threadIdx.x % NV;
     const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
-    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]) &&
+                       cell_in(g, (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)));
     // every lane runs the shuffles; invalid cells work on zeros and are not stored
     const int tnode = (li + (n & 1)) + NTX * ((lj + ((n >> 1) & 1)) + NTY * (DIM == 3 ? lk + ((n >> 2) & 1) : 0));
     const int64_t gid = valid ? (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)) : 0;
@@ -738,7 +740,8 @@ __global__ void __launch_bounds__(256) k_q1_apply_direct(Q1ApplyArgs<typename Sc
     const int64_t nn = g.n_nodes;
     const int cell = threadIdx.x / NV, n = threadIdx.x % NV;
     const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
-    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]) &&
+                       cell_in(g, (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)));
     const int gi = ci0 + li + (n & 1), gj = cj0 + lj + ((n >> 1) & 1), gk = DIM == 3 ? ck0 + lk + ((n >> 2) & 1) : 0;
     const int64_t gn = valid ? (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk) : 0;
     const int64_t gid = valid ? (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)) : 0;
@@ -855,7 +858,7 @@ k_q1_apply_batched(const BLevel* __restrict__ L, const int* __restrict__ tile_st
     const int tx = (d.g.nc[0] + TT::TX - 1) / TT::TX, ty = (d.g.nc[1] + TT::TY - 1) / TT::TY;
     const int bx = local % tx, by = (local / tx) % ty, bz = local / (tx * ty);
     if constexpr (LANES) q1_apply_lanes_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);
-    else q1_apply_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);
+    else q1_apply_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz, &d.k);
 }
 
 int q1_tiles(const Geom& g, bool fp64, bool lanes) {
@@ -1037,7 +1040,8 @@ k_q1_resdiag(Geom g, ResConsts rk, DiagConsts dk, const double* __restrict__ U, 
     }
     const int cell = threadIdx.x;
     const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
-    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]);
+    const bool valid = (ci0 + li < g.nc[0]) && (cj0 + lj < g.nc[1]) && (DIM == 2 || ck0 + lk < g.nc[2]) &&
+                       cell_in(g, (int64_t)(ci0 + li) + (int64_t)g.nc[0] * ((int64_t)(cj0 + lj) + (int64_t)g.nc[1] * (ck0 + lk)));
     double el[NV][NC];
 #pragma unroll
     for (int n = 0; n < NV; ++n)
@@ -1322,6 +1326,7 @@ __global__ void k_q1_energy(Geom g, Phys ph, const double* __restrict__ U, doubl
     double eb = 0.0, ec = 0.0;
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < g.n_cells;
          cell += (int64_t)gridDim.x * blockDim.x) {
+        if (!cell_in(g, cell)) continue;
         int ci[3] = {0, 0, 0};
         int64_t r = cell;
         for (int a = 0; a < DIM; ++a) { ci[a] = (int)(r % g.nc[a]); r /= g.nc[a]; }

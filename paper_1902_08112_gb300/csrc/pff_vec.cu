@@ -471,21 +471,76 @@ template cudaError_t launch_cg_update_p<float>(const Geom&, float*, const float*
 // Gauss-Lobatto lumping on a uniform tensor grid: the nodal weight is the product over axes of
 // the 1D lumped weights (Q1: h/2 per adjacent cell; Q2: h/6 at cell vertices, 2h/3 at
 // midpoints), summed over the cells that share the node.
+// Gauss-Lobatto lumped mass: sum over the domain cells around the node of |K| times the product of
+// the 1D Lobatto weights (1/2, 1/2 for Q1; 1/6, 2/3, 1/6 for Q2) of the node's position in the cell.
 __global__ void k_lumped_mass(Geom g, double* __restrict__ M) {
     GRID_STRIDE(n, g.n_nodes) {
         int idx[3];
         node_ijk(g, n, idx[0], idx[1], idx[2]);
-        double w = 1.0;
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
         for (int a = 0; a < g.dim; ++a) {
-            const int i = idx[a], last = g.nn[a] - 1;
-            double wa;
-            if (g.deg == 1) wa = (i == 0 || i == last) ? 0.5 : 1.0;
-            else if (i % 2 == 1) wa = 2.0 / 3.0;
-            else wa = (i == 0 || i == last) ? 1.0 / 6.0 : 2.0 / 6.0;
-            w *= wa * g.h[a];
+            // cells c with deg c <= idx <= deg c + deg
+            lo[a] = idx[a] >= g.deg ? (idx[a] - 1) / g.deg : 0;
+            hi[a] = min(g.nc[a] - 1, idx[a] / g.deg);
         }
+        double w = 0.0;
+        for (int ck = lo[2]; ck <= hi[2]; ++ck)
+            for (int cj = lo[1]; cj <= hi[1]; ++cj)
+                for (int ci = lo[0]; ci <= hi[0]; ++ci) {
+                    const int64_t cell = (int64_t)ci + (int64_t)g.nc[0] * ((int64_t)cj + (int64_t)g.nc[1] * ck);
+                    if (!cell_in(g, cell)) continue;
+                    const int c3[3] = {ci, cj, ck};
+                    double wc = 1.0;
+                    for (int a = 0; a < g.dim; ++a) {
+                        const int loc = idx[a] - g.deg * c3[a];
+                        const double wa = g.deg == 1 ? 0.5 : (loc == 1 ? 2.0 / 3.0 : 1.0 / 6.0);
+                        wc *= wa * g.h[a];
+                    }
+                    w += wc;
+                }
         M[n] = w;
     }
+}
+
+// domain masks: a coarse cell is in the domain if any of its children is
+__global__ void k_coarsen_cell_mask(Geom gc, Geom gf, const uint8_t* __restrict__ mf, uint8_t* __restrict__ mc) {
+    GRID_STRIDE(c, gc.n_cells) {
+        const int i = (int)(c % gc.nc[0]), j = (int)((c / gc.nc[0]) % gc.nc[1]), k = (int)(c / ((int64_t)gc.nc[0] * gc.nc[1]));
+        const int kz = gc.dim == 3 ? 2 : 1;
+        uint8_t any = 0;
+        for (int dk = 0; dk < kz; ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int di = 0; di < 2; ++di)
+                    any |= mf[(int64_t)(2 * i + di) + (int64_t)gf.nc[0] * ((int64_t)(2 * j + dj) + (int64_t)gf.nc[1] * (kz == 2 ? 2 * k + dk : 0))] != 0;
+        mc[c] = any;
+    }
+}
+cudaError_t launch_coarsen_cell_mask(const Geom& gc, const Geom& gf, const uint8_t* mf, uint8_t* mc, cudaStream_t s) {
+    k_coarsen_cell_mask<<<grid_for(gc.n_cells), kThreads, 0, s>>>(gc, gf, mf, mc);
+    return count_launch(cudaGetLastError());
+}
+
+// nodes on no cell of the domain: every component fixed (identity rows)
+__global__ void k_outside_nodes(Geom g, uint8_t* __restrict__ mask) {
+    GRID_STRIDE(n, g.n_nodes) {
+        int idx[3];
+        node_ijk(g, n, idx[0], idx[1], idx[2]);
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) {
+            lo[a] = idx[a] >= g.deg ? (idx[a] - 1) / g.deg : 0;
+            hi[a] = min(g.nc[a] - 1, idx[a] / g.deg);
+        }
+        bool in = false;
+        for (int ck = lo[2]; ck <= hi[2]; ++ck)
+            for (int cj = lo[1]; cj <= hi[1]; ++cj)
+                for (int ci = lo[0]; ci <= hi[0]; ++ci)
+                    in = in || cell_in(g, (int64_t)ci + (int64_t)g.nc[0] * ((int64_t)cj + (int64_t)g.nc[1] * ck));
+        if (!in) mask[n] |= (uint8_t)(MASK_U_ALL | PFF_MASK_PHI_DIR);
+    }
+}
+cudaError_t launch_outside_nodes(const Geom& g, uint8_t* mask, cudaStream_t s) {
+    k_outside_nodes<<<grid_for(g.n_nodes), kThreads, 0, s>>>(g, mask);
+    return count_launch(cudaGetLastError());
 }
 cudaError_t launch_lumped_mass(const Geom& g, double* M, cudaStream_t s) {
     k_lumped_mass<<<grid_for(g.n_nodes), kThreads, 0, s>>>(g, M);
@@ -500,9 +555,11 @@ __global__ void k_active_set(Geom g, const double* __restrict__ R, const double*
     const int64_t nn = g.n_nodes;
     int na = 0, nch = 0;
     GRID_STRIDE(n, nn) {
-        const double lam = R[g.dim * nn + n] / M[n];
-        const bool act = lam + c * (U[g.dim * nn + n] - phi_old[n]) > thr;
         const uint8_t m = mask[n];
+        // prescribed phi (phi Dirichlet, nodes outside the domain) never enters the active set
+        const bool fixed = (m & PFF_MASK_PHI_DIR) != 0 || !(M[n] > 0.0);
+        const double lam = fixed ? 0.0 : R[g.dim * nn + n] / M[n];
+        const bool act = !fixed && lam + c * (U[g.dim * nn + n] - phi_old[n]) > thr;
         const bool was = (m & PFF_MASK_ACTIVE) != 0;
         mask[n] = (uint8_t)((m & ~PFF_MASK_ACTIVE) | (act ? PFF_MASK_ACTIVE : 0));
         na += act;

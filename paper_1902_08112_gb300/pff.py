@@ -21,7 +21,8 @@ MASK_UX, MASK_UY, MASK_UZ, MASK_ACTIVE, MASK_PHI_DIR = 1, 2, 4, 8, 16
 class Mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("n_cells", ctypes.c_int * 3),
                 ("n_levels", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("dirichlet_faces", ctypes.c_uint), ("dirichlet_mask", ctypes.c_void_p)]
+                ("dirichlet_faces", ctypes.c_uint), ("dirichlet_mask", ctypes.c_void_p),
+                ("cell_mask", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
@@ -154,7 +155,8 @@ def default_params(**kw) -> Params:
     return p
 
 
-def make_mesh(dim, degree, n_cells, n_levels, lo, hi, dirichlet_faces=0x3F) -> Mesh:
+def make_mesh(dim, degree, n_cells, n_levels, lo, hi, dirichlet_faces=0x3F, cell_mask=None) -> Mesh:
+    """cell_mask: optional host uint8 array of the finest level's cells (x fastest), 1 = in the domain."""
     m = Mesh()
     m.dim, m.degree, m.n_levels = dim, degree, n_levels
     for a in range(3):
@@ -163,6 +165,12 @@ def make_mesh(dim, degree, n_cells, n_levels, lo, hi, dirichlet_faces=0x3F) -> M
         m.hi[a] = float(hi[a]) if a < dim else 1.0
     m.dirichlet_faces = dirichlet_faces
     m.dirichlet_mask = None
+    m.cell_mask = None
+    if cell_mask is not None:
+        import numpy as np
+        arr = np.ascontiguousarray(cell_mask, dtype=np.uint8)
+        m._cell_mask_keep = arr          # the library copies it during pff_create_hierarchy
+        m.cell_mask = arr.ctypes.data
     return m
 
 

@@ -60,7 +60,8 @@ class PffBackend:
         self.restart = restart
 
     def mesh(self, w):
-        return self.pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi)
+        return self.pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi,
+                                  dirichlet_faces=w.dirichlet_faces, cell_mask=w.cell_mask())
 
     def bytes_for(self, w) -> int:
         return self.pff.hierarchy_bytes(self.mesh(w), self.restart) + 3 * w.n_dofs * 8
@@ -212,13 +213,17 @@ def summarize(results: dict, wall: float) -> dict:
 
 
 def poisson_requests(count: int, rate_per_s: float, sizes=(16, 24, 32), load_steps=2, seed: int = W.SEED,
-                     coarsest: int = 4) -> list:
-    """Seeded Poisson arrivals of random pressurised-crack instances (the batch recipe)."""
+                     coarsest: int = 4, lshape_every: int = 0, lshape_sizes=(16, 32)) -> list:
+    """Seeded Poisson arrivals of random pressurised-crack instances (the batch recipe); with
+    lshape_every = k every k-th request is a 3D L-shaped panel (edge 2^j cells, j from lshape_sizes)."""
     rng = np.random.default_rng(seed)
     inst = W.batch_instances(count, sizes=sizes, seed=seed, coarsest=coarsest)
     t = 0.0
     out = []
     for i, w in enumerate(inst):
         t += rng.exponential(1.0 / rate_per_s)
+        if lshape_every and i % lshape_every == lshape_every - 1:
+            n = int(rng.choice(lshape_sizes))
+            w = W.config_3d_lshape(n, n_levels=3 if n <= 16 else 4)
         out.append(Request(i, w, load_steps=load_steps, arrival=t))
     return out

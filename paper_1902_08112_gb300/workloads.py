@@ -53,6 +53,18 @@ class Workload:
     dirichlet_faces: int = ALL_FACES
     cracks: list = field(default_factory=list)
     seed: int = SEED
+    domain: str = "box"            # "box" or "lshape" (the box minus its x >= mid, y >= mid quarter)
+
+    def cell_mask(self):
+        """uint8 per cell (x fastest), 1 = in the domain; None for the whole box."""
+        if self.domain == "box":
+            return None
+        nx, ny = self.n_cells[0], self.n_cells[1]
+        i = np.arange(nx)[None, :]
+        j = np.arange(ny)[:, None]
+        plane = ~((i >= nx // 2) & (j >= ny // 2))
+        nz = self.n_cells[2] if self.dim == 3 else 1
+        return np.broadcast_to(plane, (nz, ny, nx)).ravel().astype(np.uint8)
 
     @property
     def edge(self) -> float:
@@ -99,6 +111,23 @@ def config_2d_two_cracks(n: int = 128, n_levels: int = 4, deg: int = 1) -> Workl
                  kappa=1e-10, pressure=10.0, eps_factor=1.0)
     w.cracks = [Crack((2.5, 1.15), (1.0, 0.0), 0.35, half_width=0.5),
                 Crack((1.0, 3.0), (0.0, 1.0), 0.5, half_width=0.5)]
+    return w.finalize()
+
+
+def config_3d_lshape(n: int = 32, n_levels: int = 4, deg: int = 1) -> Workload:
+    """L-shaped panel of Sec. 5.3 as a serving instance: [0,2]^2 minus [1,2]^2 extruded to a depth
+    of 0.5 (n x n x n/4 cells of edge 2/n), clamped on the face y = 0, no initial crack, loaded by
+    the pressure term (phi~^2 p, div w), which with phi = 1 acts as a normal traction p on the free
+    faces; E = 1, nu = 0.2, Gc = 1e-3."""
+    w = Workload("3d_lshape", 3, deg, (n, n, n // 4), n_levels, (0.0, 0.0, 0.0), (2.0, 2.0, 0.5), Gc=1e-3,
+                 pressure=1e-3, dirichlet_faces=1 << 2, domain="lshape")
+    return w.finalize()
+
+
+def config_2d_lshape(n: int = 32, n_levels: int = 4, deg: int = 1) -> Workload:
+    """2D L-shaped panel [0,2]^2 minus [1,2]^2, clamped on y = 0, loaded like config_3d_lshape."""
+    w = Workload("2d_lshape", 2, deg, (n, n), n_levels, (0.0, 0.0), (2.0, 2.0), Gc=1e-3, pressure=1e-3,
+                 dirichlet_faces=1 << 2, domain="lshape")
     return w.finalize()
 
 

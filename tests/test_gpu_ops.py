@@ -47,7 +47,9 @@ class Case:
         self.U, self.po, self.pt = U, po, pt
         self.prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu,
                                       Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f, split=split)
-        self.h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi), self.prm)
+        cm = w.cell_mask()
+        self.h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi,
+                                                    dirichlet_faces=w.dirichlet_faces, cell_mask=cm), self.prm)
         pff.set_kernel_variant(self.h, variant)
         es = W.modulus_field(w) if modulus else None
         if modulus:
@@ -55,10 +57,10 @@ class Case:
         pff.set_state(self.h, t(U), t(po), t(pt))
         act = W.random_active(w, active_fraction) if active_fraction > 0 else np.zeros(w.n_nodes, np.uint8)
         pff.set_active_set(self.h, t(act))
-        self.mesh = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi)
+        self.mesh = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi, cm)
         self.phys = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, f=f, escale=es,
                              split=split)
-        self.mask = fem.dirichlet_face_mask(self.mesh, 0x3F) | (act * fem.BIT_ACTIVE).astype(np.uint8)
+        self.mask = fem.dirichlet_face_mask(self.mesh, w.dirichlet_faces) | (act * fem.BIT_ACTIVE).astype(np.uint8)
         self.levels = mg.build_levels(self.mesh, w.n_levels, self.phys, U, pt, self.mask)
 
     def close(self):
@@ -89,6 +91,11 @@ CASES = {
     "3d_q1_split": (lambda: W.small(W.config_3d_penny(), 12, 2), 0, False, 1),
     "2d_q1_split": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 0, False, 1),
     "3d_q2_split": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1, False, 1),
+    # L-shaped domains (cell masks): fast path, lanes, generic Q2
+    "3d_q1_lshape": (lambda: W.small(W.config_3d_lshape(), (16, 16, 4), 2), 0),
+    "2d_q1_lshape": (lambda: W.small(W.config_2d_lshape(), 24, 3), 0),
+    "3d_q1_lshape_lanes": (lambda: W.small(W.config_3d_lshape(), (16, 16, 4), 2), 2),
+    "2d_q2_lshape": (lambda: W.small(W.config_2d_lshape(deg=2), 12, 2), 1),
 }
 
 

@@ -366,3 +366,65 @@ def test_miehe_split_derivatives(dim, deg):
     # symmetric displacement block
     Guu = G.toarray()[:dim * m.n_nodes, :dim * m.n_nodes]
     assert np.abs(Guu - Guu.T).max() <= 1e-13 * np.abs(Guu).max()
+
+
+def _lshape_mask(n):
+    """cells of [0,2]^2 minus [1,2]^2 on an n x n grid (x fastest)."""
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    return (~((i >= n // 2) & (j >= n // 2))).ravel().astype(np.uint8)
+
+
+@pytest.mark.parametrize("deg", [1, 2])
+def test_cell_mask_matches_union_of_boxes(deg):
+    """A cell-masked box (the L-shaped panel [0,2]^2 minus [1,2]^2) gives the residual, Jacobian and
+    lumped mass of assembling the two boxes [0,1]x[0,2] and [1,2]x[0,1] separately and adding them
+    on the shared nodes; nodes outside the domain get nothing; the lumped mass sums to |L| = 3."""
+    n = 4
+    m = fem.Mesh(2, deg, (n, n), (0.0, 0.0), (2.0, 2.0), _lshape_mask(n))
+    ph = fem.Phys(E=1.3, nu=0.25, p=0.02, eps=0.5, Gc=0.8, kappa=1e-3)
+    rng = np.random.default_rng(41)
+    U = np.concatenate([0.01 * rng.standard_normal(2 * m.n_nodes), rng.uniform(0.2, 1.0, m.n_nodes)])
+    pt = rng.uniform(0.0, 1.0, m.n_nodes)
+    A = fem.residual_A(m, ph, U, pt)
+    M = fem.lumped_mass(m)
+    X = m.node_coords()
+    parts = [fem.Mesh(2, deg, (n // 2, n), (0.0, 0.0), (1.0, 2.0)), fem.Mesh(2, deg, (n // 2, n // 2), (1.0, 0.0), (2.0, 1.0))]
+    A_ref = np.zeros_like(A)
+    M_ref = np.zeros_like(M)
+    for b in parts:
+        Xb = b.node_coords()
+        # global node index of every node of the part
+        key = {tuple(np.round(x, 9)): k for k, x in enumerate(X)}
+        gidx = np.array([key[tuple(np.round(x, 9))] for x in Xb])
+        Ub = np.concatenate([U[c * m.n_nodes + gidx] for c in range(3)])
+        Ab = fem.residual_A(b, ph, Ub, pt[gidx])
+        for c in range(3):
+            np.add.at(A_ref, c * m.n_nodes + gidx, Ab[c * b.n_nodes:(c + 1) * b.n_nodes])
+        np.add.at(M_ref, gidx, fem.lumped_mass(b))
+    np.testing.assert_allclose(A, A_ref, rtol=0, atol=1e-13 * np.abs(A_ref).max())
+    np.testing.assert_allclose(M, M_ref, rtol=0, atol=1e-15)
+    assert M.sum() == pytest.approx(3.0, rel=1e-14)
+    outside = ~m.node_touches_domain()
+    assert outside.sum() > 0 and np.all(M[outside] == 0.0)
+    dm = fem.dirichlet_face_mask(m, 0)
+    assert np.all(dm[outside] == (fem.BIT_U[0] | fem.BIT_U[1] | fem.BIT_PHI_DIR))
+    G = fem.assemble(m, ph, U, pt, dm)
+    cons = fem.constrained_dofs(m, dm)
+    Gd = G.toarray()
+    assert np.array_equal(np.diag(Gd)[cons], np.ones(cons.sum()))
+
+
+def test_cell_mask_coarsening_and_energy():
+    """Coarse cell masks keep a cell whose children are in the domain; the energy of an affine
+    field on the L-shape is E_s |L| (phi = 1, p = 0)."""
+    n = 8
+    m = fem.Mesh(2, 1, (n, n), (0.0, 0.0), (2.0, 2.0), _lshape_mask(n))
+    c = m.coarsen()
+    np.testing.assert_array_equal(c.cell_mask, _lshape_mask(n // 2))
+    ph = fem.Phys(E=2.0, nu=0.3, p=0.0, eps=0.5, Gc=1.0)
+    mu, lam = fem.lame(2.0, 0.3)
+    Aff = np.array([[0.01, 0.004], [-0.002, 0.006]])
+    U = np.concatenate([_affine_u(m, Aff), np.ones(m.n_nodes)])
+    e = 0.5 * (Aff + Aff.T)
+    Es = 0.5 * lam * np.trace(e) ** 2 + mu * np.sum(e * e)
+    assert fem.energy(m, ph, U) == pytest.approx(Es * 3.0, rel=1e-12)
