@@ -255,6 +255,58 @@ def bench_multi(n: int, dev):
     return out
 
 
+def bench_variants(n: int, dev):
+    """Next-row variants on the 3D penny crack (n^3 Q1, smooth displacement, active set of
+    Algorithm 1): P_full vs P_diag (Sec. 3.3), the Miehe split (Sec. 2.1, generic kernels) and a
+    spatially varying E.  Per variant: FP64-accurate fine apply time and a 1e-8 FGMRES solve of the
+    Newton right-hand side with the FP32 V-cycle."""
+    import torch
+    from paper_1902_08112_gb300 import pff, workloads as W
+    w = W.config_3d_penny(n=n, n_levels=4)
+    U, po, pt = W.initial_state(w, displacement="smooth")
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": f"3d_penny_q1_{n}", "n_dofs": w.n_dofs}
+    cases = {"p_full": dict(), "p_diag": dict(preconditioner=1), "miehe_split": dict(split=1),
+             "varying_E": dict()}
+    for name, extra in cases.items():
+        prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
+                                 mg_precision=32, **extra)
+        h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm, stream)
+        try:
+            with torch.cuda.stream(stream):
+                Ud, pod, ptd = (torch.from_numpy(a).to(dev) for a in (U, po, pt))
+                x = torch.randn(w.n_dofs, dtype=torch.float64, device=dev)
+                y = torch.empty_like(x)
+                R = torch.empty_like(x)
+                xs = torch.zeros_like(x)
+                es = torch.from_numpy(W.modulus_field(w)).to(dev) if name == "varying_E" else None
+            stream.synchronize()
+            if es is not None:
+                pff.set_modulus(h, es)
+            pff.set_state(h, Ud, pod, ptd)
+            pff.update_active_set(h)
+            pff.setup(h)
+            pff.apply_jacobian(h, -1, x, y)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                pff.apply_jacobian(h, -1, x, y)
+            e1.record(stream)
+            e1.synchronize()
+            pff.residual(h, R)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=300, allow_noconv=True)
+            stream.synchronize()
+            out[name] = {"apply64_ms": e0.elapsed_time(e1) / 5, "solve_ms": (time.perf_counter() - t0) * 1e3,
+                         "iterations": info.iterations, "converged": bool(info.converged)}
+        finally:
+            pff.destroy_hierarchy(h)
+    return out
+
+
 def bench_serve(count: int):
     """Serving pattern: Poisson arrivals of random pressurised-crack requests (N in {16,24,32}) mixed
     with 3D L-shaped panels (every 4th request), 2 load steps each, served by the
@@ -324,6 +376,7 @@ def main():
     ap.add_argument("--batch", type=int, default=32, help="instances in the batching measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving measurement (0: skip)")
     ap.add_argument("--multi", type=int, default=256, help="cells per edge of the multi-crack measurement (0: skip)")
+    ap.add_argument("--variants", type=int, default=64, help="cells per edge of the variant measurements (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -534,6 +587,8 @@ def main():
         line["serve"] = bench_serve(args.serve)
     if args.multi > 0:
         line["multi_crack"] = bench_multi(args.multi, dev)
+    if args.variants > 0:
+        line["variants"] = bench_variants(args.variants, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline()
         line["cpu_baseline"] = cb
