@@ -97,8 +97,10 @@ typedef struct {
  *  seed           seed of the SplitMix64 start vector of the CG eigenvalue estimate.
  *  split          0: no split of the elastic energy (E_s^+ = E_s, default); 1: Miehe split (Sec. 2.1):
  *                 E_s^+ = lambda/2 <tr e>_+^2 + mu tr(e_+^2) over the strain eigenvalues, sigma^+ its
- *                 derivative; g(phi) degrades only the + part.  Operators then run in the generic
- *                 kernels (any degree); batches require 0.
+ *                 derivative; g(phi) degrades only the + part.  Q1 levels store the Gauss-point
+ *                 tangent of g sigma^+ + sigma^- (28 coefficients per Gauss point in 3D, allocated
+ *                 on first use, not counted by pff_hierarchy_bytes); residuals, diagonals and Q2 use
+ *                 the generic kernels; batches require 0.
  *  preconditioner 0: P_full = MG(G~), the monolithic V-cycle (Sec. 3.3, default);
  *                 1: P_diag = blockdiag(MG(U~), MG(P~)) (Sec. 3.3): the coupling G_phiu is
  *                 left out of every V-cycle residual and of the coarse solve.  Batches

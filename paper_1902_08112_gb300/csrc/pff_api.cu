@@ -129,6 +129,19 @@ static cudaError_t dalloc(pff_hierarchy* h, T** p, size_t count) {
     return cudaMemsetAsync(q, 0, count * sizeof(T) + 16, h->stream);
 }
 
+// Gauss-point tangent storage of the Miehe split on Q1 levels (allocated when the split is first used)
+static cudaError_t ensure_split_storage(pff_hierarchy* h) {
+    if (!h->ph.split) return cudaSuccess;
+    for (auto& L : h->lv) {
+        if (L.g.deg != 1 || L.qps64) continue;
+        const size_t nq = (size_t)q1_nks(L.g.dim) * (size_t)(1 << L.g.dim) * (size_t)L.g.n_cells;
+        cudaError_t e = dalloc(h, &L.qps32, nq);
+        if (e == cudaSuccess) e = dalloc(h, &L.qps64, nq);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_params* params, void* cuda_stream,
                                            pff_hierarchy** out) {
     if (!out) return PFF_EINVAL;
@@ -211,6 +224,14 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
     if (e == cudaSuccess) e = dalloc(h, &h->d_counts, 16);
     if (e == cudaSuccess) e = dalloc(h, &h->d_scal, 4096);
     if (e == cudaSuccess) e = dalloc(h, &h->d_scratch, (size_t)dot_partials() * 64);
+    if (e != cudaSuccess) {
+        st = (e == cudaErrorMemoryAllocation) ? PFF_ENOMEM : PFF_ECUDA;
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return st;
+    }
+    if (e == cudaSuccess) e = ensure_split_storage(h);
     if (e != cudaSuccess) {
         st = (e == cudaErrorMemoryAllocation) ? PFF_ENOMEM : PFF_ECUDA;
         cudaGetLastError();
@@ -324,6 +345,14 @@ extern "C" pff_status pff_set_params(pff_hierarchy* h, const pff_params* params)
     REQUIRE(h, !why, PFF_EINVAL, why ? why : "");
     h->prm = *params;
     h->ph = make_phys(*params);
+    {
+        cudaError_t e = ensure_split_storage(h);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->err = "pff_set_params: no device memory for the split's Gauss-point data";
+            return e == cudaErrorMemoryAllocation ? PFF_ENOMEM : PFF_ECUDA;
+        }
+    }
     if (h->has_state) CUDA_OR_FAIL(h, propagate_state(h));   // linearisation data depend on the physics
     h->stale = true;
     return PFF_OK;

@@ -66,6 +66,8 @@ struct Level {
     float2* qpd64 = nullptr;     // Q1: the same as df64 pairs (hi, lo)
     double* es_buf = nullptr;    // storage of g.es once a varying modulus is set
     uint8_t* cm_buf = nullptr;   // storage of g.cm (domains cut from the box)
+    float* qps32 = nullptr;      // Q1 with the Miehe split: Gauss-point tangent data, FP32
+    float2* qps64 = nullptr;     // the same as df64 pairs
     double lam_min[2] = {1, 1};  // eigenvalue estimates of D^-1 G_bb, blocks u / phi
     double lam_max[2] = {1, 1};
 };

@@ -37,7 +37,16 @@ struct Q1Dims {
     static constexpr int NC = DIM + 1;
     static constexpr int NK = DIM == 3 ? 8 : 5; // stored coefficients per Gauss point
     static constexpr int NS = DIM == 3 ? 6 : 3; // symmetric tensor components
+    // Miehe split: symmetric Voigt tangent K (upper triangle), Sp, c1 per Gauss point
+    static constexpr int NKK = NS * (NS + 1) / 2;
+    static constexpr int NKS = NKK + NS + 1;
 };
+
+// upper-triangle position of (a, b) in a symmetric NS x NS matrix stored row by row
+template <int NS>
+__host__ __device__ constexpr int ut_idx(int a, int b) {
+    return a <= b ? a * NS - a * (a - 1) / 2 + (b - a) : b * NS - b * (b - 1) / 2 + (a - b);
+}
 
 // symmetric index helpers: (i,j) -> 0..NS-1 with diagonal first: 3D xx yy zz xy xz yz; 2D xx yy xy
 template <int DIM>
@@ -243,6 +252,112 @@ cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, 
     return count_launch(cudaGetLastError());
 }
 
+// ------------------------------------------------------------------ linearisation data, Miehe split
+// With the split (Sec. 2.1) the displacement block is no longer isotropic: per Gauss point the
+// tangent of g(phi~) sigma^+ + sigma^- is stored as a symmetric Voigt matrix K (engineering shear
+// strains, upper triangle), together with Sp = w [2 f (1-k) phi sigma^+(u) + 2 p phi I] and
+// c1 = w [2 f (1-k) E_s^+ + 2 p div u + Gc/eps].  Native FP64 (eigen-decompositions); once per state.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_q1_linearize_split(Geom g, Phys ph, const double* __restrict__ U,
+                                                            const double* __restrict__ pt, double gpt,
+                                                            float* __restrict__ q32, float2* __restrict__ q64) {
+    using D = Q1Dims<DIM>;
+    constexpr int NV = D::NV, NS = D::NS, NKK = D::NKK, NKS = D::NKS;
+    const int64_t nc = g.n_cells, nn = g.n_nodes;
+    double vol = 1.0;
+    for (int a = 0; a < DIM; ++a) vol *= g.h[a];
+    const double w = vol / NV;
+    double gp[DIM + 1];
+    gp[0] = 1.0;
+    for (int j = 1; j <= DIM; ++j) gp[j] = gp[j - 1] * gpt;
+    // Voigt index -> tensor indices (diagonal first, then xy xz yz / xy)
+    const int vi[6] = {0, 1, DIM == 3 ? 2 : 0, 0, 0, 1}, vj[6] = {0, 1, DIM == 3 ? 2 : 1, 1, 2, 2};
+    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < nc;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        if (!cell_in(g, cell)) continue;
+        int ci[3] = {0, 0, 0};
+        int64_t r = cell;
+        for (int a = 0; a < DIM; ++a) { ci[a] = (int)(r % g.nc[a]); r /= g.nc[a]; }
+        const double sE = g.es ? g.es[cell] : 1.0;
+        const double cmu = ph.mu * sE, clam = ph.lam * sE;
+        double mu_[DIM][NV], mphi[NV], mpt[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) {
+            const int i = ci[0] + (n & 1), j = ci[1] + ((n >> 1) & 1), k = DIM == 3 ? ci[2] + ((n >> 2) & 1) : 0;
+            const int64_t node = (int64_t)i + (int64_t)g.nn[0] * ((int64_t)j + (int64_t)g.nn[1] * k);
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) mu_[c][n] = U[c * nn + node];
+            mphi[n] = U[DIM * nn + node];
+            mpt[n] = pt[node];
+        }
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) fwd<DIM>(mu_[c]);
+        fwd<DIM>(mphi);
+        fwd<DIM>(mpt);
+        for (int q = 0; q < NV; ++q) {
+            double e3[3][3] = {{0.0}}, phi = 0.0, ptv = 0.0, tr = 0.0;
+            for (int k = 0; k < NV; ++k) {
+                const double sc = sgn(k, q) * gp[popc(k)] / NV;
+                phi += sc * mphi[k];
+                ptv += sc * mpt[k];
+            }
+            double gu[DIM][DIM];
+            for (int c = 0; c < DIM; ++c)
+                for (int d = 0; d < DIM; ++d) {
+                    double acc = 0.0;
+                    for (int kp = 0; kp < NV; ++kp) {
+                        if (kp & (1 << d)) continue;
+                        acc += sgn(kp, q) * gp[popc(kp)] * mu_[c][kp | (1 << d)];
+                    }
+                    gu[c][d] = acc * (2.0 / (g.h[d] * NV));
+                }
+            for (int i = 0; i < DIM; ++i)
+                for (int j = 0; j < DIM; ++j) e3[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
+            for (int i = 0; i < DIM; ++i) tr += e3[i][i];
+            double sp[3][3], Esp;
+            SplitEig<double> se;
+            split_stress(cmu, clam, DIM, e3, sp, Esp, se);
+            const double gk = (1.0 - ph.kappa) * ptv * ptv + ph.kappa;
+            double vals[NKS];
+            for (int b = 0; b < NS; ++b) {
+                // unit engineering strain b: e_ii = 1 or e_ij = e_ji = 1/2
+                double E[3][3] = {{0.0}}, cp[3][3];
+                if (vi[b] == vj[b]) E[vi[b]][vi[b]] = 1.0;
+                else { E[vi[b]][vj[b]] = 0.5; E[vj[b]][vi[b]] = 0.5; }
+                split_tangent(cmu, clam, DIM, se, E, cp);
+                const double trE = vi[b] == vj[b] ? 1.0 : 0.0;
+                for (int a = b; a < NS; ++a) {
+                    const int i = vi[a], j = vj[a];
+                    const double full = 2.0 * cmu * E[i][j] + (i == j ? clam * trE : 0.0);
+                    vals[ut_idx<NS>(b, a)] = w * (full - (1.0 - gk) * cp[i][j]);
+                }
+            }
+            for (int a = 0; a < NS; ++a) {
+                const int i = vi[a], j = vj[a];
+                vals[NKK + a] = w * (2.0 * ph.f * (1.0 - ph.kappa) * phi * sp[i][j] + (i == j ? 2.0 * ph.p * phi : 0.0));
+            }
+            vals[NKS - 1] = w * (2.0 * ph.f * (1.0 - ph.kappa) * Esp + 2.0 * ph.p * tr + ph.Gc / ph.eps);
+            for (int k = 0; k < NKS; ++k) {
+                const int64_t idx = (int64_t)(q * NKS + k) * nc + cell;
+                const float hi = __double2float_rn(vals[k]);
+                q32[idx] = hi;
+                q64[idx] = make_float2(hi, __double2float_rn(vals[k] - (double)hi));
+            }
+        }
+    }
+}
+
+cudaError_t launch_q1_linearize_split(const Geom& g, const Phys& ph, const double* U, const double* pt, float* q32,
+                                      float2* q64, cudaStream_t s) {
+    const double gpt = 1.0 / sqrt(3.0);
+    int64_t blocks = (g.n_cells + 127) / 128;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    if (g.dim == 3) k_q1_linearize_split<3><<<(int)blocks, 128, 0, s>>>(g, ph, U, pt, gpt, q32, q64);
+    else k_q1_linearize_split<2><<<(int)blocks, 128, 0, s>>>(g, ph, U, pt, gpt, q32, q64);
+    return count_launch(cudaGetLastError());
+}
+
 // ------------------------------------------------------------------ modal apply
 template <int DIM, typename S>
 struct Q1Tile;
@@ -298,15 +413,46 @@ template <> struct QData<df64> {
     }
 };
 
+// Miehe split: flux of the displacement block at one Gauss point, sigma = K eps with the stored
+// symmetric Voigt tangent K (upper triangle at base + ut_idx * stride) and the engineering strain
+// eps of the gradient g_ of du.
+template <int DIM, typename S, typename QT>
+__device__ __forceinline__ void split_flux(const QT* qd, int64_t base, int64_t stride, const S (&g_)[DIM][DIM],
+                                           S (&fu)[DIM][DIM]) {
+    constexpr int NS = Q1Dims<DIM>::NS;
+    S ev[NS], sv[NS];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = i; j < DIM; ++j) ev[sidx<DIM>(i, j)] = (i == j) ? g_[i][i] : g_[i][j] + g_[j][i];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) sv[a] = Scalar<S>::zero();
+#pragma unroll
+    for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int b = a; b < NS; ++b) {
+            const S kab = QData<S>::get(qd, base + (int64_t)ut_idx<NS>(a, b) * stride);
+            sv[a] = sv[a] + kab * ev[b];
+            if (a != b) sv[b] = sv[b] + kab * ev[a];
+        }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = i; j < DIM; ++j) {
+            fu[i][j] = sv[sidx<DIM>(i, j)];
+            fu[j][i] = fu[i][j];
+        }
+}
+
 // kg: the Gauss-point scalings in global memory (batched launches), nullptr to read them from the
-// kernel parameters (a.k)
-template <int DIM, typename S, bool BLOCKDIAG>
+// kernel parameters (a.k).  SPLIT: Gauss-point data of the Miehe split (K, Sp, c1).
+template <int DIM, typename S, bool BLOCKDIAG, bool SPLIT = false>
 __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
                                               int bx, int by, int bz, const Q1Consts* __restrict__ kg = nullptr) {
     using T = Q1Tile<DIM, S>;
     using D = Q1Dims<DIM>;
     using St = typename Scalar<S>::storage;
-    constexpr int NV = D::NV, NC = D::NC, NK = D::NK;
+    constexpr int NV = D::NV, NC = D::NC, NK = SPLIT ? D::NKS : D::NK, SPO = SPLIT ? D::NKK : 1;
     constexpr int NCELL = T::TX * T::TY * T::TZ;
     constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = DIM == 3 ? T::TZ + 1 : 1;
     constexpr int NT = NTX * NTY * NTZ;
@@ -393,7 +539,9 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                 for (int c = 0; c < DIM; ++c)
 #pragma unroll
                     for (int d = 0; d < DIM; ++d) g_[c][d] = gd[c][d][(q & ((1 << d) - 1)) | ((q >> (d + 1)) << d)];
-                const S c0 = QData<S>::get(a.qd, (int64_t)(q * NK + 0) * g.n_cells + gid);
+                S fs[DIM][DIM];
+                if constexpr (SPLIT) split_flux<DIM, S>(a.qd, (int64_t)(q * NK) * g.n_cells + gid, g.n_cells, g_, fs);
+                const S c0 = SPLIT ? Scalar<S>::zero() : QData<S>::get(a.qd, (int64_t)(q * NK + 0) * g.n_cells + gid);
                 S tr = g_[0][0];
 #pragma unroll
                 for (int i = 1; i < DIM; ++i) tr = tr + g_[i][i];
@@ -404,7 +552,7 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                     for (int i = 0; i < DIM; ++i)
 #pragma unroll
                         for (int j = i; j < DIM; ++j) {
-                            const S sp = QData<S>::get(a.qd, (int64_t)(q * NK + 1 + sidx<DIM>(i, j)) * g.n_cells + gid);
+                            const S sp = QData<S>::get(a.qd, (int64_t)(q * NK + SPO + sidx<DIM>(i, j)) * g.n_cells + gid);
                             cp = cp + sp * ((i == j) ? g_[i][i] : g_[i][j] + g_[j][i]);   // Sp : e(du)
                         }
                 }
@@ -415,7 +563,7 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
                     for (int j = i; j < DIM; ++j) {
                         // c0 sigma(du)_ij with sigma = 2 mu e + lambda tr I and 2 e_ij = du_i,j + du_j,i
                         const S sg = (i == j) ? mu2 * g_[i][i] + ltr : mu * (g_[i][j] + g_[j][i]);
-                        const S f = c0 * sg;
+                        const S f = SPLIT ? fs[i][j] : c0 * sg;
                         const int ji = (q & ((1 << j) - 1)) | ((q >> (j + 1)) << j);
                         ps[i][j][ji] = ps[i][j][ji] + f;
                         if (i != j) {
@@ -730,11 +878,11 @@ __device__ __forceinline__ void q1_apply_lanes_tile(
 // Lane apply without shared memory: every lane reads its node's x from global memory (neighbour
 // cells hit the caches) and adds its contribution to y with one atomic per component; no CTA
 // barrier.  Same arithmetic as q1_apply_lanes_tile.
-template <int DIM, typename S, bool BLOCKDIAG>
+template <int DIM, typename S, bool BLOCKDIAG, bool SPLIT = false>
 __global__ void __launch_bounds__(256) k_q1_apply_direct(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
     using T = LaneTile<DIM>;
     using D = Q1Dims<DIM>;
-    constexpr int NV = D::NV, NC = D::NC, NK = D::NK;
+    constexpr int NV = D::NV, NC = D::NC, NK = SPLIT ? D::NKS : D::NK, SPO = SPLIT ? D::NKK : 1;
     const Geom& g = a.g;
     const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = DIM == 3 ? blockIdx.z * T::TZ : 0;
     const int64_t nn = g.n_nodes;
@@ -770,7 +918,7 @@ __global__ void __launch_bounds__(256) k_q1_apply_direct(Q1ApplyArgs<typename Sc
     S dphi, gphi[DIM];
     lane_eval<DIM, S, true>(xv[DIM], n, k, dphi, gphi);
     const int64_t qbase = (int64_t)(n * NK) * g.n_cells + gid;
-    const S c0 = valid ? QData<S>::get(a.qd, qbase) : Scalar<S>::zero();
+    const S c0 = (valid && !SPLIT) ? QData<S>::get(a.qd, qbase) : Scalar<S>::zero();
     const S c1 = valid ? QData<S>::get(a.qd, qbase + (int64_t)(NK - 1) * g.n_cells) : Scalar<S>::zero();
     S tr = gd[0][0];
 #pragma unroll
@@ -786,13 +934,16 @@ __global__ void __launch_bounds__(256) k_q1_apply_direct(Q1ApplyArgs<typename Sc
             fu[i][j] = f;
             fu[j][i] = f;
         }
+    if constexpr (SPLIT) {
+        if (valid) split_flux<DIM, S>(a.qd, qbase, g.n_cells, gd, fu);
+    }
     S fp = c1 * dphi;
     if constexpr (!BLOCKDIAG) {
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
             for (int j = i; j < DIM; ++j) {
-                const S sp = valid ? QData<S>::get(a.qd, qbase + (int64_t)(1 + sidx<DIM>(i, j)) * g.n_cells)
+                const S sp = valid ? QData<S>::get(a.qd, qbase + (int64_t)(SPO + sidx<DIM>(i, j)) * g.n_cells)
                                    : Scalar<S>::zero();
                 fp = fp + sp * ((i == j) ? gd[i][i] : gd[i][j] + gd[j][i]);
             }
@@ -811,10 +962,10 @@ __global__ void __launch_bounds__(256) k_q1_apply_direct(Q1ApplyArgs<typename Sc
     }
 }
 
-template <int DIM, typename S, bool BLOCKDIAG>
+template <int DIM, typename S, bool BLOCKDIAG, bool SPLIT = false>
 __global__ void __launch_bounds__(Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ, Q1Tile<DIM, S>::MINB)
 k_q1_apply(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
-    q1_apply_tile<DIM, S, BLOCKDIAG>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    q1_apply_tile<DIM, S, BLOCKDIAG, SPLIT>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int DIM, typename S, bool BLOCKDIAG>
@@ -975,6 +1126,59 @@ cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, co
     if (lanes || direct)
         return blockdiag ? launch_lanes_dim<float, true>(a, s, direct) : launch_lanes_dim<float, false>(a, s, direct);
     return blockdiag ? launch_apply_dim<float, true>(a, s) : launch_apply_dim<float, false>(a, s);
+}
+
+// Miehe split (Gauss-point tangent K): FP64-accurate operator as atomic lanes, FP32 per cell
+template <typename S, bool BD, typename A>
+static cudaError_t launch_split_dim(const A& a, cudaStream_t s) {
+    if constexpr (sizeof(typename Scalar<S>::storage) == 8) {
+        if (a.g.dim == 3) {
+            using T = LaneTile<3>;
+            dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, (a.g.nc[2] + T::TZ - 1) / T::TZ);
+            k_q1_apply_direct<3, S, BD, true><<<grid, 256, 0, s>>>(a);
+        } else {
+            using T = LaneTile<2>;
+            dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, 1);
+            k_q1_apply_direct<2, S, BD, true><<<grid, 256, 0, s>>>(a);
+        }
+    } else {
+        if (a.g.dim == 3) {
+            using T = Q1Tile<3, S>;
+            dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, (a.g.nc[2] + T::TZ - 1) / T::TZ);
+            k_q1_apply<3, S, BD, true><<<grid, T::TX * T::TY * T::TZ, 0, s>>>(a);
+        } else {
+            using T = Q1Tile<2, S>;
+            dim3 grid((a.g.nc[0] + T::TX - 1) / T::TX, (a.g.nc[1] + T::TY - 1) / T::TY, 1);
+            k_q1_apply<2, S, BD, true><<<grid, T::TX * T::TY, 0, s>>>(a);
+        }
+    }
+    return count_launch(cudaGetLastError());
+}
+
+cudaError_t launch_q1_apply_split64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
+                                    const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s) {
+    Q1ApplyArgs<double, float2> a;
+    a.g = g;
+    a.qd = qd;
+    a.x = x;
+    a.y = y;
+    a.mask = mask;
+    a.phi_bits = phi_bits;
+    fill_consts(a, ph);
+    return blockdiag ? launch_split_dim<df64, true>(a, s) : launch_split_dim<df64, false>(a, s);
+}
+
+cudaError_t launch_q1_apply_split32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
+                                    const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s) {
+    Q1ApplyArgs<float, float> a;
+    a.g = g;
+    a.qd = qd;
+    a.x = x;
+    a.y = y;
+    a.mask = mask;
+    a.phi_bits = phi_bits;
+    fill_consts(a, ph);
+    return blockdiag ? launch_split_dim<float, true>(a, s) : launch_split_dim<float, false>(a, s);
 }
 
 // ------------------------------------------------------------------ residual and diagonal (FP64)

@@ -56,4 +56,13 @@ cudaError_t launch_q1_diagonal(const Geom& g, const Phys& ph, const float2* q64,
 cudaError_t launch_q1_energies(const Geom& g, const Phys& ph, const double* U, double* part, double* out,
                                cudaStream_t s);
 
+// Miehe split: Gauss-point tangent data (NKS coefficients per Gauss point) and the applies that use it
+cudaError_t launch_q1_linearize_split(const Geom& g, const Phys& ph, const double* U, const double* pt, float* q32,
+                                      float2* q64, cudaStream_t s);
+cudaError_t launch_q1_apply_split64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
+                                    const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
+cudaError_t launch_q1_apply_split32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
+                                    const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
+inline int q1_nks(int dim) { return dim == 3 ? 28 : 10; }
+
 }  // namespace pff

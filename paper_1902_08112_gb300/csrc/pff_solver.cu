@@ -58,7 +58,15 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
         if (e0 && e1) CK(cudaEventRecord(e0, h->stream));
     }
     if (preset) CK(launch_init_masked<T>(L.g, L.mask, MASK_U_ALL, phi_bits, x, y, T(0), h->stream));
-    if (h->fast_q1 && L.g.deg == 1 && !h->ph.split && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
+    if (h->fast_q1 && L.g.deg == 1 && h->ph.split && L.qps64 && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
+        const bool bd = op == OP_APPLY_BLOCKDIAG;
+        if constexpr (sizeof(T) == 8)
+            CK(launch_q1_apply_split64(L.g, h->ph, L.qps64, (const double*)x, (double*)y, L.mask, phi_bits, bd,
+                                       h->stream));
+        else
+            CK(launch_q1_apply_split32(L.g, h->ph, L.qps32, (const float*)x, (float*)y, L.mask, phi_bits, bd,
+                                       h->stream));
+    } else if (h->fast_q1 && L.g.deg == 1 && !h->ph.split && (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
         const bool bd = op == OP_APPLY_BLOCKDIAG;
         if constexpr (sizeof(T) == 8)
             CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd,
@@ -150,6 +158,8 @@ cudaError_t propagate_state(pff_hierarchy* h, bool values) {
         CK(launch_cast_f64_f32(L.U64, L.U32, n_dofs(L.g), h->stream));
         CK(launch_cast_f64_f32(L.pt64, L.pt32, L.g.n_nodes, h->stream));
         if (L.qpd64 && !h->ph.split) CK(launch_q1_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
+        if (L.qps64 && h->ph.split)
+            CK(launch_q1_linearize_split(L.g, h->ph, L.U64, L.pt64, L.qps32, L.qps64, h->stream));
     }
     h->stale = true;
     return cudaSuccess;

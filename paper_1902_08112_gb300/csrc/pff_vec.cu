@@ -535,7 +535,7 @@ __global__ void k_outside_nodes(Geom g, uint8_t* __restrict__ mask) {
             for (int cj = lo[1]; cj <= hi[1]; ++cj)
                 for (int ci = lo[0]; ci <= hi[0]; ++ci)
                     in = in || cell_in(g, (int64_t)ci + (int64_t)g.nc[0] * ((int64_t)cj + (int64_t)g.nc[1] * ck));
-        if (!in) mask[n] |= (uint8_t)(MASK_U_ALL | PFF_MASK_PHI_DIR);
+        if (!in) mask[n] |= (uint8_t)((g.dim == 3 ? MASK_U_ALL : (PFF_MASK_UX | PFF_MASK_UY)) | PFF_MASK_PHI_DIR);
     }
 }
 cudaError_t launch_outside_nodes(const Geom& g, uint8_t* mask, cudaStream_t s) {

@@ -87,8 +87,10 @@ CASES = {
     "3d_q1_modulus": (lambda: W.small(W.config_3d_penny(), 20, 3), 0, True),
     "3d_q1_lanes_modulus": (lambda: W.small(W.config_3d_penny(), 12, 2), 2, True),
     "2d_q2_modulus": (lambda: W.small(W.config_2d_single_crack(deg=2), 12, 2), 1, True),
-    # Miehe split (generic kernels); random states mix tension and compression
+    # Miehe split (Q1: Gauss-point tangent data; variant 1 and Q2: generic kernels); random states
+    # mix tension and compression
     "3d_q1_split": (lambda: W.small(W.config_3d_penny(), 12, 2), 0, False, 1),
+    "3d_q1_split_generic": (lambda: W.small(W.config_3d_penny(), 12, 2), 1, False, 1),
     "2d_q1_split": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 0, False, 1),
     "3d_q2_split": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1, False, 1),
     # L-shaped domains (cell masks): fast path, lanes, generic Q2
