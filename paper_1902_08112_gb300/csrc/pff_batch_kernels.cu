@@ -273,18 +273,30 @@ __global__ void kb_dots2_final(const double* __restrict__ part, int P, double* _
 }
 
 // FGMRES on the finest levels: h[inst * ldh + j] = V_j . w for j < k (two stages)
+// <V_j, w> for j < k, eight basis vectors per pass over w (their sums kept in registers)
 __global__ void kb_multidot_partial(const BLevel* __restrict__ L, int k, int sw, double* __restrict__ part, int kmax) {
+    constexpr int G = 8;
     const BLevel& d = L[blockIdx.y];
     const int64_t nd = d.valid ? n_dofs(d.g) : 0;
     const double* w = d.valid ? bvec<double>(d, sw) : nullptr;
-    for (int j = 0; j < k; ++j) {
-        double s = 0.0;
+    const double* V = d.valid ? bvec<double>(d, bsel(BV_KV, 0)) : nullptr;
+    for (int j0 = 0; j0 < k; j0 += G) {
+        const int kk = min(G, k - j0);
+        double s[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) s[t] = 0.0;
         if (d.valid) {
-            const double* v = bvec<double>(d, bsel(BV_KV, j));
-            BSTRIDE(i, nd) s += v[i] * w[i];
+            BSTRIDE(i, nd) {
+                const double wi = w[i];
+#pragma unroll
+                for (int t = 0; t < G; ++t)
+                    if (t < kk) s[t] += V[(int64_t)(j0 + t) * nd + i] * wi;
+            }
         }
-        s = bblock_sum(s);
-        if (threadIdx.x == 0) part[((int64_t)blockIdx.y * kmax + j) * gridDim.x + blockIdx.x] = s;
+        for (int t = 0; t < kk; ++t) {
+            const double v = bblock_sum(s[t]);
+            if (threadIdx.x == 0) part[((int64_t)blockIdx.y * kmax + j0 + t) * gridDim.x + blockIdx.x] = v;
+        }
     }
 }
 __global__ void kb_multidot_final(const double* __restrict__ part, int P, int k, int kmax, double* __restrict__ h,

@@ -705,20 +705,36 @@ cudaError_t launch_newton_rhs(const Geom& g, const double* R, const double* t, c
 
 // ---------------------------------------------------------------- FGMRES kernels
 // h[j] = V_j . w for j < k (two stages, fixed order); V column-major with leading dim ld.
-__global__ void k_multidot_partial(int64_t n, const double* __restrict__ V, int64_t ld, int k,
-                                   const double* __restrict__ w, double* __restrict__ part) {
-    __shared__ double sh[32];
-    for (int j = 0; j < k; ++j) {
-        double s = 0.0;
-        GRID_STRIDE(i, n) s += V[j * ld + i] * w[i];
-        s = warp_sum(s);
-        const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
-        if (l == 0) sh[wid] = s;
+// Partial dots <V_j, w> for j < k: each thread reads w once per group of 8 basis vectors and keeps
+// the group's 8 sums in registers; per-CTA partials in a fixed order (deterministic).
+constexpr int kMultiDotGroup = 8, kMultiDotThreads = 512;
+__global__ void __launch_bounds__(kMultiDotThreads) k_multidot_partial(int64_t n, const double* __restrict__ V, int64_t ld,
+                                                                      int k, const double* __restrict__ w,
+                                                                      double* __restrict__ part) {
+    __shared__ double sh[kMultiDotGroup][kMultiDotThreads / 32];
+    const int wid = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j0 = 0; j0 < k; j0 += kMultiDotGroup) {
+        const int kk = min(kMultiDotGroup, k - j0);
+        double s[kMultiDotGroup];
+#pragma unroll
+        for (int t = 0; t < kMultiDotGroup; ++t) s[t] = 0.0;
+        GRID_STRIDE(i, n) {
+            const double wi = w[i];
+#pragma unroll
+            for (int t = 0; t < kMultiDotGroup; ++t)
+                if (t < kk) s[t] += V[(int64_t)(j0 + t) * ld + i] * wi;
+        }
+#pragma unroll
+        for (int t = 0; t < kMultiDotGroup; ++t) {
+            const double v = warp_sum(s[t]);
+            if (l == 0) sh[t][wid] = v;
+        }
         __syncthreads();
         if (wid == 0) {
-            s = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
-            s = warp_sum(s);
-            if (l == 0) part[(int64_t)j * gridDim.x + blockIdx.x] = s;
+            for (int t = 0; t < kk; ++t) {
+                const double v = warp_sum(l < nw ? sh[t][l] : 0.0);
+                if (l == 0) part[(int64_t)(j0 + t) * gridDim.x + blockIdx.x] = v;
+            }
         }
         __syncthreads();
     }
@@ -735,7 +751,7 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nparts, in
 }
 cudaError_t launch_multidot(int64_t n, const double* V, int64_t ld, int k, const double* w, double* scratch,
                             double* h, cudaStream_t s) {
-    k_multidot_partial<<<kRedBlocks, kThreads, 0, s>>>(n, V, ld, k, w, scratch);
+    k_multidot_partial<<<kRedBlocks, kMultiDotThreads, 0, s>>>(n, V, ld, k, w, scratch);
     count_launch(cudaGetLastError());
     k_multidot_final<<<1, 1024, 0, s>>>(scratch, kRedBlocks, k, h);
     return count_launch(cudaGetLastError());
