@@ -137,9 +137,9 @@ def cpu_baseline(n: int = 24, seconds: float = 3.0):
 
 def bench_batch(count: int, dev):
     """Batching pattern: 'count' instances of the batch recipe (N in {16,24,32,48,64}), one active-set
-    step each (one linear solve to 1e-8).  Solves/s of the batched FP32-MG solver against the same
-    instances solved one after another by the single-instance solver with the same FP32 V-cycle,
-    and with the FP64 V-cycle."""
+    step each (one linear solve to 1e-8).  Solves/s of the batched solver with the FP32 and with the
+    FP64 V-cycle against the same instances solved one after another by the single-instance solver
+    with the same V-cycles."""
     import torch
     from paper_1902_08112_gb300 import pff, workloads as W
     ws = W.batch_instances(count)
@@ -176,6 +176,19 @@ def bench_batch(count: int, dev):
             for h in hs:
                 pff.destroy_hierarchy(h)
             hs, _ = build(64)
+            # batched FP64 V-cycle on the same instances
+            b64 = pff.batch_create(hs)
+            for u, u0 in zip(Us, U0):
+                u.copy_(u0)
+            pff.batch_newton_step(b64, Us, allow_noconv=True)     # warm-up
+            for u, u0 in zip(Us, U0):
+                u.copy_(u0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            infos64 = pff.batch_newton_step(b64, Us, allow_noconv=True)
+            torch.cuda.synchronize()
+            tb64 = time.perf_counter() - t0
+            pff.batch_destroy(b64)
         for u, u0 in zip(Us, U0):
             u.copy_(u0)
         pff.newton_step(hs[0], Us[0].clone(), allow_noconv=True)   # warm-up
@@ -189,6 +202,8 @@ def bench_batch(count: int, dev):
     dofs = sum(w.n_dofs for w in ws)
     return {"instances": count, "dofs": dofs, "sizes": sorted({w.n_cells[0] for w in ws}),
             "batched_fp32mg_solves_per_s": count / tb,
+            "batched_fp64mg_solves_per_s": count / tb64,
+            "gmres_its_batched_fp64mg": [i.solve.iterations for i in infos64],
             "single_fp32mg_solves_per_s": count / single[32][0],
             "single_fp64mg_solves_per_s": count / single[64][0],
             "speedup_vs_single_fp32mg": single[32][0] / tb,

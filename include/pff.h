@@ -302,7 +302,7 @@ pff_status pff_load_step(pff_hierarchy* h, double* U, const double* phi_prev, do
 
 /* ---- Batches of independent instances (one launch per level and operation across instances).
  * A batch is a view over n existing hierarchies created on the same stream, all Q1 with the same
- * dimension, mg_precision 32, preconditioner 0, split 0 and cheb_degree; instances may differ in mesh size, number of levels
+ * dimension, one mg_precision (32 or 64), preconditioner 0, split 0 and cheb_degree; instances may differ in mesh size, number of levels
  * and physical parameters.  The batch owns only descriptor tables and reduction scratch; the
  * hierarchies keep their data (a hierarchy may belong to several batches, but batches that share a
  * hierarchy must not run concurrently).  Per-instance results equal those of the single-instance
@@ -312,7 +312,8 @@ pff_status pff_batch_create(int n, pff_hierarchy* const* hierarchies, int restar
 pff_status pff_batch_destroy(pff_batch* b);
 /* Diagonals and eigenvalue bounds of every instance (batched CG estimates, Sec. 3.2.1). */
 pff_status pff_batch_setup(pff_batch* b);
-/* z_i ~ G~_i^-1 r_i for every instance: one FP32 V-cycle run in lockstep over all instances. */
+/* z_i ~ G~_i^-1 r_i for every instance: one V-cycle (FP32 or FP64 levels, FP64 coarse solve) run
+ * in lockstep over all instances. */
 pff_status pff_batch_vcycle(pff_batch* b, const double* const* r, double* const* z);
 /* FGMRES(restart) of every instance to ||b_i - G~_i x_i|| <= rtol ||b_i - G~_i x0_i|| (device arrays
  * of pointers are NOT used: 'rhs' and 'x' are host arrays of n device pointers).  info: host array of

@@ -41,6 +41,7 @@ struct pff_batch {
     double* d_coef = nullptr;                // Chebyshev tables (smoother and coarse)
     uint64_t* d_seeds = nullptr;
     int cheb_k = 4, coarse_k = 1;
+    bool mg64 = false;                       // FP64 V-cycle (mg_precision 64 in every instance)
     bool stale = true;
     std::vector<void*> allocs;
     std::string err;
@@ -168,17 +169,19 @@ cudaError_t b_cheb_run(pff_batch* b, int l, int K, bool coarse, int phase, int s
     return cudaSuccess;
 }
 
-// FP32 smoother on level l: zero guess (x = S b) or x += S (b - G x)
+// Smoother on level l in precision T: zero guess (x = S b) or x += S (b - G x)
+template <typename T>
 cudaError_t b_smooth(pff_batch* b, int l, bool zero_guess) {
     const BLevel* L = tab(b, l);
-    const int bb = bsel(BV_W32 + 0), x = bsel(BV_W32 + 1), r = bsel(BV_W32 + 2), t = bsel(BV_W32 + 4);
+    const int W = sizeof(T) == 8 ? BV_W64 : BV_W32;
+    const int bb = bsel(W + 0), x = bsel(W + 1), r = bsel(W + 2), t = bsel(W + 4);
     if (zero_guess) {
-        BCK(bl_copy<float>(L, b->n, b->blocks[l], bb, r, -1, b->stream));
+        BCK(bl_copy<T>(L, b->n, b->blocks[l], bb, r, -1, b->stream));
     } else {
-        BCK(b_apply(b, l, false, false, x, t, PHI_BITS_ALL));
-        BCK(bl_sub<float>(L, b->n, b->blocks[l], bb, t, r, b->stream));
+        BCK(b_apply(b, l, sizeof(T) == 8, false, x, t, PHI_BITS_ALL));
+        BCK(bl_sub<T>(L, b->n, b->blocks[l], bb, t, r, b->stream));
     }
-    return b_cheb_run<float>(b, l, b->cheb_k, false, 0, x, zero_guess ? 1 : 2);
+    return b_cheb_run<T>(b, l, b->cheb_k, false, 0, x, zero_guess ? 1 : 2);
 }
 
 // FP64 coarse solve on level 0: b (W64_0) -> x (W64_1), u block then phi block
@@ -196,28 +199,32 @@ cudaError_t b_coarse(pff_batch* b) {
     return bl_axpby64(L, b->n, w, nullptr, xp, 1.0, x, 0, b->stream);
 }
 
-// z (fine selector) = V-cycle(v (fine selector)); FP32 levels, FP64 coarse solve
-cudaError_t b_vcycle(pff_batch* b, int sv, int sz) {
+// z (fine selector) = V-cycle(v (fine selector)); levels in precision T, FP64 coarse solve
+template <typename T>
+cudaError_t b_vcycle_t(pff_batch* b, int sv, int sz) {
     const int F = b->Lmax;
-    BCK(bl_convert<double, float>(tab(b, F), b->n, b->blocks[F], sv, bsel(BV_W32 + 0), 1, b->stream));
+    const int W = sizeof(T) == 8 ? BV_W64 : BV_W32;
+    const bool f64 = sizeof(T) == 8;
+    BCK(bl_convert<double, T>(tab(b, F), b->n, b->blocks[F], sv, bsel(W + 0), 1, b->stream));
     for (int l = b->Lmax - 1; l >= 1; --l) {
-        BCK(b_smooth(b, l, true));
-        BCK(b_apply(b, l, false, false, bsel(BV_W32 + 1), bsel(BV_W32 + 4), PHI_BITS_ALL));
-        BCK(bl_sub<float>(tab(b, l), b->n, b->blocks[l], bsel(BV_W32 + 0), bsel(BV_W32 + 4), bsel(BV_W32 + 2),
-                          b->stream));
-        BCK(bl_restrict<float>(tab(b, l - 1), tab(b, l), b->n, b->blocks[l - 1], bsel(BV_W32 + 2), bsel(BV_W32 + 0),
-                               b->stream));
+        BCK(b_smooth<T>(b, l, true));
+        BCK(b_apply(b, l, f64, false, bsel(W + 1), bsel(W + 4), PHI_BITS_ALL));
+        BCK(bl_sub<T>(tab(b, l), b->n, b->blocks[l], bsel(W + 0), bsel(W + 4), bsel(W + 2), b->stream));
+        BCK(bl_restrict<T>(tab(b, l - 1), tab(b, l), b->n, b->blocks[l - 1], bsel(W + 2), bsel(W + 0), b->stream));
     }
-    BCK(bl_convert<float, double>(tab(b, 0), b->n, b->blocks[0], bsel(BV_W32 + 0), bsel(BV_W64 + 0), 0, b->stream));
+    if (!f64) BCK(bl_convert<float, double>(tab(b, 0), b->n, b->blocks[0], bsel(BV_W32 + 0), bsel(BV_W64 + 0), 0, b->stream));
     BCK(b_coarse(b));
-    BCK(bl_convert<double, float>(tab(b, 0), b->n, b->blocks[0], bsel(BV_W64 + 1), bsel(BV_W32 + 1), 0, b->stream));
+    if (!f64) BCK(bl_convert<double, float>(tab(b, 0), b->n, b->blocks[0], bsel(BV_W64 + 1), bsel(BV_W32 + 1), 0, b->stream));
     for (int l = 1; l < b->Lmax; ++l) {
-        BCK(bl_prolongate_add<float>(tab(b, l - 1), tab(b, l), b->n, b->blocks[l], bsel(BV_W32 + 1), bsel(BV_W32 + 1),
-                                     b->stream));
-        BCK(b_smooth(b, l, false));
+        BCK(bl_prolongate_add<T>(tab(b, l - 1), tab(b, l), b->n, b->blocks[l], bsel(W + 1), bsel(W + 1), b->stream));
+        BCK(b_smooth<T>(b, l, false));
     }
-    BCK(bl_convert<float, double>(tab(b, F), b->n, b->blocks[F], bsel(BV_W32 + 1), sz, 0, b->stream));
+    BCK(bl_convert<T, double>(tab(b, F), b->n, b->blocks[F], bsel(W + 1), sz, 0, b->stream));
     return bl_convert<double, double>(tab(b, F), b->n, b->blocks[F], sv, sz, 2, b->stream);
+}
+
+cudaError_t b_vcycle(pff_batch* b, int sv, int sz) {
+    return b->mg64 ? b_vcycle_t<double>(b, sv, sz) : b_vcycle_t<float>(b, sv, sz);
 }
 
 // ---------------------------------------------------------------- batched eigenvalue estimates
@@ -376,7 +383,7 @@ cudaError_t b_setup(pff_batch* b) {
     const int steps = std::min(b->hs[0]->prm.cg_steps, kMaxCG);
     double* d_eig = b->d_vals + 12 * (size_t)n + (size_t)kMaxCG * 4 * n;   // [l][inst][4]
     for (int l = 0; l < b->Lmax; ++l) {
-        if (l == 0) BCK(b_eigen_level<double>(b, l, steps, b->d_seeds, d_eig + (size_t)l * 4 * n));
+        if (l == 0 || b->mg64) BCK(b_eigen_level<double>(b, l, steps, b->d_seeds, d_eig + (size_t)l * 4 * n));
         else BCK(b_eigen_level<float>(b, l, steps, b->d_seeds, d_eig + (size_t)l * 4 * n));
     }
     std::vector<double> eig((size_t)b->Lmax * 4 * n);
@@ -631,7 +638,7 @@ extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int rest
         if (!hs[i]) return PFF_EINVAL;
         if (hs[i]->mesh.degree != 1 || hs[i]->mesh.dim != hs[0]->mesh.dim) return PFF_EINVAL;
         if (hs[i]->stream != hs[0]->stream) return PFF_EINVAL;
-        if (hs[i]->prm.mg_precision != 32 || hs[i]->prm.preconditioner != 0 || hs[i]->prm.split != 0 || hs[i]->prm.cheb_degree != hs[0]->prm.cheb_degree) return PFF_EINVAL;
+        if (hs[i]->prm.mg_precision != hs[0]->prm.mg_precision || hs[i]->prm.preconditioner != 0 || hs[i]->prm.split != 0 || hs[i]->prm.cheb_degree != hs[0]->prm.cheb_degree) return PFF_EINVAL;
         if (!hs[i]->fast_q1) return PFF_EINVAL;
     }
     pff_batch* b = new (std::nothrow) pff_batch();
@@ -639,6 +646,7 @@ extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int rest
     b->n = n;
     b->dim = hs[0]->mesh.dim;
     b->m = restart;
+    b->mg64 = hs[0]->prm.mg_precision == 64;
     b->hs.assign(hs, hs + n);
     b->stream = hs[0]->stream;
     b->cheb_k = hs[0]->prm.cheb_degree;

@@ -218,12 +218,6 @@ struct pff_hierarchy {
     long long vgraph_nodes = 0;
     bool active_known = false;       // an active set has been computed or set
     bool derived_dirty = false;      // fine U changed; coarse levels, FP32 copies, Gauss-point data not yet
-    // coarse Chebyshev solve in one cluster launch: per-step coefficients on the device
-    double* d_coarse_coef = nullptr;
-    std::vector<double> coarse_coef;
-    int coarse_k1 = 0, coarse_k2 = 0;
-    bool coarse_fused = false;
-    bool use_fused_coarse = true;
     bool stale = true;               // preconditioner data out of date
     std::vector<void*> allocs;       // every device allocation, freed on destroy
     // kernel timing: event pairs per class, recorded while prof_on

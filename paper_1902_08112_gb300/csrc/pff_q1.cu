@@ -19,8 +19,6 @@
 // compile-time constants after unrolling.
 #include <cstring>
 
-#include <cooperative_groups.h>
-
 #include "pff_df64.cuh"
 #include "pff_split.cuh"
 #include "pff_internal.cuh"
@@ -1016,7 +1014,7 @@ k_q1_apply_batched(const BLevel* __restrict__ L, const int* __restrict__ tile_st
     const int local = b - tile_start[lo];
     const int tx = (d.g.nc[0] + TT::TX - 1) / TT::TX, ty = (d.g.nc[1] + TT::TY - 1) / TT::TY;
     const int bx = local % tx, by = (local / tx) % ty, bz = local / (tx * ty);
-    if constexpr (LANES) q1_apply_lanes_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);
+    if constexpr (LANES) q1_direct_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);   // atomic lanes, no barrier
     else q1_apply_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz, &d.k);
 }
 
@@ -1187,146 +1185,6 @@ cudaError_t launch_q1_apply_split32(const Geom& g, const Phys& ph, const float* 
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
     return blockdiag ? launch_split_dim<float, true>(a, s) : launch_split_dim<float, false>(a, s);
-}
-
-// ------------------------------------------------------------------ coarse solve in one launch
-// Chebyshev iteration as coarse solver (Sec. 3.2.2) on the coarsest level, all steps in one kernel:
-// a thread-block cluster owns the level's lane tiles; every step applies the block-diagonal
-// operator (atomic lanes, df64), meets at a cluster barrier, updates r, d, x and the preset of the
-// next apply (each CTA a slice of the DoFs) and meets again.  The cluster barrier is a hardware
-// barrier with release/acquire ordering of global memory within the cluster.  P_full runs the u
-// block, moves G_phiu x_u to the right-hand side and runs the phi block (block forward
-// substitution); P_diag runs both blocks at once.
-struct CoarseChebArgs {
-    Q1ApplyArgs<double, float2> a;   // coarsest-level operator (x, y unused)
-    const double* b;
-    double* x;
-    double* r;
-    double* d;
-    double* t;
-    double* xp;
-    const double* dinv;
-    const double* coef;              // per step: c1u, c1p, c2u, c2p (run 1, then run 2)
-    int k1, k2;                      // steps of run 1 and of run 2 (0: P_diag)
-    int ntiles, tx, ty;              // lane tiles of the level
-};
-
-template <int DIM, bool SPLIT>
-__global__ void __launch_bounds__(256) k_coarse_cheb(CoarseChebArgs c) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank(), nblk = (int)cl.num_blocks();
-    const Geom& g = c.a.g;
-    const int64_t nn = g.n_nodes, nd = n_dofs(g), nu = nn * DIM;
-    const int64_t tid = (int64_t)rank * blockDim.x + threadIdx.x, nthr = (int64_t)nblk * blockDim.x;
-    auto elim = [&](int64_t i) {
-        const int comp = dof_comp(i, nn);
-        const uint8_t m = c.a.mask[i - comp * nn];
-        return comp < DIM ? ((m >> comp) & 1) != 0 : (m & PHI_BITS_ALL) != 0;
-    };
-    auto apply = [&](const double* xin, double* yout, bool bd) {
-        Q1ApplyArgs<double, float2> a = c.a;
-        a.x = xin;
-        a.y = yout;
-        for (int tile = rank; tile < c.ntiles; tile += nblk) {
-            const int bx = tile % c.tx, by = (tile / c.tx) % c.ty, bz = tile / (c.tx * c.ty);
-            if (bd) q1_direct_tile<DIM, df64, true, SPLIT>(a, bx, by, bz);
-            else q1_direct_tile<DIM, df64, false, SPLIT>(a, bx, by, bz);
-        }
-    };
-    auto run = [&](int k, int coff, double* xo) {
-        const double* cf = c.coef + (int64_t)coff * 4;
-        for (int64_t i = tid; i < nd; i += nthr) {
-            const double di = (i < nu ? cf[2] : cf[3]) * c.dinv[i] * c.r[i];
-            c.d[i] = di;
-            xo[i] = di;
-            c.t[i] = elim(i) ? di : 0.0;
-        }
-        cl.sync();
-        for (int st = 1; st < k; ++st) {
-            apply(c.d, c.t, true);
-            cl.sync();
-            cf = c.coef + (int64_t)(coff + st) * 4;
-            for (int64_t i = tid; i < nd; i += nthr) {
-                const bool u = i < nu;
-                const double c1 = u ? cf[0] : cf[1], c2 = u ? cf[2] : cf[3];
-                const double ri = c.r[i] - c.t[i];
-                c.r[i] = ri;
-                const double di = c1 * c.d[i] + c2 * c.dinv[i] * ri;
-                c.d[i] = di;
-                xo[i] += di;
-                c.t[i] = elim(i) ? di : 0.0;
-            }
-            cl.sync();
-        }
-    };
-    for (int64_t i = tid; i < nd; i += nthr) c.r[i] = (c.k2 == 0 || i < nu) ? c.b[i] : 0.0;
-    cl.sync();
-    run(c.k1, 0, c.x);
-    if (c.k2 > 0) {
-        for (int64_t i = tid; i < nd; i += nthr) c.t[i] = elim(i) ? c.x[i] : 0.0;
-        cl.sync();
-        apply(c.x, c.t, false);
-        cl.sync();
-        for (int64_t i = tid; i < nd; i += nthr) c.r[i] = i >= nu ? c.b[i] - c.t[i] : 0.0;
-        cl.sync();
-        run(c.k2, c.k1, c.xp);
-        for (int64_t i = tid; i < nd; i += nthr) c.x[i] += c.xp[i];
-    }
-}
-
-bool coarse_cheb_fits(const Geom& g) {
-    if (g.deg != 1) return false;
-    const int tz = g.dim == 3 ? (g.nc[2] + LaneTile<3>::TZ - 1) / LaneTile<3>::TZ : 1;
-    const int tx = (g.nc[0] + (g.dim == 3 ? LaneTile<3>::TX : LaneTile<2>::TX) - 1) / (g.dim == 3 ? LaneTile<3>::TX : LaneTile<2>::TX);
-    const int ty = (g.nc[1] + (g.dim == 3 ? LaneTile<3>::TY : LaneTile<2>::TY) - 1) / (g.dim == 3 ? LaneTile<3>::TY : LaneTile<2>::TY);
-    return (int64_t)tx * ty * tz <= 64;
-}
-
-cudaError_t launch_coarse_cheb(const Geom& g, const Phys& ph, const float2* qd, const uint8_t* mask, bool split,
-                               const double* b, double* x, double* r, double* d, double* t, double* xp,
-                               const double* dinv, const double* coef, int k1, int k2, cudaStream_t s) {
-    CoarseChebArgs c;
-    c.a.g = g;
-    c.a.qd = qd;
-    c.a.x = nullptr;
-    c.a.y = nullptr;
-    c.a.mask = mask;
-    c.a.phi_bits = PHI_BITS_ALL;
-    fill_consts(c.a, ph);
-    c.b = b;
-    c.x = x;
-    c.r = r;
-    c.d = d;
-    c.t = t;
-    c.xp = xp;
-    c.dinv = dinv;
-    c.coef = coef;
-    c.k1 = k1;
-    c.k2 = k2;
-    const int TX = g.dim == 3 ? LaneTile<3>::TX : LaneTile<2>::TX, TY = g.dim == 3 ? LaneTile<3>::TY : LaneTile<2>::TY;
-    c.tx = (g.nc[0] + TX - 1) / TX;
-    c.ty = (g.nc[1] + TY - 1) / TY;
-    const int tz = g.dim == 3 ? (g.nc[2] + LaneTile<3>::TZ - 1) / LaneTile<3>::TZ : 1;
-    c.ntiles = c.tx * c.ty * tz;
-    const int nblk = c.ntiles < 8 ? c.ntiles : 8;   // portable cluster size
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nblk, 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = nblk;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e;
-    if (g.dim == 3) e = split ? cudaLaunchKernelEx(&cfg, k_coarse_cheb<3, true>, c) : cudaLaunchKernelEx(&cfg, k_coarse_cheb<3, false>, c);
-    else e = split ? cudaLaunchKernelEx(&cfg, k_coarse_cheb<2, true>, c) : cudaLaunchKernelEx(&cfg, k_coarse_cheb<2, false>, c);
-    if (e != cudaSuccess) return e;
-    return count_launch(cudaGetLastError());
 }
 
 // ------------------------------------------------------------------ residual and diagonal (FP64)

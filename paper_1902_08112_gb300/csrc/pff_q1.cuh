@@ -65,12 +65,4 @@ cudaError_t launch_q1_apply_split32(const Geom& g, const Phys& ph, const float* 
                                     const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
 inline int q1_nks(int dim) { return dim == 3 ? 28 : 10; }
 
-// Chebyshev coarse solve of the coarsest Q1 level in one cluster launch (coarse_cheb_fits: the
-// level has at most 64 lane tiles).  coef: device, per step (c1u, c1p, c2u, c2p), k1 steps of the
-// first run then k2 of the second (k2 = 0: both blocks in one run, P_diag).
-bool coarse_cheb_fits(const Geom& g);
-cudaError_t launch_coarse_cheb(const Geom& g, const Phys& ph, const float2* qd, const uint8_t* mask, bool split,
-                               const double* b, double* x, double* r, double* d, double* t, double* xp,
-                               const double* dinv, const double* coef, int k1, int k2, cudaStream_t s);
-
 }  // namespace pff

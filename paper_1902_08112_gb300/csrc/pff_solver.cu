@@ -325,7 +325,6 @@ cudaError_t setup(pff_hierarchy* h) {
             h->lv[l].lam_max[b] = eig[4 * l + 2 * b + 1];
         }
     }
-    CK(setup_coarse_fused(h));
     h->stale = false;
     return cudaSuccess;
 }
@@ -357,50 +356,6 @@ static int coarse_steps(double alpha, double beta, double rtol, int maxit) {
     const double k = ceil(acosh(1.0 / rtol) / acosh(sigma1));
     int ki = (int)std::min<double>(k, (double)maxit);
     return std::max(1, ki);
-}
-
-// Per-step coefficients of the coarse Chebyshev solve for the one-launch coarse kernel (same
-// recurrences as coarse_solve's cheb_run calls), uploaded once per setup outside any graph capture.
-cudaError_t setup_coarse_fused(pff_hierarchy* h) {
-    Level& L = h->lv[0];
-    const bool direct = (h->q1_style & 4) != 0;
-    h->coarse_fused = h->use_fused_coarse && h->fast_q1 && direct && coarse_cheb_fits(L.g) &&
-                      (h->ph.split ? L.qps64 != nullptr : L.qpd64 != nullptr);
-    if (!h->coarse_fused) return cudaSuccess;
-    const double au = 0.9 * L.lam_min[0], bu = 1.2 * L.lam_max[0];
-    const double ap = 0.9 * L.lam_min[1], bp = 1.2 * L.lam_max[1];
-    const int ku = coarse_steps(au, bu, h->prm.coarse_rtol, h->prm.coarse_maxit);
-    const int kp = coarse_steps(ap, bp, h->prm.coarse_rtol, h->prm.coarse_maxit);
-    const ChebCoef cu = cheb_coefs(au, bu, ku), cp = cheb_coefs(ap, bp, kp);
-    std::vector<double>& cf = h->coarse_coef;
-    cf.clear();
-    auto push = [&](double c1u, double c1p, double c2u, double c2p) {
-        cf.push_back(c1u);
-        cf.push_back(c1p);
-        cf.push_back(c2u);
-        cf.push_back(c2p);
-    };
-    if (h->prm.preconditioner == 1) {
-        const int k = std::max(ku, kp);
-        for (int st = 0; st < k; ++st)
-            push(st < ku ? cu.c1[st] : 0.0, st < kp ? cp.c1[st] : 0.0, st < ku ? cu.c2[st] : 0.0, st < kp ? cp.c2[st] : 0.0);
-        h->coarse_k1 = k;
-        h->coarse_k2 = 0;
-    } else {
-        for (int st = 0; st < ku; ++st) push(cu.c1[st], 0.0, cu.c2[st], 0.0);
-        for (int st = 0; st < kp; ++st) push(0.0, cp.c1[st], 0.0, cp.c2[st]);
-        h->coarse_k1 = ku;
-        h->coarse_k2 = kp;
-    }
-    if (!h->d_coarse_coef) {
-        CK(cudaMalloc(&h->d_coarse_coef, sizeof(double) * 4 * 2 * 1024));
-        h->allocs.push_back(h->d_coarse_coef);
-    }
-    if (cf.size() > (size_t)4 * 2 * 1024) {   // more steps than the buffer holds: keep the multi-launch path
-        h->coarse_fused = false;
-        return cudaSuccess;
-    }
-    return cudaMemcpyAsync(h->d_coarse_coef, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, h->stream);
 }
 
 // Operator of the V-cycle residuals: G~ (P_full) or its block diagonal (P_diag, Sec. 3.3).
@@ -453,11 +408,6 @@ template cudaError_t smooth<float>(pff_hierarchy*, int, const float*, float*, in
 // moved to the right-hand side (P_full); both blocks at once without the coupling (P_diag).
 cudaError_t coarse_solve(pff_hierarchy* h, const double* b, double* x) {
     Level& L = h->lv[0];
-    if (h->coarse_fused) {
-        return launch_coarse_cheb(L.g, h->ph, h->ph.split ? L.qps64 : L.qpd64, L.mask, h->ph.split != 0, b, x,
-                                  work<double>(L, 2), work<double>(L, 3), work<double>(L, 4), work<double>(L, 5),
-                                  L.dinv64, h->d_coarse_coef, h->coarse_k1, h->coarse_k2, h->stream);
-    }
     const int64_t nd = n_dofs(L.g);
     double* r = work<double>(L, 2);
     double* t = work<double>(L, 4);

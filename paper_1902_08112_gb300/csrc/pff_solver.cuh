@@ -13,11 +13,9 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
 template <typename T>
 cudaError_t diagonal_level(pff_hierarchy* h, int l, T* d);
 cudaError_t residual_fine(pff_hierarchy* h, double* R);
-cudaError_t propagate_state(pff_hierarchy* h, bool values = true);
+cudaError_t propagate_state(pff_hierarchy* h, bool values = true);   // values=false: masks only
 // propagate_state once if the fine state changed since the last propagation
 cudaError_t refresh_state(pff_hierarchy* h);
-// coefficients of the one-launch coarse Chebyshev solve (called by setup)
-cudaError_t setup_coarse_fused(pff_hierarchy* h);   // values=false: masks only
 cudaError_t setup(pff_hierarchy* h);
 void drop_graph(pff_hierarchy* h);
 template <typename T>

@@ -29,7 +29,7 @@ def rel(a, b):
 SIZES = [(8, 2), (16, 3), (12, 2), (24, 3), (16, 2)]   # (cells per edge, levels): uneven mix
 
 
-def make_instances(sizes=SIZES, seed=0):
+def make_instances(sizes=SIZES, seed=0, mgp=32):
     out = []
     rng = np.random.default_rng(seed)
     for k, (n, L) in enumerate(sizes):
@@ -37,7 +37,7 @@ def make_instances(sizes=SIZES, seed=0):
         w.pressure = float(rng.uniform(5e-4, 2e-3))
         w.cracks = [W.Crack(tuple(rng.uniform(-4, 4, 3)), (0.0, 0.0, 1.0), float(rng.uniform(1.0, 3.0)))]
         U, po, pt = W.initial_state(w, displacement="smooth")
-        prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, seed=100 + k)
+        prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, seed=100 + k, mg_precision=mgp)
         h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm)
         Ud, pod, ptd = t(U), t(po), t(pt)
         pff.set_state(h, Ud, pod, ptd)
@@ -142,3 +142,36 @@ def test_batch_rejects_mixed_precision():
     finally:
         pff.destroy_hierarchy(h1)
         pff.destroy_hierarchy(h2)
+
+
+def test_batch_fp64_vcycle_and_solve_match_single():
+    """mg_precision 64 in every instance: the batched FP64 V-cycle equals the single-instance one
+    (1e-9: atomic accumulation order only) and the batched FGMRES needs the same iterations."""
+    xs = make_instances(mgp=64)
+    try:
+        rs = [t(W.random_vector(x["w"].n_dofs, 40 + i)) for i, x in enumerate(xs)]
+        zs_single, its_single = [], []
+        for x, r in zip(xs, rs):
+            pff.setup(x["h"])
+            z = torch.zeros_like(r)
+            pff.vcycle(x["h"], r, z)
+            zs_single.append(z)
+            xx = torch.zeros_like(r)
+            its_single.append(pff.gmres_solve(x["h"], r, xx, rtol=1e-8, restart=30, maxit=200).iterations)
+        b = pff.batch_create([x["h"] for x in xs])
+        try:
+            pff.batch_setup(b)
+            zs = [torch.zeros_like(r) for r in rs]
+            pff.batch_vcycle(b, rs, zs)
+            torch.cuda.synchronize()
+            for z, zr in zip(zs, zs_single):
+                assert rel(z, zr) <= 1e-9
+            xb = [torch.zeros_like(r) for r in rs]
+            infos = pff.batch_gmres_solve(b, rs, xb, rtol=1e-8, maxit=200)
+            assert [i.iterations for i in infos] == its_single
+            assert all(i.converged for i in infos)
+        finally:
+            pff.batch_destroy(b)
+    finally:
+        for x in xs:
+            pff.destroy_hierarchy(x["h"])
