@@ -39,9 +39,15 @@ def _peaks():
         return {}
 
 
-# DRAM bytes per cell of the FP64-accurate apply k_q1_apply_direct<3, df64, 0> from one ncu capture
-# at 64^3 (158.6 MB per launch over 262,144 cells): the df64 Gauss-point data plus x, mask and y
-TRAFFIC_DF64_PER_CELL = 158.613248e6 / 262144
+# DRAM bytes per cell of the FP64-accurate apply k_q1_apply_cell64<false> from one ncu capture at
+# 64^3 (156.5 MB per launch over 262,144 cells): the df64 Gauss-point data plus x, mask and y
+TRAFFIC_DF64_PER_CELL = 156.509696e6 / 262144
+# Algorithmic work of that kernel per cell, counted from its operations: 622 double-float adds
+# (8 FP32 flops each: TwoSum and two low-part adds) and 223 double-float multiplies (7 flops:
+# product and three fused multiply-adds).  Displacement transforms 144 adds + 36 multiplies, phi
+# values 48 + 8, Gauss-point loop 8 x (24 adds + 16 multiplies), flux integration 159 + 36, phi
+# rows 79 + 15.
+DF64_ADDS_PER_CELL, DF64_MULS_PER_CELL = 622, 223
 
 
 def _nvtx(name: str, push: bool):
@@ -543,33 +549,34 @@ def main():
     # ---- FP32 fine-level apply (the V-cycle operator), timed alone
     x32 = torch.randn(nd, dtype=torch.float32, device=dev)
     y32 = torch.empty_like(x32)
+    torch.cuda.synchronize()   # x32 is written on torch's stream, read on the library's
     ms32_fine = timed(lambda: pff.apply_jacobian_f32(h, -1, x32, y32), reps=10)
 
     # ---- rooflines.  The applies are arithmetic-bound on GB300: the FP64-accurate apply runs as
     # double-float on the FP32 pipes.  Peak = FP32 pipe from unit counts and the max clock:
     # 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  Algorithmic FP32 flops per cell of the
-    # double-float lane apply: 8 lanes x (92 double-float adds x 8 + 131 multiplies x 7) = 13224;
-    # of the FP32 per-cell apply (butterfly form, counted from its operations): pass 1 756
-    # (transforms 180, Gauss-point work 8 x 45, integration 72 + 144), pass 2 176: 932.
+    # double-float per-cell apply: 622 adds x 8 + 223 multiplies x 7 = 6537; of the FP32 per-cell
+    # apply (butterfly form, counted from its operations): pass 1 756 (transforms 180, Gauss-point
+    # work 8 x 45, integration 72 + 144), pass 2 176: 932.
     classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32),
                "vcycle_graph": (cntv, msv)}
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     cells = w.n_cells_total
-    fl64 = 13224.0 * cells
+    fl64 = (8.0 * DF64_ADDS_PER_CELL + 7.0 * DF64_MULS_PER_CELL) * cells
     fl32 = 932.0 * cells
-    roof = {"kernel": "k_q1_apply_direct<3, df64, 0> (FP64-accurate fine-level Jacobian apply)",
+    roof = {"kernel": "k_q1_apply_cell64<false> (FP64-accurate fine-level Jacobian apply)",
             "bound": "alu", "achieved": fl64 / (apply_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
             "traffic": TRAFFIC_DF64_PER_CELL * cells if TRAFFIC_DF64_PER_CELL else None,
             "algorithmic_flops_per_launch": fl64,
             "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 64^3 "
-                            "(158.7 MB), scaled by cells",
+                            "(%.1f MB), scaled by cells" % (TRAFFIC_DF64_PER_CELL * 262144 / 1e6),
             "note": "peak: FP32 pipe derived from unit counts and 2.07 GHz; double-float arithmetic on FP32 pipes",
             "hbm": {"achieved": 105.0 * nn / (apply_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": 105.0 * nn / (apply_ms * 1e-3) / 1e9 / hbm,
                     "algorithmic_bytes_per_launch": 105.0 * nn, "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"},
-            "fp64_equivalent_tflops": 8 * 223.0 * cells / (apply_ms * 1e-3) / 1e12}
+            "fp64_equivalent_tflops": (DF64_ADDS_PER_CELL + DF64_MULS_PER_CELL) * cells / (apply_ms * 1e-3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof32 = {"kernel": "k_q1_apply<3, float, 0> (FP32 fine-level V-cycle operator)", "ms": ms32_fine,
               "bound": "alu", "achieved": fl32 / (ms32_fine * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",

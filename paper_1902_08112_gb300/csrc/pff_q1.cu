@@ -392,6 +392,17 @@ Q1Consts make_q1_consts(const Geom& g, const Phys& ph) {
     k.mu2 = split_pair(2.0 * ph.mu);
     k.lam = split_pair(ph.lam);
     k.gcew = split_pair(ph.Gc * ph.eps * vol / NV);
+    for (int kk = 0; kk < 8; ++kk) {
+        double acc = 0.0;
+        for (int d = 0; d < dim; ++d) {
+            if (kk >= NV || !(kk & (1 << d))) continue;
+            int pc = 0;
+            for (int b = 0; b < dim; ++b) pc += (kk >> b) & 1;
+            const double c = gp[pc - 1] * 2.0 / (g.h[d] * NV);
+            acc += c * c;
+        }
+        k.gk[kk] = split_pair(ph.Gc * ph.eps * vol * acc);   // 2^d (Gc eps vol / 2^d) sum cg^2
+    }
     k.g2 = split_pair(0.5 * gpt);
     k.al = split_pair(0.5 * (1.0 + gpt));
     k.be = split_pair(0.5 * (1.0 - gpt));
@@ -492,7 +503,6 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
         auto cv = [&](int j) { return cpair<S>(kg ? kg->cv[j] : a.k.cv[j]); };
         auto cg = [&](int d, int j) { return cpair<S>(kg ? kg->cg[d][j] : a.k.cg[d][j]); };
         const S mu2 = cpair<S>(a.k.mu2), lam = cpair<S>(a.k.lam);
-        const S gcew = cpair<S>(a.k.gcew);
 
         const S mu = cpair<S>(a.k.mu);
 
@@ -615,18 +625,10 @@ __device__ __forceinline__ void q1_apply_tile(const Q1ApplyArgs<typename Scalar<
             }
             fwd<DIM>(F);
             S Y[NV];
+            Y[0] = F[0] * cv(0);
+            // gradient-gradient term: diagonal in modal coefficients, factor gk
 #pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                S acc = F[k] * cv(popc(k));
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) {
-                    if (!(k & (1 << d))) continue;
-                    const int kp = k & ~(1 << d);
-                    // gradient term: 2^d Gc eps w cg^2 times the modal coefficient k
-                    acc = acc + df_scale((gcew * v[k]) * (cg(d, popc(kp)) * cg(d, popc(kp))), float(NV));
-                }
-                Y[k] = acc;
-            }
+            for (int k = 1; k < NV; ++k) Y[k] = F[k] * cv(popc(k)) + v[k] * cpair<S>(kg ? kg->gk[k] : a.k.gk[k]);
             inv<DIM>(Y);
 #pragma unroll
             for (int n = 0; n < NV; ++n) sel[(n * NC + DIM) * NCELL + cell] = Y[n];
@@ -979,6 +981,194 @@ __global__ void __launch_bounds__(256) k_q1_apply_lanes(Q1ApplyArgs<typename Sca
     q1_apply_lanes_tile<DIM, S, BLOCKDIAG>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// ------------------------------------------------------------------ per-cell FP64-accurate apply
+// One thread per cell in df64, modal form (3D).  After the modal transform of a displacement
+// component, the 4 distinct Gauss-point values of each derivative (c, d) go to shared memory, so
+// only the flux accumulators stay in registers through the Gauss-point loop (about 100
+// registers: four 128-thread CTAs per SM, limited by the 53 KB of shared memory each); the
+// accumulators then return to the same shared slots and each component's element vector is added
+// to y with FP64 atomics (no element buffer, no node gather, one CTA barrier).  The per-component
+// stages are loops, not unrolled, to keep the code small (the fully unrolled form stalled on
+// instruction fetch).  Arithmetic as in q1_apply_tile.
+struct Cell64Tile { static constexpr int TX = 16, TY = 4, TZ = 2; };
+
+template <bool BLOCKDIAG>
+__global__ void __launch_bounds__(128, 3) k_q1_apply_cell64(Q1ApplyArgs<double, float2> a) {
+    using S = df64;
+    using T = Cell64Tile;
+    constexpr int NV = 8, NC = 4, NH = 4, NK = Q1Dims<3>::NK;
+    constexpr int NCELL = T::TX * T::TY * T::TZ;
+    constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = T::TZ + 1;
+    constexpr int NT = NTX * NTY * NTZ;
+    static_assert(NCELL == 128, "launch bounds assume 128 cells per CTA");
+
+    // dynamic shared memory (above the 48 KB static limit): nodal x, derivatives / flux sums
+    // [(c * 3 + d) * 4 + class][cell], phi-row Gauss-point values [q][cell], node masks
+    extern __shared__ __align__(16) unsigned char c64_smem[];
+    S* sx = reinterpret_cast<S*>(c64_smem);
+    S* sgrad = sx + NC * NT;
+    S* sfq = sgrad + 9 * NH * NCELL;
+    uint8_t* smask = reinterpret_cast<uint8_t*>(sfq + NV * NCELL);
+
+    const Geom& g = a.g;
+    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = blockIdx.z * T::TZ;
+    const int64_t nn = g.n_nodes;
+    for (int t = threadIdx.x; t < NT; t += NCELL) {
+        const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
+        const int gi = ci0 + ti, gj = cj0 + tj, gk = ck0 + tk;
+        const bool in = gi < g.nn[0] && gj < g.nn[1] && gk < g.nn[2];
+        const int64_t gn = in ? (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk) : 0;
+        const uint8_t m = in ? a.mask[gn] : 0;
+        smask[t] = m;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const bool el = c < 3 ? ((m >> c) & 1) != 0 : (m & a.phi_bits) != 0;
+            sx[c * NT + t] = (in && !el) ? Scalar<S>::load(a.x[c * nn + gn]) : Scalar<S>::zero();
+        }
+    }
+    __syncthreads();
+
+    const int cell = threadIdx.x;
+    const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
+    const int gi = ci0 + li, gj = cj0 + lj, gk = ck0 + lk;
+    if (gi >= g.nc[0] || gj >= g.nc[1] || gk >= g.nc[2]) return;
+    const int64_t gid = (int64_t)gi + (int64_t)g.nc[0] * ((int64_t)gj + (int64_t)g.nc[1] * gk);
+    if (!cell_in(g, gid)) return;
+    const int tb = li + NTX * (lj + NTY * lk);
+    auto tnode = [&](int n) { return tb + (n & 1) + NTX * (((n >> 1) & 1) + NTY * ((n >> 2) & 1)); };
+    auto cls = [](int q, int d) { return (q & ((1 << d) - 1)) | ((q >> (d + 1)) << d); };   // q without bit d
+    auto cv = [&](int j) { return cpair<S>(a.k.cv[j]); };
+    auto cg = [&](int d, int j) { return cpair<S>(a.k.cg[d][j]); };
+    const S mu = cpair<S>(a.k.mu), lam = cpair<S>(a.k.lam);
+
+    // displacement derivatives at the Gauss points -> shared memory
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        S v[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) v[n] = sx[c * NT + tnode(n)];
+        fwd<3>(v);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            S t[NH];
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+                const int kp = ((j >> d) << (d + 1)) | (j & ((1 << d) - 1));   // j with a zero bit d inserted
+                t[j] = v[kp | (1 << d)] * cg(d, popc(kp));
+            }
+            inv<2>(t);
+#pragma unroll
+            for (int j = 0; j < NH; ++j) sgrad[((c * 3 + d) * NH + j) * NCELL + cell] = t[j];
+        }
+    }
+    // phi at the Gauss points -> shared memory
+    {
+        S v[NV], fq[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) v[n] = sx[3 * NT + tnode(n)];
+        fwd<3>(v);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) fq[k] = v[k] * cv(popc(k));
+        inv<3>(fq);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sfq[q * NCELL + cell] = fq[q];
+    }
+
+    S ps[3][3][NH];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int j = 0; j < NH; ++j) ps[c][d][j] = Scalar<S>::zero();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        S g_[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g_[c][d] = sgrad[((c * 3 + d) * NH + cls(q, d)) * NCELL + cell];
+        const int64_t qb = (int64_t)(q * NK) * g.n_cells + gid;
+        const S c0 = QData<S>::get(a.qd, qb);
+        // c0 sigma(du): c0 mu (du_i,j + du_j,i) off the diagonal, 2 c0 mu du_i,i + c0 lambda div du on it
+        const S c0m = c0 * mu, c0m2 = df_scale(c0m, 2.f);
+        const S c0lt = (c0 * lam) * (g_[0][0] + g_[1][1] + g_[2][2]);
+        S cp = Scalar<S>::zero();
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j) {
+                const S e2 = (i == j) ? g_[i][i] : g_[i][j] + g_[j][i];   // 2 e_ij off the diagonal
+                if constexpr (!BLOCKDIAG) {
+                    const S sp = QData<S>::get(a.qd, qb + (int64_t)(1 + sidx<3>(i, j)) * g.n_cells);
+                    cp = cp + sp * e2;   // Sp : e(du)
+                }
+                const S f = (i == j) ? c0m2 * e2 + c0lt : c0m * e2;
+                ps[i][j][cls(q, j)] = ps[i][j][cls(q, j)] + f;
+                if (i != j) ps[j][i][cls(q, i)] = ps[j][i][cls(q, i)] + f;
+            }
+        const S c1 = QData<S>::get(a.qd, qb + (int64_t)(NK - 1) * g.n_cells);
+        sfq[q * NCELL + cell] = c1 * sfq[q * NCELL + cell] + cp;
+    }
+    // flux sums back to this cell's shared slots (the derivatives are no longer needed)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int j = 0; j < NH; ++j) sgrad[((c * 3 + d) * NH + j) * NCELL + cell] = ps[c][d][j];
+
+    const int64_t gn0 = (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk);
+    auto noff = [&](int n) {
+        return (int64_t)(n & 1) + (int64_t)g.nn[0] * (((n >> 1) & 1) + (int64_t)g.nn[1] * ((n >> 2) & 1));
+    };
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        S p[3][NH];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int j = 0; j < NH; ++j) p[d][j] = sgrad[((c * 3 + d) * NH + j) * NCELL + cell];
+            fwd<2>(p[d]);
+        }
+        S Y[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            S acc = Scalar<S>::zero();
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (!(k & (1 << d))) continue;
+                const int kp = k & ~(1 << d);
+                acc = acc + p[d][cls(kp, d)] * cg(d, popc(kp));
+            }
+            Y[k] = acc;
+        }
+        inv<3>(Y);
+        double* yc = a.y + c * nn + gn0;
+#pragma unroll
+        for (int n = 0; n < NV; ++n)
+            if (!((smask[tnode(n)] >> c) & 1)) atomicAdd(yc + noff(n), Scalar<S>::store(Y[n]));
+    }
+    {
+        S v[NV], fq[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) {
+            v[n] = sx[3 * NT + tnode(n)];
+            fq[n] = sfq[n * NCELL + cell];
+        }
+        fwd<3>(v);
+        fwd<3>(fq);
+        S Y[NV];
+        Y[0] = fq[0] * cv(0);
+#pragma unroll
+        for (int k = 1; k < NV; ++k) Y[k] = fq[k] * cv(popc(k)) + v[k] * cpair<S>(a.k.gk[k]);
+        inv<3>(Y);
+#pragma unroll
+        for (int n = 0; n < NV; ++n)
+            if (!(smask[tnode(n)] & a.phi_bits)) atomicAdd(&a.y[3 * nn + gn0 + noff(n)], Scalar<S>::store(Y[n]));
+    }
+}
+
 // ---- batched: one launch over the tiles of all instances of a level
 template <int DIM, typename S, bool LANES>
 struct TileOf {
@@ -1102,9 +1292,39 @@ static void fill_consts(Q1ApplyArgs<St, QT>& a, const Phys& ph) {
     a.k = make_q1_consts(a.g, ph);
 }
 
+static constexpr size_t cell64_smem_bytes() {
+    using T = Cell64Tile;
+    constexpr int NCELL = T::TX * T::TY * T::TZ, NT = (T::TX + 1) * (T::TY + 1) * (T::TZ + 1);
+    return sizeof(df64) * (4 * NT + 9 * 4 * NCELL + 8 * NCELL) + NT;
+}
+// opt in to the dynamic shared memory of k_q1_apply_cell64 (once per instantiation and device)
+template <bool BD>
+static cudaError_t cell64_prepare() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_q1_apply_cell64<BD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cell64_smem_bytes());
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
+template <bool BD>
+static cudaError_t launch_cell64(const Q1ApplyArgs<double, float2>& a, cudaStream_t s) {
+    using T = Cell64Tile;
+    const Geom& g = a.g;
+    const cudaError_t e = cell64_prepare<BD>();
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
+    k_q1_apply_cell64<BD><<<grid, T::TX * T::TY * T::TZ, cell64_smem_bytes(), s>>>(a);
+    return count_launch(cudaGetLastError());
+}
+
 cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
                               const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
-                              bool direct) {
+                              bool direct, bool cell) {
     Q1ApplyArgs<double, float2> a;
     a.g = g;
     a.qd = qd;
@@ -1113,6 +1333,7 @@ cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, c
     a.mask = mask;
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
+    if (cell && g.dim == 3) return blockdiag ? launch_cell64<true>(a, s) : launch_cell64<false>(a, s);
     if (lanes || direct)
         return blockdiag ? launch_lanes_dim<df64, true>(a, s, direct) : launch_lanes_dim<df64, false>(a, s, direct);
     return blockdiag ? launch_apply_dim<df64, true>(a, s) : launch_apply_dim<df64, false>(a, s);

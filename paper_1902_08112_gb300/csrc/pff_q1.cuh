@@ -12,6 +12,8 @@ struct Q1Consts {
     float2 cg[3][3];         // g^j * 2 / (h_d 2^d)
     float2 mu, mu2, lam;     // Lame coefficients, 2 mu
     float2 gcew;             // Gc eps w (w = Gauss weight x |K|)
+    float2 gk[8];            // 2^d Gc eps w sum_{d in k} cg[d][|k|-1]^2: the phi gradient-gradient term
+                             // of modal coefficient k
     float2 g2;               // g / 2
     float2 al, be;           // (1 + g) / 2, (1 - g) / 2
     float2 ih[3];            // 1 / h_d
@@ -38,9 +40,10 @@ cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, 
                                 float2* q64, cudaStream_t s);
 // lanes = true: one thread per (cell, Gauss point) with shuffle butterflies; false: one thread
 // per cell with the modal form in registers
+// cell = true (3D): one thread per cell in df64 with shared-memory Gauss-point derivatives
 cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
                               const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
-                              bool direct = false);
+                              bool direct = false, bool cell = false);
 cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
                               const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
                               bool direct = false);

@@ -70,7 +70,9 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
         const bool bd = op == OP_APPLY_BLOCKDIAG;
         if constexpr (sizeof(T) == 8)
             CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd,
-                                 (h->q1_style & 1) != 0, h->stream, (h->q1_style & 4) != 0));
+                                 (h->q1_style & 1) != 0, h->stream, (h->q1_style & 4) != 0,
+                                 (h->q1_style & 64) != 0 ||
+                                     ((h->q1_style & 16) != 0 && L.g.n_cells >= kCell64MinCells)));
         else
             CK(launch_q1_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd,
                                  (h->q1_style & 2) != 0, h->stream, (h->q1_style & 8) != 0));

@@ -69,7 +69,8 @@ class Case:
 
 # (workload, kernel variant): 0 = Q1 fast path (df64 / FP32 with stored linearisation data),
 # 1 = generic kernels, 2 = one thread per Gauss point, 3 = one thread per cell, 5 = Gauss-point
-# lanes adding to y with global atomics.  Sizes span several tiles with ragged edges.
+# lanes adding to y with global atomics, 6 = FP64 per cell with shared-memory derivatives.  Sizes
+# span several tiles with ragged edges.
 CASES = {
     "2d_q1": (lambda: W.small(W.config_2d_single_crack(), 40, 3), 0),
     "2d_q1_generic": (lambda: W.small(W.config_2d_single_crack(), 24, 3), 1),
@@ -82,6 +83,9 @@ CASES = {
     "2d_q1_percell": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 3),
     "3d_q2": (lambda: W.small(W.config_3d_penny(deg=2), 6, 2), 1),
     "3d_q1_direct": (lambda: W.small(W.config_3d_penny(), 12, 2), 5),
+    "3d_q1_cell64": (lambda: W.small(W.config_3d_penny(), 20, 3), 6),
+    "3d_q1_cell64_modulus": (lambda: W.small(W.config_3d_penny(), 12, 2), 6, True),
+    "3d_q1_cell64_lshape": (lambda: W.small(W.config_3d_lshape(), (20, 20, 6), 2), 6),
     "2d_q1_direct": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 5),
     # spatially varying modulus (per-cell factor from a smooth seeded field)
     "3d_q1_modulus": (lambda: W.small(W.config_3d_penny(), 20, 3), 0, True),
@@ -180,8 +184,9 @@ def test_transfers_match_oracle(case):
         assert rel(xf, x0 + corr) <= 1e-14
 
 
-# (kernel variant, split): the Q1 fast path, the generic kernels, the Miehe split
-@pytest.fixture(scope="module", params=[(0, 0), (1, 0), (0, 1)], ids=["fast", "generic", "split"])
+# (kernel variant, split): the Q1 fast path, the generic kernels, the Miehe split, the per-cell
+# FP64-accurate apply
+@pytest.fixture(scope="module", params=[(0, 0), (1, 0), (0, 1), (6, 0)], ids=["fast", "generic", "split", "cell64"])
 def solver_case(request):
     variant, split = request.param
     c = Case(W.small(W.config_3d_penny(), 8, 2), active_fraction=0.05, state="initial", variant=variant,
