@@ -39,7 +39,7 @@ def _peaks():
         return {}
 
 
-# DRAM bytes per cell of the FP64-accurate apply k_q1_apply_cell64<false> from one ncu capture at
+# DRAM bytes per cell of the FP64-accurate apply k_q1_apply_cell<df64, false> from one ncu capture at
 # 64^3 (156.5 MB per launch over 262,144 cells): the df64 Gauss-point data plus x, mask and y
 TRAFFIC_DF64_PER_CELL = 156.509696e6 / 262144
 # Algorithmic work of that kernel per cell, counted from its operations: 622 double-float adds
@@ -555,9 +555,8 @@ def main():
     # ---- rooflines.  The applies are arithmetic-bound on GB300: the FP64-accurate apply runs as
     # double-float on the FP32 pipes.  Peak = FP32 pipe from unit counts and the max clock:
     # 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  Algorithmic FP32 flops per cell of the
-    # double-float per-cell apply: 622 adds x 8 + 223 multiplies x 7 = 6537; of the FP32 per-cell
-    # apply (butterfly form, counted from its operations): pass 1 756 (transforms 180, Gauss-point
-    # work 8 x 45, integration 72 + 144), pass 2 176: 932.
+    # double-float per-cell apply: 622 adds x 8 + 223 multiplies x 7 = 6537; the FP32 per-cell
+    # apply runs the same operations in FP32: 622 + 223 = 845.
     classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32),
                "vcycle_graph": (cntv, msv)}
     peaks = _peaks()
@@ -565,8 +564,8 @@ def main():
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     cells = w.n_cells_total
     fl64 = (8.0 * DF64_ADDS_PER_CELL + 7.0 * DF64_MULS_PER_CELL) * cells
-    fl32 = 932.0 * cells
-    roof = {"kernel": "k_q1_apply_cell64<false> (FP64-accurate fine-level Jacobian apply)",
+    fl32 = float(DF64_ADDS_PER_CELL + DF64_MULS_PER_CELL) * cells
+    roof = {"kernel": "k_q1_apply_cell<df64, false> (FP64-accurate fine-level Jacobian apply)",
             "bound": "alu", "achieved": fl64 / (apply_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
             "traffic": TRAFFIC_DF64_PER_CELL * cells if TRAFFIC_DF64_PER_CELL else None,
             "algorithmic_flops_per_launch": fl64,
@@ -578,7 +577,7 @@ def main():
                     "algorithmic_bytes_per_launch": 105.0 * nn, "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "fp64_equivalent_tflops": (DF64_ADDS_PER_CELL + DF64_MULS_PER_CELL) * cells / (apply_ms * 1e-3) / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof32 = {"kernel": "k_q1_apply<3, float, 0> (FP32 fine-level V-cycle operator)", "ms": ms32_fine,
+    roof32 = {"kernel": "k_q1_apply_cell<float, false> (FP32 fine-level V-cycle operator)", "ms": ms32_fine,
               "bound": "alu", "achieved": fl32 / (ms32_fine * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
               "frac": fl32 / (ms32_fine * 1e-3) / 1e12 / fp32_peak,
               "hbm_frac": 53.0 * nn / (ms32_fine * 1e-3) / 1e9 / hbm, "gdofs": nd / (ms32_fine * 1e-3) / 1e9}

@@ -171,17 +171,18 @@ pff_status pff_set_params(pff_hierarchy* h, const pff_params* params);
 pff_status pff_set_modulus(pff_hierarchy* h, const double* escale);
 
 /* Kernel variant of the level operators: 0 (default) = Q1 fast path (Gauss-point linearisation
- * data precomputed per state; FP64-accurate operators evaluated in double-float arithmetic, on 3D
- * levels of at least 100,000 cells with one thread per cell (Gauss-point derivatives in shared
- * memory, element vectors added to y with global atomics), on smaller levels and in 2D with one
- * thread per Gauss point, each adding its node's result to y with global atomics; FP32
- * operators in FP32 with one thread per cell and a shared-memory gather), 1 = generic kernels
+ * data precomputed per state; FP64-accurate operators evaluated in double-float arithmetic, FP32
+ * operators in FP32; on 3D levels of at least 100,000 cells both run one thread per cell with the
+ * Gauss-point derivatives in shared memory and add element vectors to y with global atomics; on
+ * smaller levels and in 2D the FP64-accurate operators run one thread per Gauss point, each adding
+ * its node's result to y with global atomics, and the FP32 operators one thread per cell with a
+ * shared-memory gather), 1 = generic kernels
  * (Q1 and Q2, native FP64 or FP32, state evaluated at every apply), 2 = one thread per Gauss point
  * with a shared-memory gather in both precisions, 3 = one thread per cell in both precisions,
  * 4 = as 0 but the FP64-accurate operator gathers through shared memory, 5 = one thread per Gauss
- * point with global atomics in both precisions, 6 = as 0 with the per-cell FP64-accurate 3D
- * operator on every 3D level.  Q2 meshes always use the generic kernels.  Errors: PFF_EINVAL
- * outside 0 .. 6. */
+ * point with global atomics in both precisions, 6 / 7 = as 0 with the per-cell FP64-accurate /
+ * FP32 form with shared-memory derivatives on every 3D level.  Q2 meshes always use the generic
+ * kernels.  Errors: PFF_EINVAL outside 0 .. 7. */
 pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant);
 
 /* Set the linearisation point.  U: FP64 [u | phi] (n_dofs), phi_old: FP64 (n_nodes) = the

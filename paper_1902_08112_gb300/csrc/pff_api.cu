@@ -387,10 +387,10 @@ extern "C" pff_status pff_set_modulus(pff_hierarchy* h, const double* escale) {
 
 extern "C" pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant) {
     if (!h) return PFF_EINVAL;
-    REQUIRE(h, variant >= 0 && variant <= 6, PFF_EINVAL, "variant must be 0 .. 6");
+    REQUIRE(h, variant >= 0 && variant <= 7, PFF_EINVAL, "variant must be 0 .. 7");
     drop_graph(h);
     h->fast_q1 = variant != 1;
-    static const int style[7] = {20, 20, 3, 0, 1, 12, 68};
+    static const int style[8] = {52, 52, 3, 0, 1, 12, 52 | 64, 52 | 128};
     h->q1_style = style[variant];
     h->stale = true;
     return PFF_OK;

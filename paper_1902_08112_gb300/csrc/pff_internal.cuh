@@ -187,8 +187,8 @@ cudaError_t launch_gemv_add(int64_t n, const double* Z, int64_t ld, int k, const
 }  // namespace pff
 
 // The opaque hierarchy of the C ABI.
-// Smallest 3D level that the per-cell FP64-accurate apply serves by default: below about two waves
-// of its CTAs (4 per SM) the Gauss-point lanes finish sooner.
+// Smallest 3D level that the per-cell applies with shared-memory derivatives serve by default: below
+// about two waves of their CTAs the lane and per-cell-gather kernels finish sooner.
 constexpr int64_t kCell64MinCells = 100000;
 
 struct pff_hierarchy {
@@ -216,9 +216,10 @@ struct pff_hierarchy {
     double* kr_h = nullptr;          // device column of H (2 * (m + 1))
     bool has_state = false;
     bool fast_q1 = true;             // Q1 levels use the linearisation-data kernels of pff_q1.cu
-    int q1_style = 20;               // bit 0/1: lanes for FP64/FP32; bit 2/3: lanes with global atomics for FP64/FP32;
-                                     // bit 4/6: FP64 per cell with shared-memory derivatives on 3D levels of at
-                                     // least kCell64MinCells cells / on every 3D level
+    int q1_style = 52;               // bit 0/1: lanes for FP64/FP32; bit 2/3: lanes with global atomics for FP64/FP32;
+                                     // bit 4/6 (FP64), 5/7 (FP32): per cell with shared-memory derivatives and
+                                     // global atomics on 3D levels of at least kCell64MinCells cells / on every
+                                     // 3D level
     bool use_graphs = true;          // replay the V-cycle body from a captured CUDA graph
     cudaGraphExec_t vgraph = nullptr;   // captured V-cycle body (valid until the next setup)
     long long vgraph_nodes = 0;

@@ -981,8 +981,8 @@ __global__ void __launch_bounds__(256) k_q1_apply_lanes(Q1ApplyArgs<typename Sca
     q1_apply_lanes_tile<DIM, S, BLOCKDIAG>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// ------------------------------------------------------------------ per-cell FP64-accurate apply
-// One thread per cell in df64, modal form (3D).  After the modal transform of a displacement
+// ------------------------------------------------------------------ per-cell apply
+// One thread per cell (df64 for the FP64-accurate operator, or FP32), modal form (3D).  After the modal transform of a displacement
 // component, the 4 distinct Gauss-point values of each derivative (c, d) go to shared memory, so
 // only the flux accumulators stay in registers through the Gauss-point loop (about 100
 // registers: four 128-thread CTAs per SM, limited by the 53 KB of shared memory each); the
@@ -990,12 +990,12 @@ __global__ void __launch_bounds__(256) k_q1_apply_lanes(Q1ApplyArgs<typename Sca
 // to y with FP64 atomics (no element buffer, no node gather, one CTA barrier).  The per-component
 // stages are loops, not unrolled, to keep the code small (the fully unrolled form stalled on
 // instruction fetch).  Arithmetic as in q1_apply_tile.
-struct Cell64Tile { static constexpr int TX = 16, TY = 4, TZ = 2; };
+struct CellTile { static constexpr int TX = 16, TY = 4, TZ = 2; };
 
-template <bool BLOCKDIAG>
-__global__ void __launch_bounds__(128, 3) k_q1_apply_cell64(Q1ApplyArgs<double, float2> a) {
-    using S = df64;
-    using T = Cell64Tile;
+template <typename S, bool BLOCKDIAG>
+__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 3 : 4)
+k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
+    using T = CellTile;
     constexpr int NV = 8, NC = 4, NH = 4, NK = Q1Dims<3>::NK;
     constexpr int NCELL = T::TX * T::TY * T::TZ;
     constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = T::TZ + 1;
@@ -1004,8 +1004,8 @@ __global__ void __launch_bounds__(128, 3) k_q1_apply_cell64(Q1ApplyArgs<double, 
 
     // dynamic shared memory (above the 48 KB static limit): nodal x, derivatives / flux sums
     // [(c * 3 + d) * 4 + class][cell], phi-row Gauss-point values [q][cell], node masks
-    extern __shared__ __align__(16) unsigned char c64_smem[];
-    S* sx = reinterpret_cast<S*>(c64_smem);
+    extern __shared__ __align__(16) unsigned char cell_smem[];
+    S* sx = reinterpret_cast<S*>(cell_smem);
     S* sgrad = sx + NC * NT;
     S* sfq = sgrad + 9 * NH * NCELL;
     uint8_t* smask = reinterpret_cast<uint8_t*>(sfq + NV * NCELL);
@@ -1144,7 +1144,7 @@ __global__ void __launch_bounds__(128, 3) k_q1_apply_cell64(Q1ApplyArgs<double, 
             Y[k] = acc;
         }
         inv<3>(Y);
-        double* yc = a.y + c * nn + gn0;
+        typename Scalar<S>::storage* yc = a.y + c * nn + gn0;
 #pragma unroll
         for (int n = 0; n < NV; ++n)
             if (!((smask[tnode(n)] >> c) & 1)) atomicAdd(yc + noff(n), Scalar<S>::store(Y[n]));
@@ -1292,33 +1292,35 @@ static void fill_consts(Q1ApplyArgs<St, QT>& a, const Phys& ph) {
     a.k = make_q1_consts(a.g, ph);
 }
 
-static constexpr size_t cell64_smem_bytes() {
-    using T = Cell64Tile;
+template <typename S>
+static constexpr size_t cell_smem_bytes() {
+    using T = CellTile;
     constexpr int NCELL = T::TX * T::TY * T::TZ, NT = (T::TX + 1) * (T::TY + 1) * (T::TZ + 1);
-    return sizeof(df64) * (4 * NT + 9 * 4 * NCELL + 8 * NCELL) + NT;
+    return sizeof(S) * (4 * NT + 9 * 4 * NCELL + 8 * NCELL) + NT;
 }
-// opt in to the dynamic shared memory of k_q1_apply_cell64 (once per instantiation and device)
-template <bool BD>
-static cudaError_t cell64_prepare() {
+// opt in to the dynamic shared memory of k_q1_apply_cell (once per instantiation and device)
+template <typename S, bool BD>
+static cudaError_t cell_prepare() {
     static bool done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_q1_apply_cell64<BD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cell64_smem_bytes());
+    e = cudaFuncSetAttribute(k_q1_apply_cell<S, BD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cell_smem_bytes<S>());
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }
 
-template <bool BD>
-static cudaError_t launch_cell64(const Q1ApplyArgs<double, float2>& a, cudaStream_t s) {
-    using T = Cell64Tile;
+template <typename S, bool BD>
+static cudaError_t launch_cell(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
+                               cudaStream_t s) {
+    using T = CellTile;
     const Geom& g = a.g;
-    const cudaError_t e = cell64_prepare<BD>();
+    const cudaError_t e = cell_prepare<S, BD>();
     if (e != cudaSuccess) return e;
     dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
-    k_q1_apply_cell64<BD><<<grid, T::TX * T::TY * T::TZ, cell64_smem_bytes(), s>>>(a);
+    k_q1_apply_cell<S, BD><<<grid, T::TX * T::TY * T::TZ, cell_smem_bytes<S>(), s>>>(a);
     return count_launch(cudaGetLastError());
 }
 
@@ -1333,7 +1335,7 @@ cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, c
     a.mask = mask;
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
-    if (cell && g.dim == 3) return blockdiag ? launch_cell64<true>(a, s) : launch_cell64<false>(a, s);
+    if (cell && g.dim == 3) return blockdiag ? launch_cell<df64, true>(a, s) : launch_cell<df64, false>(a, s);
     if (lanes || direct)
         return blockdiag ? launch_lanes_dim<df64, true>(a, s, direct) : launch_lanes_dim<df64, false>(a, s, direct);
     return blockdiag ? launch_apply_dim<df64, true>(a, s) : launch_apply_dim<df64, false>(a, s);
@@ -1341,7 +1343,7 @@ cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, c
 
 cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
                               const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
-                              bool direct) {
+                              bool direct, bool cell) {
     Q1ApplyArgs<float, float> a;
     a.g = g;
     a.qd = qd;
@@ -1350,6 +1352,7 @@ cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, co
     a.mask = mask;
     a.phi_bits = phi_bits;
     fill_consts(a, ph);
+    if (cell && g.dim == 3) return blockdiag ? launch_cell<float, true>(a, s) : launch_cell<float, false>(a, s);
     if (lanes || direct)
         return blockdiag ? launch_lanes_dim<float, true>(a, s, direct) : launch_lanes_dim<float, false>(a, s, direct);
     return blockdiag ? launch_apply_dim<float, true>(a, s) : launch_apply_dim<float, false>(a, s);

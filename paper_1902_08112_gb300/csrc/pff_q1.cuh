@@ -46,7 +46,7 @@ cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, c
                               bool direct = false, bool cell = false);
 cudaError_t launch_q1_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
                               const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,
-                              bool direct = false);
+                              bool direct = false, bool cell = false);
 
 // -A(U) on a Q1 level (R zeroed by the caller) and diag(G~) on free rows (eliminated rows preset)
 cudaError_t launch_q1_residual(const Geom& g, const Phys& ph, const double* U, const double* pt, double* R,

@@ -75,7 +75,9 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
                                      ((h->q1_style & 16) != 0 && L.g.n_cells >= kCell64MinCells)));
         else
             CK(launch_q1_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd,
-                                 (h->q1_style & 2) != 0, h->stream, (h->q1_style & 8) != 0));
+                                 (h->q1_style & 2) != 0, h->stream, (h->q1_style & 8) != 0,
+                                 (h->q1_style & 128) != 0 ||
+                                     ((h->q1_style & 32) != 0 && L.g.n_cells >= kCell64MinCells)));
     } else {
         CellArgs<T> a;
         a.g = L.g;

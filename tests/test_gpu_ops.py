@@ -69,8 +69,8 @@ class Case:
 
 # (workload, kernel variant): 0 = Q1 fast path (df64 / FP32 with stored linearisation data),
 # 1 = generic kernels, 2 = one thread per Gauss point, 3 = one thread per cell, 5 = Gauss-point
-# lanes adding to y with global atomics, 6 = FP64 per cell with shared-memory derivatives.  Sizes
-# span several tiles with ragged edges.
+# lanes adding to y with global atomics, 6 = FP64 per cell with shared-memory derivatives, 7 = the
+# same per-cell form for the FP32 operators.  Sizes span several tiles with ragged edges.
 CASES = {
     "2d_q1": (lambda: W.small(W.config_2d_single_crack(), 40, 3), 0),
     "2d_q1_generic": (lambda: W.small(W.config_2d_single_crack(), 24, 3), 1),
@@ -86,6 +86,7 @@ CASES = {
     "3d_q1_cell64": (lambda: W.small(W.config_3d_penny(), 20, 3), 6),
     "3d_q1_cell64_modulus": (lambda: W.small(W.config_3d_penny(), 12, 2), 6, True),
     "3d_q1_cell64_lshape": (lambda: W.small(W.config_3d_lshape(), (20, 20, 6), 2), 6),
+    "3d_q1_cell32": (lambda: W.small(W.config_3d_penny(), 20, 3), 7),
     "2d_q1_direct": (lambda: W.small(W.config_2d_single_crack(), 24, 2), 5),
     # spatially varying modulus (per-cell factor from a smooth seeded field)
     "3d_q1_modulus": (lambda: W.small(W.config_3d_penny(), 20, 3), 0, True),
