@@ -42,12 +42,12 @@ def _peaks():
 # DRAM bytes per cell of the FP64-accurate apply k_q1_apply_cell<df64, false> from one ncu capture at
 # 64^3 (156.5 MB per launch over 262,144 cells): the df64 Gauss-point data plus x, mask and y
 TRAFFIC_DF64_PER_CELL = 156.544512e6 / 262144
-# Algorithmic work of that kernel per cell, counted from its operations: 622 double-float adds
+# Algorithmic work of that kernel per cell, counted from its operations: 572 double-float adds
 # (8 FP32 flops each: TwoSum and two low-part adds) and 223 double-float multiplies (7 flops:
 # product and three fused multiply-adds).  Displacement transforms 144 adds + 36 multiplies, phi
-# values 48 + 8, Gauss-point loop 8 x (24 adds + 16 multiplies), flux integration 159 + 36, phi
-# rows 79 + 15.
-DF64_ADDS_PER_CELL, DF64_MULS_PER_CELL = 622, 223
+# values 48 + 8, Gauss-point loop 148 adds (8 x 23, less the 36 flux sums' first terms) + 128
+# multiplies, flux integration 153 + 36, phi rows 79 + 15.
+DF64_ADDS_PER_CELL, DF64_MULS_PER_CELL = 572, 223
 
 
 def _nvtx(name: str, push: bool):
@@ -555,8 +555,8 @@ def main():
     # ---- rooflines.  The applies are arithmetic-bound on GB300: the FP64-accurate apply runs as
     # double-float on the FP32 pipes.  Peak = FP32 pipe from unit counts and the max clock:
     # 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  Algorithmic FP32 flops per cell of the
-    # double-float per-cell apply: 622 adds x 8 + 223 multiplies x 7 = 6537; the FP32 per-cell
-    # apply runs the same operations in FP32: 622 + 223 = 845.
+    # double-float per-cell apply: 572 adds x 8 + 223 multiplies x 7 = 6137; the FP32 per-cell
+    # apply runs the same operations in FP32: 572 + 223 = 795.
     classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32),
                "vcycle_graph": (cntv, msv)}
     peaks = _peaks()

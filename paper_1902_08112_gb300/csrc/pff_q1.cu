@@ -70,6 +70,26 @@ __device__ __forceinline__ void fwd(S* v) {
                 v[i | (1 << a)] = q - p;
             }
 }
+// inv<3> when v[0] == 0: its first pair (0, v1) becomes (-v1, v1) without additions
+template <typename S>
+__device__ __forceinline__ void inv3_v0_zero(S* v) {
+    v[0] = -v[1];
+#pragma unroll
+    for (int i = 2; i < 8; i += 2) {
+        const S p = v[i], q = v[i + 1];
+        v[i] = p - q;
+        v[i + 1] = p + q;
+    }
+#pragma unroll
+    for (int a = 1; a < 3; ++a)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (!(i & (1 << a))) {
+                const S p = v[i], q = v[i | (1 << a)];
+                v[i] = p - q;
+                v[i | (1 << a)] = p + q;
+            }
+}
 template <int DIM, typename S>
 __device__ __forceinline__ void inv(S* v) {
 #pragma unroll
@@ -1074,13 +1094,9 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
         for (int q = 0; q < NV; ++q) sfq[q * NCELL + cell] = fq[q];
     }
 
+    // flux sums per (c, d, class); each sum starts at its first Gauss point (the one with bit d of
+    // q clear), so no addition with zero is spent
     S ps[3][3][NH];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int j = 0; j < NH; ++j) ps[c][d][j] = Scalar<S>::zero();
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         S g_[3][3];
@@ -1101,14 +1117,19 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
                 const S e2 = (i == j) ? g_[i][i] : g_[i][j] + g_[j][i];   // 2 e_ij off the diagonal
                 if constexpr (!BLOCKDIAG) {
                     const S sp = QData<S>::get(a.qd, qb + (int64_t)(1 + sidx<3>(i, j)) * g.n_cells);
-                    cp = cp + sp * e2;   // Sp : e(du)
+                    cp = (i == 0 && j == 0) ? sp * e2 : cp + sp * e2;   // Sp : e(du)
                 }
                 const S f = (i == j) ? c0m2 * e2 + c0lt : c0m * e2;
-                ps[i][j][cls(q, j)] = ps[i][j][cls(q, j)] + f;
-                if (i != j) ps[j][i][cls(q, i)] = ps[j][i][cls(q, i)] + f;
+                S& pj = ps[i][j][cls(q, j)];
+                pj = ((q >> j) & 1) ? pj + f : f;
+                if (i != j) {
+                    S& pi = ps[j][i][cls(q, i)];
+                    pi = ((q >> i) & 1) ? pi + f : f;
+                }
             }
         const S c1 = QData<S>::get(a.qd, qb + (int64_t)(NK - 1) * g.n_cells);
-        sfq[q * NCELL + cell] = c1 * sfq[q * NCELL + cell] + cp;
+        if constexpr (BLOCKDIAG) sfq[q * NCELL + cell] = c1 * sfq[q * NCELL + cell];
+        else sfq[q * NCELL + cell] = c1 * sfq[q * NCELL + cell] + cp;
     }
     // flux sums back to this cell's shared slots (the derivatives are no longer needed)
 #pragma unroll
@@ -1132,18 +1153,20 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
             fwd<2>(p[d]);
         }
         S Y[NV];
+        Y[0] = Scalar<S>::zero();
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            S acc = Scalar<S>::zero();
+        for (int k = 1; k < NV; ++k) {
+            const int d0 = (k & 1) ? 0 : ((k & 2) ? 1 : 2);   // lowest axis in k
+            S acc = p[d0][cls(k & ~(1 << d0), d0)] * cg(d0, popc(k) - 1);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
+            for (int d = d0 + 1; d < 3; ++d) {
                 if (!(k & (1 << d))) continue;
                 const int kp = k & ~(1 << d);
                 acc = acc + p[d][cls(kp, d)] * cg(d, popc(kp));
             }
             Y[k] = acc;
         }
-        inv<3>(Y);
+        inv3_v0_zero(Y);
         typename Scalar<S>::storage* yc = a.y + c * nn + gn0;
 #pragma unroll
         for (int n = 0; n < NV; ++n)
