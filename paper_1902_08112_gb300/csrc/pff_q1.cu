@@ -1,14 +1,19 @@
 // Q1 fast path of the level operator (Sec. 4.1, 4.2), dim 2 and 3.
 //
-// 1) k_q1_linearize (FP64, once per state and level): for every cell and Gauss point q the
-//    state enters the Jacobian only through
+// 1) k_q1_linearize_cell (3D) / k_q1_linearize<2> (double-float, once per state and level): for
+//    every cell and Gauss point q the state enters the Jacobian only through
 //      c0 = w g_kappa(phi~)                                   (G_uu: c0 sigma(du) : e(w))
 //      Sp = w [2 f (1-k) phi sigma(u) + 2 p phi I]            (G_phiu: Sp : e(du) psi)
 //      c1 = w [2 f (1-k) E_s(u) + 2 p div u + Gc/eps]         (G_phiphi mass part)
 //    (w = Gauss weight x |K|).  They are stored per level as FP32 and as df64 pairs, cell
 //    fastest, so the applies read them coalesced.
-// 2) k_q1_apply<DIM, S> (S = float for the FP32 V-cycle operators, S = df64 for the
-//    FP64-accurate operators): y = G~ x from x and the stored coefficients.
+// 2) The applies y = G~ x from x and the stored coefficients, in FP32 (V-cycle operators) or df64
+//    (FP64-accurate operators): k_q1_apply_cell<S> (3D levels of at least 100,000 cells: one
+//    thread per cell, Gauss-point derivatives in shared memory, global atomics),
+//    k_q1_apply_direct (one thread per cell and Gauss point) and k_q1_apply<DIM, S> (one thread
+//    per cell, shared-memory gather) elsewhere.
+// 3) The residual -A(U) (k_q1_residual_cell in 3D, k_q1_resdiag<2, 0>) and the operator
+//    diagonal (k_q1_resdiag<DIM, 1>), in df64.
 //
 // Sum factorisation for Q1 on a uniform cell (the tensor-product structure of Sec. 4.1): the 2^d
 // nodal values of a field map to 2^d "modal" coefficients m_k = sum_n prod_{a in k}(2 n_a - 1) v_n
@@ -260,15 +265,18 @@ static void fill_lin_consts(const Geom& g, const Phys& ph, K& k) {
     k.lam = split_pair(ph.lam);
 }
 
+static cudaError_t launch_linearize_cell(const Geom& g, const LinConsts& k, const double* U, const double* pt,
+                                         float* q32, float2* q64, cudaStream_t s);
+
 cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, const double* pt, float* q32,
                                 float2* q64, cudaStream_t s) {
     LinConsts k;
     fill_lin_consts(g, ph, k);
+    if (g.dim == 3) return launch_linearize_cell(g, k, U, pt, q32, q64, s);
     int64_t blocks = (g.n_cells + 127) / 128;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    if (g.dim == 3) k_q1_linearize<3><<<(int)blocks, 128, 0, s>>>(g, k, U, pt, q32, q64);
-    else k_q1_linearize<2><<<(int)blocks, 128, 0, s>>>(g, k, U, pt, q32, q64);
+    k_q1_linearize<2><<<(int)blocks, 128, 0, s>>>(g, k, U, pt, q32, q64);
     return count_launch(cudaGetLastError());
 }
 
@@ -1062,7 +1070,7 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
     const S mu = cpair<S>(a.k.mu), lam = cpair<S>(a.k.lam);
 
     // displacement derivatives at the Gauss points -> shared memory
-#pragma unroll 1
+#pragma unroll (sizeof(S) == 4 ? 3 : 1)
     for (int c = 0; c < 3; ++c) {
         S v[NV];
 #pragma unroll
@@ -1143,7 +1151,7 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
     auto noff = [&](int n) {
         return (int64_t)(n & 1) + (int64_t)g.nn[0] * (((n >> 1) & 1) + (int64_t)g.nn[1] * ((n >> 2) & 1));
     };
-#pragma unroll 1
+#pragma unroll (sizeof(S) == 4 ? 3 : 1)
     for (int c = 0; c < 3; ++c) {
         S p[3][NH];
 #pragma unroll
@@ -1703,6 +1711,368 @@ k_q1_resdiag(Geom g, ResConsts rk, DiagConsts dk, const double* __restrict__ U, 
     }
 }
 
+// Residual -A(U) in 3D, one thread per cell in df64 with the layout of k_q1_apply_cell: U and phi~
+// staged in shared memory as df64, the 4 distinct Gauss-point values of each displacement
+// derivative and the Gauss-point values of phi and phi~ in per-cell shared slots, the 36 flux
+// sums in registers, element vectors added to R with FP64 atomics.  Arithmetic as in
+// k_q1_resdiag<3, 0>.
+__global__ void __launch_bounds__(128, 3)
+k_q1_residual_cell(Geom g, ResConsts rk, const double* __restrict__ U, const double* __restrict__ pt,
+                   double* __restrict__ y) {
+    using T = CellTile;
+    constexpr int NV = 8, NC = 4, NH = 4;
+    constexpr int NCELL = T::TX * T::TY * T::TZ;
+    constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = T::TZ + 1;
+    constexpr int NT = NTX * NTY * NTZ;
+    extern __shared__ __align__(16) unsigned char res_smem[];
+    df64* sv = reinterpret_cast<df64*>(res_smem);   // [field][node]: u_x, u_y, u_z, phi, phi~
+    df64* sgrad = sv + 5 * NT;                      // [(c * 3 + d) * 4 + class][cell]
+    df64* sq = sgrad + 9 * NH * NCELL;              // [q][cell]: phi(q) then the phi-row flux; [8 + q]: phi~(q)
+
+    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = blockIdx.z * T::TZ;
+    const int64_t nn = g.n_nodes;
+    for (int t = threadIdx.x; t < NT; t += NCELL) {
+        const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
+        const int gi = ci0 + ti, gj = cj0 + tj, gk = ck0 + tk;
+        const bool in = gi < g.nn[0] && gj < g.nn[1] && gk < g.nn[2];
+        const int64_t gn = in ? (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk) : 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sv[c * NT + t] = in ? df_from_double(U[c * nn + gn]) : df_make(0.f, 0.f);
+        sv[NC * NT + t] = in ? df_from_double(pt[gn]) : df_make(0.f, 0.f);
+    }
+    __syncthreads();
+
+    const int cell = threadIdx.x;
+    const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
+    const int gi = ci0 + li, gj = cj0 + lj, gk = ck0 + lk;
+    if (gi >= g.nc[0] || gj >= g.nc[1] || gk >= g.nc[2]) return;
+    const int64_t gid = (int64_t)gi + (int64_t)g.nc[0] * ((int64_t)gj + (int64_t)g.nc[1] * gk);
+    if (!cell_in(g, gid)) return;
+    const int tb = li + NTX * (lj + NTY * lk);
+    auto tnode = [&](int n) { return tb + (n & 1) + NTX * (((n >> 1) & 1) + NTY * ((n >> 2) & 1)); };
+    auto cls = [](int q, int d) { return (q & ((1 << d) - 1)) | ((q >> (d + 1)) << d); };
+    auto cg = [&](int d, int j) { return dfc(rk.cg[d][j]); };
+    auto cv = [&](int j) { return dfc(rk.cv[j]); };
+    const df64 sE = g.es ? df_from_double(g.es[gid]) : df_make(1.f, 0.f);
+    const df64 cmu = dfc(rk.mu) * sE, clam = dfc(rk.lam) * sE;
+
+    // phi rows: the gradient part (integrated: constant along its axis) and phi, phi~ at the
+    // Gauss points
+    df64 Hp[3][NH];
+    {
+        df64 vphi[NV], vpt[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) {
+            vphi[n] = sv[3 * NT + tnode(n)];
+            vpt[n] = sv[4 * NT + tnode(n)];
+        }
+        fwd<3>(vphi);
+        fwd<3>(vpt);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+                const int kp = ((j >> d) << (d + 1)) | (j & ((1 << d) - 1));
+                Hp[d][j] = df_scale(vphi[kp | (1 << d)] * cg(d, popc(kp)) * dfc(rk.wgce2), -(float)NH);
+            }
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            vphi[m] = vphi[m] * cv(popc(m));
+            vpt[m] = vpt[m] * cv(popc(m));
+        }
+        inv<3>(vphi);
+        inv<3>(vpt);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            sq[q * NCELL + cell] = vphi[q];
+            sq[(NV + q) * NCELL + cell] = vpt[q];
+        }
+    }
+    // displacement derivatives at the Gauss points
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        df64 m_[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) m_[n] = sv[c * NT + tnode(n)];
+        fwd<3>(m_);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            df64 t[NH];
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+                const int kp = ((j >> d) << (d + 1)) | (j & ((1 << d) - 1));
+                t[j] = m_[kp | (1 << d)] * cg(d, popc(kp));
+            }
+            inv<2>(t);
+#pragma unroll
+            for (int j = 0; j < NH; ++j) sgrad[((c * 3 + d) * NH + j) * NCELL + cell] = df_renorm(t[j]);
+        }
+    }
+
+    const df64 w = dfc(rk.w), omk = dfc(rk.omk), kap = dfc(rk.kap), f2k = dfc(rk.f2k), p2 = dfc(rk.p2);
+    df64 ps[3][3][NH];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        df64 gu[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) gu[c][d] = sgrad[((c * 3 + d) * NH + cls(q, d)) * NCELL + cell];
+        df64 e[3][3], tr = gu[0][0], ee = gu[0][0] * gu[0][0];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            e[a][a] = gu[a][a];
+            if (a > 0) { tr = tr + gu[a][a]; ee = ee + gu[a][a] * gu[a][a]; }
+#pragma unroll
+            for (int b = a + 1; b < 3; ++b) {
+                e[a][b] = df_scale(gu[a][b] + gu[b][a], 0.5f);
+                e[b][a] = e[a][b];
+                ee = ee + df_scale(e[a][b] * e[a][b], 2.f);
+            }
+        }
+        tr = df_renorm(tr);
+        const df64 Es = df_scale(clam * tr * tr, 0.5f) + cmu * ee;
+        const df64 phi = df_renorm(sq[q * NCELL + cell]), ptv = df_renorm(sq[(NV + q) * NCELL + cell]);
+        const df64 gk = omk * ptv * ptv + kap;
+        const df64 wg = w * gk, wp = w * ptv * ptv * dfc(rk.p);
+        const df64 ltr = clam * tr;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b) {
+                df64 sg = df_scale(cmu * e[a][b], 2.f);
+                if (a == b) sg = sg + ltr;
+                df64 f = wg * sg;
+                if (a == b) f = f + wp;
+                df64& pb = ps[a][b][cls(q, b)];
+                pb = ((q >> b) & 1) ? pb - f : -f;
+                if (a != b) {
+                    df64& pa = ps[b][a][cls(q, a)];
+                    pa = ((q >> a) & 1) ? pa - f : -f;
+                }
+            }
+        // value part of the phi rows: -w (f g'(phi) E_s + 2 p phi tr - Gc/eps (1 - phi))
+        const df64 one_m = df_make(1.f, 0.f) - phi;
+        sq[q * NCELL + cell] = w * (dfc(rk.gce) * one_m - f2k * phi * Es - p2 * phi * tr);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int j = 0; j < NH; ++j) sgrad[((c * 3 + d) * NH + j) * NCELL + cell] = ps[c][d][j];
+
+    const int64_t gn0 = (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk);
+    auto noff = [&](int n) {
+        return (int64_t)(n & 1) + (int64_t)g.nn[0] * (((n >> 1) & 1) + (int64_t)g.nn[1] * ((n >> 2) & 1));
+    };
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        df64 p[3][NH];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int j = 0; j < NH; ++j) p[d][j] = sgrad[((c * 3 + d) * NH + j) * NCELL + cell];
+            fwd<2>(p[d]);
+        }
+        df64 Y[NV];
+        Y[0] = df_make(0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k < NV; ++k) {
+            const int d0 = (k & 1) ? 0 : ((k & 2) ? 1 : 2);
+            df64 acc = p[d0][cls(k & ~(1 << d0), d0)] * cg(d0, popc(k) - 1);
+#pragma unroll
+            for (int d = d0 + 1; d < 3; ++d) {
+                if (!(k & (1 << d))) continue;
+                const int kp = k & ~(1 << d);
+                acc = acc + p[d][cls(kp, d)] * cg(d, popc(kp));
+            }
+            Y[k] = acc;
+        }
+        inv3_v0_zero(Y);
+        double* yc = y + c * nn + gn0;
+#pragma unroll
+        for (int n = 0; n < NV; ++n) atomicAdd(yc + noff(n), df_to_double(Y[n]));
+    }
+    {
+        df64 fv[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) fv[q] = sq[q * NCELL + cell];
+        fwd<3>(fv);
+        df64 Y[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            df64 acc = fv[k] * cv(popc(k));
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (!(k & (1 << d))) continue;
+                const int kp = k & ~(1 << d);
+                acc = acc + Hp[d][cls(kp, d)] * cg(d, popc(kp));
+            }
+            Y[k] = acc;
+        }
+        inv<3>(Y);
+#pragma unroll
+        for (int n = 0; n < NV; ++n) atomicAdd(&y[3 * nn + gn0 + noff(n)], df_to_double(Y[n]));
+    }
+}
+
+static constexpr size_t residual_cell_smem_bytes() {
+    using T = CellTile;
+    constexpr int NCELL = T::TX * T::TY * T::TZ, NT = (T::TX + 1) * (T::TY + 1) * (T::TZ + 1);
+    return sizeof(df64) * (5 * NT + 9 * 4 * NCELL + 16 * NCELL);
+}
+
+// Gauss-point linearisation data in 3D with the tile layout of k_q1_apply_cell: U and phi~ staged
+// in shared memory as df64 (one conversion per tile node), the displacement derivatives at the
+// Gauss points in per-cell shared slots; one thread per cell writes its 8 x NK coefficients.
+// Arithmetic as in k_q1_linearize<3>.
+__global__ void __launch_bounds__(128, 4)
+k_q1_linearize_cell(Geom g, LinConsts k, const double* __restrict__ U, const double* __restrict__ pt,
+                    float* __restrict__ q32, float2* __restrict__ q64) {
+    using T = CellTile;
+    constexpr int NV = 8, NC = 4, NH = 4, NK = Q1Dims<3>::NK;
+    constexpr int NCELL = T::TX * T::TY * T::TZ;
+    constexpr int NTX = T::TX + 1, NTY = T::TY + 1, NTZ = T::TZ + 1;
+    constexpr int NT = NTX * NTY * NTZ;
+    extern __shared__ __align__(16) unsigned char lin_smem[];
+    df64* sv = reinterpret_cast<df64*>(lin_smem);   // [field][node]: u_x, u_y, u_z, phi, phi~
+    df64* sgrad = sv + 5 * NT;                      // [(c * 3 + d) * 4 + class][cell]
+
+    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = blockIdx.z * T::TZ;
+    const int64_t nn = g.n_nodes, nc = g.n_cells;
+    for (int t = threadIdx.x; t < NT; t += NCELL) {
+        const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
+        const int gi = ci0 + ti, gj = cj0 + tj, gk = ck0 + tk;
+        const bool in = gi < g.nn[0] && gj < g.nn[1] && gk < g.nn[2];
+        const int64_t gn = in ? (int64_t)gi + (int64_t)g.nn[0] * ((int64_t)gj + (int64_t)g.nn[1] * gk) : 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sv[c * NT + t] = in ? df_from_double(U[c * nn + gn]) : df_make(0.f, 0.f);
+        sv[NC * NT + t] = in ? df_from_double(pt[gn]) : df_make(0.f, 0.f);
+    }
+    __syncthreads();
+
+    const int cell = threadIdx.x;
+    const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
+    const int gi = ci0 + li, gj = cj0 + lj, gk = ck0 + lk;
+    if (gi >= g.nc[0] || gj >= g.nc[1] || gk >= g.nc[2]) return;
+    const int64_t gid = (int64_t)gi + (int64_t)g.nc[0] * ((int64_t)gj + (int64_t)g.nc[1] * gk);
+    if (!cell_in(g, gid)) return;
+    const int tb = li + NTX * (lj + NTY * lk);
+    auto tnode = [&](int n) { return tb + (n & 1) + NTX * (((n >> 1) & 1) + NTY * ((n >> 2) & 1)); };
+    auto cls = [](int q, int d) { return (q & ((1 << d) - 1)) | ((q >> (d + 1)) << d); };
+    const df64 sE = g.es ? df_from_double(g.es[gid]) : df_make(1.f, 0.f);
+    const df64 cmu = dfc(k.mu) * sE, clam = dfc(k.lam) * sE;
+
+    // Gauss-point values of phi and phi~
+    df64 vphi[NV], vpt[NV];
+#pragma unroll
+    for (int n = 0; n < NV; ++n) {
+        vphi[n] = sv[3 * NT + tnode(n)];
+        vpt[n] = sv[4 * NT + tnode(n)];
+    }
+    fwd<3>(vphi);
+    fwd<3>(vpt);
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        vphi[m] = vphi[m] * dfc(k.cv[popc(m)]);
+        vpt[m] = vpt[m] * dfc(k.cv[popc(m)]);
+    }
+    inv<3>(vphi);
+    inv<3>(vpt);
+    // displacement derivatives at the Gauss points
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        df64 m_[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) m_[n] = sv[c * NT + tnode(n)];
+        fwd<3>(m_);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            df64 t[NH];
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+                const int kp = ((j >> d) << (d + 1)) | (j & ((1 << d) - 1));
+                t[j] = m_[kp | (1 << d)] * dfc(k.cg[d][popc(kp)]);
+            }
+            inv<2>(t);
+#pragma unroll
+            for (int j = 0; j < NH; ++j) sgrad[((c * 3 + d) * NH + j) * NCELL + cell] = df_renorm(t[j]);
+        }
+    }
+    const df64 w = dfc(k.w), omk = dfc(k.omk), kap = dfc(k.kap), f2k = dfc(k.f2k), p2 = dfc(k.p2);
+    const df64 gce = dfc(k.gce);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        df64 gu[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) gu[c][d] = sgrad[((c * 3 + d) * NH + cls(q, d)) * NCELL + cell];
+        df64 e[3][3], tr = gu[0][0], ee = gu[0][0] * gu[0][0];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            e[i][i] = gu[i][i];
+            if (i > 0) { tr = tr + gu[i][i]; ee = ee + gu[i][i] * gu[i][i]; }
+#pragma unroll
+            for (int jx = i + 1; jx < 3; ++jx) {
+                e[i][jx] = df_scale(gu[i][jx] + gu[jx][i], 0.5f);
+                e[jx][i] = e[i][jx];
+                ee = ee + df_scale(e[i][jx] * e[i][jx], 2.f);
+            }
+        }
+        tr = df_renorm(tr);
+        const df64 Es = df_scale(clam * tr * tr, 0.5f) + cmu * ee;
+        const df64 phi = df_renorm(vphi[q]), ptv = df_renorm(vpt[q]);
+        df64 vals[NK];
+        vals[0] = w * (omk * ptv * ptv + kap) * sE;
+        const df64 a1 = f2k * phi, b1 = p2 * phi;
+        const df64 ltr = clam * tr;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int jx = i; jx < 3; ++jx) {
+                df64 sig = df_scale(cmu * e[i][jx], 2.f);
+                if (i == jx) sig = sig + ltr;
+                df64 v = a1 * sig;
+                if (i == jx) v = v + b1;
+                vals[1 + sidx<3>(i, jx)] = w * v;
+            }
+        vals[NK - 1] = w * (f2k * Es + p2 * tr + gce);
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) {
+            const df64 v = df_renorm(vals[kk]);
+            const int64_t idx = (int64_t)(q * NK + kk) * nc + gid;
+            q32[idx] = v.hi;
+            q64[idx] = make_float2(v.hi, v.lo);
+        }
+    }
+}
+
+static constexpr size_t linearize_cell_smem_bytes() {
+    using T = CellTile;
+    constexpr int NCELL = T::TX * T::TY * T::TZ, NT = (T::TX + 1) * (T::TY + 1) * (T::TZ + 1);
+    return sizeof(df64) * (5 * NT + 9 * 4 * NCELL);
+}
+
+static cudaError_t launch_linearize_cell(const Geom& g, const LinConsts& k, const double* U, const double* pt,
+                                         float* q32, float2* q64, cudaStream_t s) {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!(dev >= 0 && dev < 64 && done[dev])) {
+        e = cudaFuncSetAttribute(k_q1_linearize_cell, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)linearize_cell_smem_bytes());
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    using T = CellTile;
+    dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
+    k_q1_linearize_cell<<<grid, T::TX * T::TY * T::TZ, linearize_cell_smem_bytes(), s>>>(g, k, U, pt, q32, q64);
+    return count_launch(cudaGetLastError());
+}
+
 static ResConsts make_res_consts(const Geom& g, const Phys& ph) {
     ResConsts k;
     fill_lin_consts(g, ph, k);
@@ -1744,6 +2114,22 @@ static cudaError_t launch_resdiag(const Geom& g, const Phys& ph, const double* U
                                   const float2* q64, const uint8_t* mask, double* y, cudaStream_t s) {
     const DiagConsts dk = make_diag_consts(g, ph);
     const ResConsts rk = make_res_consts(g, ph);
+    if (OP == 0 && g.dim == 3) {
+        static bool done[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (!(dev >= 0 && dev < 64 && done[dev])) {
+            e = cudaFuncSetAttribute(k_q1_residual_cell, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)residual_cell_smem_bytes());
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) done[dev] = true;
+        }
+        using T = CellTile;
+        dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
+        k_q1_residual_cell<<<grid, T::TX * T::TY * T::TZ, residual_cell_smem_bytes(), s>>>(g, rk, U, pt, y);
+        return count_launch(cudaGetLastError());
+    }
     if (g.dim == 3) {
         using T = RDTile<3>;
         dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);

@@ -7,6 +7,7 @@
 //  - deterministic two-stage reductions (fixed grid, fixed summation order),
 //  - SplitMix64 counter-based start vector (Steele, Lea, Flood 2014),
 //  - lumped Gauss-Lobatto mass and active-set decision (Algorithm 1, steps 1-4).
+#include "pff_df64.cuh"
 #include "pff_internal.cuh"
 
 namespace pff {
@@ -367,15 +368,45 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
     __syncthreads();
 }
 
+// FP32 vectors: the product of two floats is exact as a double-float pair (FMA) and the per-thread
+// sums run in double-float on the FP32 pipes (FP64 arithmetic issues at 1/64 of the FP32 rate on
+// GB300, which made these reductions FP64-bound); FP64 vectors: plain FP64.
 template <typename T>
 __global__ void k_block_dots_partial(int64_t nn, int dim, const T* __restrict__ a, const T* __restrict__ b,
                                      const T* __restrict__ w, double* __restrict__ part) {
     const int64_t nd = nn * (dim + 1), nu = nn * dim;
     double su = 0.0, sp = 0.0;
-    GRID_STRIDE(i, nd) {
-        double v = (double)a[i] * (double)b[i];
-        if (w) v *= (double)w[i];
-        if (i < nu) su += v; else sp += v;
+    if constexpr (sizeof(T) == 4) {
+        // four elements per iteration so that each thread keeps several loads in flight
+        constexpr int U = 4;
+        df64 fu = df_make(0.f, 0.f), fp = df_make(0.f, 0.f);
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nd; i0 += U * stride) {
+            float x[U], y[U], z[U];
+#pragma unroll
+            for (int r = 0; r < U; ++r) {
+                const int64_t i = i0 + r * stride;
+                x[r] = i < nd ? a[i] : 0.f;
+                y[r] = i < nd ? b[i] : 0.f;
+                z[r] = (w && i < nd) ? w[i] : 1.f;
+            }
+#pragma unroll
+            for (int r = 0; r < U; ++r) {
+                const int64_t i = i0 + r * stride;
+                const float pr = __fmul_rn(x[r], y[r]);
+                df64 v = df_make(pr, __fmaf_rn(x[r], y[r], -pr));
+                if (w) v = v * df_make(z[r], 0.f);
+                if (i < nu) fu = fu + v; else fp = fp + v;
+            }
+        }
+        su = df_to_double(fu);
+        sp = df_to_double(fp);
+    } else {
+        GRID_STRIDE(i, nd) {
+            double v = (double)a[i] * (double)b[i];
+            if (w) v *= (double)w[i];
+            if (i < nu) su += v; else sp += v;
+        }
     }
     block_sum2(su, sp);
     if (threadIdx.x == 0) { part[2 * blockIdx.x] = su; part[2 * blockIdx.x + 1] = sp; }
