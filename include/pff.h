@@ -230,6 +230,15 @@ pff_status pff_apply_jacobian(pff_hierarchy* h, int level, const double* x, doub
 /* The same operator evaluated in FP32 arithmetic with FP32 accumulation (V-cycle operator). */
 pff_status pff_apply_jacobian_f32(pff_hierarchy* h, int level, const float* x, float* y);
 
+/* pff_apply_jacobian with x and y in HOST memory (n_dofs doubles each, layout as above; page-
+ * locked memory lets the copies overlap the computation).  On 3D levels served by the per-cell
+ * kernel (variant 0: at least 100,000 cells) the level is processed in slabs of z layers, the
+ * host-to-device copy of one slab, the apply of the previous one and the device-to-host copy of
+ * finished nodes running concurrently on three streams; other levels copy, apply and copy back in
+ * order.  Uses two library-owned device vectors of the finest level's size (allocated on first
+ * use).  Synchronises.  Errors: as pff_apply_jacobian. */
+pff_status pff_apply_jacobian_host(pff_hierarchy* h, int level, const double* x, double* y);
+
 /* Diagonal of G~_l (1 on eliminated rows), computed matrix-free (remark in Sec. 4.1).
  * precision 64 -> double* d, 32 -> float* d. */
 pff_status pff_diagonal(pff_hierarchy* h, int level, int precision, void* d);

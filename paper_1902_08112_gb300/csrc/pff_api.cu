@@ -285,6 +285,9 @@ extern "C" pff_status pff_destroy_hierarchy(pff_hierarchy* h) {
     cudaStreamSynchronize(h->stream);
     drop_graph(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->slab_ev) cudaEventDestroy(e);
+    if (h->cs_in) cudaStreamDestroy(h->cs_in);
+    if (h->cs_out) cudaStreamDestroy(h->cs_out);
     free_all(h);
     delete h;
     return PFF_OK;
@@ -503,6 +506,93 @@ extern "C" pff_status pff_apply_jacobian(pff_hierarchy* h, int level, const doub
 
 extern "C" pff_status pff_apply_jacobian_f32(pff_hierarchy* h, int level, const float* x, float* y) {
     return apply_checked<float>(h, level, x, y);
+}
+
+// y = G~_l x with x, y in host memory.  On 3D levels served by the per-cell FP64-accurate kernel
+// the level is cut into slabs of z node layers and three streams overlap the host-to-device copy of
+// slab s + 1, the apply of slab s and the device-to-host copy of the finished nodes.
+extern "C" pff_status pff_apply_jacobian_host(pff_hierarchy* h, int level, const double* x, double* y) {
+    if (!h) return PFF_EINVAL;
+    const int l = resolve_level(h, level);
+    REQUIRE(h, l >= 0 && l < h->L, PFF_EINVAL, "level out of range");
+    REQUIRE(h, x && y && (const void*)x != (const void*)y, PFF_EINVAL, "apply: NULL or aliased vectors");
+    REQUIRE(h, h->has_state, PFF_ESTATE, "apply before pff_set_state");
+    Level& L = h->lv[l];
+    const Geom& g = L.g;
+    const int64_t nn = g.n_nodes, nd = n_dofs(g);
+    cudaStream_t s = h->stream;
+    if (!h->hx) {
+        const int64_t nmax = n_dofs(h->lv[h->L - 1].g);
+        CUDA_OR_FAIL(h, dalloc(h, &h->hx, (size_t)nmax));
+        CUDA_OR_FAIL(h, dalloc(h, &h->hy, (size_t)nmax));
+    }
+    const bool slabs = g.dim == 3 && g.deg == 1 && h->fast_q1 && !h->ph.split &&
+                       ((h->q1_style & 64) != 0 || ((h->q1_style & 16) != 0 && g.n_cells >= kCell64MinCells));
+    if (!slabs) {
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->hx, x, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+        CUDA_OR_FAIL(h, apply_level<double>(h, l, OP_APPLY, h->hx, h->hy, PHI_BITS_ALL));
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(y, h->hy, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(s));
+        return PFF_OK;
+    }
+    CUDA_OR_FAIL(h, refresh_state(h));
+    const int TZ = q1_cell_tile_z(), ncz = g.nc[2];
+    int zc = (ncz + 7) / 8;                  // about 8 slabs, each a whole number of CTA tiles
+    zc = ((zc + TZ - 1) / TZ) * TZ;
+    const int S = (ncz + zc - 1) / zc;
+    if (!h->cs_in) {
+        CUDA_OR_FAIL(h, cudaStreamCreateWithFlags(&h->cs_in, cudaStreamNonBlocking));
+        CUDA_OR_FAIL(h, cudaStreamCreateWithFlags(&h->cs_out, cudaStreamNonBlocking));
+    }
+    while ((int)h->slab_ev.size() < 2 * S + 1) {
+        cudaEvent_t e;
+        CUDA_OR_FAIL(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->slab_ev.push_back(e);
+    }
+    cudaEvent_t* ev_in = h->slab_ev.data() + 1;
+    cudaEvent_t* ev_app = ev_in + S;
+    const int64_t layer = (int64_t)g.nn[0] * g.nn[1];
+    auto nodes = [&](int sl, int64_t& n0, int64_t& n1) {   // node layers [sl zc, (sl + 1) zc), the last to the top
+        n0 = (int64_t)sl * zc * layer;
+        n1 = sl + 1 < S ? (int64_t)(sl + 1) * zc * layer : nn;
+    };
+    // the copies start after the library's earlier work on hx and hy
+    CUDA_OR_FAIL(h, cudaEventRecord(h->slab_ev[0], s));
+    CUDA_OR_FAIL(h, cudaStreamWaitEvent(h->cs_in, h->slab_ev[0], 0));
+    for (int sl = 0; sl < S; ++sl) {
+        int64_t n0, n1;
+        nodes(sl, n0, n1);
+        for (int c = 0; c <= g.dim; ++c)
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(h->hx + c * nn + n0, x + c * nn + n0, (n1 - n0) * sizeof(double),
+                                            cudaMemcpyHostToDevice, h->cs_in));
+        CUDA_OR_FAIL(h, cudaEventRecord(ev_in[sl], h->cs_in));
+    }
+    // slab sl's cells reach the first node layer of slab sl + 1: apply slab sl once slab sl + 1 is
+    // copied and preset
+    for (int sl = 0; sl <= S; ++sl) {
+        if (sl < S) {
+            int64_t n0, n1;
+            nodes(sl, n0, n1);
+            CUDA_OR_FAIL(h, cudaStreamWaitEvent(s, ev_in[sl], 0));
+            CUDA_OR_FAIL(h, launch_init_masked_nodes(g, L.mask, MASK_U_ALL, PHI_BITS_ALL, h->hx, h->hy, n0, n1, s));
+        }
+        if (sl >= 1) {
+            const int a = sl - 1, k0 = a * zc, k1 = std::min(ncz, (a + 1) * zc);
+            CUDA_OR_FAIL(h, launch_q1_apply64_slab(g, h->ph, L.qpd64, h->hx, h->hy, L.mask, PHI_BITS_ALL, k0, k1, s));
+            CUDA_OR_FAIL(h, cudaEventRecord(ev_app[a], s));
+        }
+    }
+    for (int sl = 0; sl < S; ++sl) {
+        int64_t n0, n1;
+        nodes(sl, n0, n1);
+        CUDA_OR_FAIL(h, cudaStreamWaitEvent(h->cs_out, ev_app[sl], 0));
+        for (int c = 0; c <= g.dim; ++c)
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(y + c * nn + n0, h->hy + c * nn + n0, (n1 - n0) * sizeof(double),
+                                            cudaMemcpyDeviceToHost, h->cs_out));
+    }
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->cs_out));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(s));
+    return PFF_OK;
 }
 
 extern "C" pff_status pff_diagonal(pff_hierarchy* h, int level, int precision, void* d) {

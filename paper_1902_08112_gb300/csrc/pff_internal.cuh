@@ -97,6 +97,9 @@ cudaError_t launch_cell_op(int op, const CellArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init_masked(const Geom& g, const uint8_t* mask, int u_bits, int phi_bits,
                                const T* x, T* y, T eliminated_value, cudaStream_t s);
+// the same on the nodes [node0, node1) only (all components), FP64
+cudaError_t launch_init_masked_nodes(const Geom& g, const uint8_t* mask, int u_bits, int phi_bits, const double* x,
+                                     double* y, int64_t node0, int64_t node1, cudaStream_t s);
 
 // ---------------------------------------------------------------- vector kernels (pff_vec.cu)
 cudaError_t launch_restrict_state(const Geom& gc, const Geom& gf, const double* Uf, const double* ptf,
@@ -230,6 +233,11 @@ struct pff_hierarchy {
     // kernel timing: event pairs per class, recorded while prof_on
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
+    // host-buffer apply: device copies of x and y, copy streams, one event per slab and stage
+    double* hx = nullptr;
+    double* hy = nullptr;
+    cudaStream_t cs_in = nullptr, cs_out = nullptr;
+    std::vector<cudaEvent_t> slab_ev;
     size_t ev_used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[PFF_PROF_NCLASS];
     std::string err;

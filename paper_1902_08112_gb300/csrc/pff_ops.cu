@@ -443,6 +443,28 @@ cudaError_t launch_init_masked(const Geom& g, const uint8_t* mask, int u_bits, i
     return count_launch(cudaGetLastError());
 }
 
+// The same preset on the nodes [node0, node1) only (all components), FP64.
+__global__ void k_init_masked_nodes(int64_t nn, int dim, int64_t node0, int64_t node1, const uint8_t* __restrict__ mask,
+                                    int u_bits, int phi_bits, const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t cnt = node1 - node0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt * (dim + 1);
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / cnt);
+        const int64_t n = node0 + (t - (int64_t)c * cnt), i = (int64_t)c * nn + n;
+        const uint8_t m = mask[n];
+        const bool e = c < dim ? (((m & u_bits) >> c) & 1) != 0 : (m & phi_bits) != 0;
+        y[i] = e ? x[i] : 0.0;
+    }
+}
+cudaError_t launch_init_masked_nodes(const Geom& g, const uint8_t* mask, int u_bits, int phi_bits, const double* x,
+                                     double* y, int64_t node0, int64_t node1, cudaStream_t s) {
+    if (node1 <= node0) return cudaSuccess;
+    const int64_t nd = (node1 - node0) * (g.dim + 1);
+    k_init_masked_nodes<<<grid_for(nd, 256), 256, 0, s>>>(g.n_nodes, g.dim, node0, node1, mask, u_bits, phi_bits,
+                                                          x, y);
+    return count_launch(cudaGetLastError());
+}
+
 template cudaError_t launch_init_masked<double>(const Geom&, const uint8_t*, int, int, const double*, double*,
                                                 double, cudaStream_t);
 template cudaError_t launch_init_masked<float>(const Geom&, const uint8_t*, int, int, const float*, float*,

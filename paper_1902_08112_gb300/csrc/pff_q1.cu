@@ -1039,7 +1039,7 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
     uint8_t* smask = reinterpret_cast<uint8_t*>(sfq + NV * NCELL);
 
     const Geom& g = a.g;
-    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = blockIdx.z * T::TZ;
+    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = (blockIdx.z + a.tz0) * T::TZ;
     const int64_t nn = g.n_nodes;
     for (int t = threadIdx.x; t < NT; t += NCELL) {
         const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
@@ -1059,7 +1059,7 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
     const int cell = threadIdx.x;
     const int li = cell % T::TX, lj = (cell / T::TX) % T::TY, lk = cell / (T::TX * T::TY);
     const int gi = ci0 + li, gj = cj0 + lj, gk = ck0 + lk;
-    if (gi >= g.nc[0] || gj >= g.nc[1] || gk >= g.nc[2]) return;
+    if (gi >= g.nc[0] || gj >= g.nc[1] || gk >= g.nc[2] || gk >= a.kz_end) return;
     const int64_t gid = (int64_t)gi + (int64_t)g.nc[0] * ((int64_t)gj + (int64_t)g.nc[1] * gk);
     if (!cell_in(g, gid)) return;
     const int tb = li + NTX * (lj + NTY * lk);
@@ -1352,6 +1352,29 @@ static cudaError_t launch_cell(const Q1ApplyArgs<typename Scalar<S>::storage, ty
     if (e != cudaSuccess) return e;
     dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
     k_q1_apply_cell<S, BD><<<grid, T::TX * T::TY * T::TZ, cell_smem_bytes<S>(), s>>>(a);
+    return count_launch(cudaGetLastError());
+}
+
+int q1_cell_tile_z() { return CellTile::TZ; }
+
+cudaError_t launch_q1_apply64_slab(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
+                                   const uint8_t* mask, int phi_bits, int kz0, int kz1, cudaStream_t s) {
+    using T = CellTile;
+    if (g.dim != 3 || kz0 % T::TZ != 0 || kz0 < 0 || kz1 > g.nc[2] || kz1 <= kz0) return cudaErrorInvalidValue;
+    Q1ApplyArgs<double, float2> a;
+    a.g = g;
+    a.qd = qd;
+    a.x = x;
+    a.y = y;
+    a.mask = mask;
+    a.phi_bits = phi_bits;
+    fill_consts(a, ph);
+    a.tz0 = kz0 / T::TZ;
+    a.kz_end = kz1;
+    const cudaError_t e = cell_prepare<df64, false>();
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (kz1 - kz0 + T::TZ - 1) / T::TZ);
+    k_q1_apply_cell<df64, false><<<grid, T::TX * T::TY * T::TZ, cell_smem_bytes<df64>(), s>>>(a);
     return count_launch(cudaGetLastError());
 }
 

@@ -31,6 +31,8 @@ struct Q1ApplyArgs {
     const uint8_t* mask;
     int phi_bits;
     Q1Consts k;
+    int tz0 = 0;             // k_q1_apply_cell: first tile along z, and the end of the cell layers
+    int kz_end = 1 << 30;    // applied (a slab of the level); the whole level by default
 };
 
 // number of stored coefficients per Gauss point and cell (c0, Sp, c1)
@@ -40,6 +42,11 @@ cudaError_t launch_q1_linearize(const Geom& g, const Phys& ph, const double* U, 
                                 float2* q64, cudaStream_t s);
 // lanes = true: one thread per (cell, Gauss point) with shuffle butterflies; false: one thread
 // per cell with the modal form in registers
+// The FP64-accurate per-cell apply on the cell layers [kz0, kz1) of a 3D level (kz0 a multiple
+// of q1_cell_tile_z()), adding to y without presetting it.
+int q1_cell_tile_z();
+cudaError_t launch_q1_apply64_slab(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
+                                   const uint8_t* mask, int phi_bits, int kz0, int kz1, cudaStream_t s);
 // cell = true (3D): one thread per cell in df64 with shared-memory Gauss-point derivatives
 cudaError_t launch_q1_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
                               const uint8_t* mask, int phi_bits, bool blockdiag, bool lanes, cudaStream_t s,

@@ -73,6 +73,7 @@ SIGNATURES = {
     "pff_boundary_load": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "pff_apply_jacobian": (_I, [_VP, _I, _VP, _VP]),
     "pff_apply_jacobian_f32": (_I, [_VP, _I, _VP, _VP]),
+    "pff_apply_jacobian_host": (_I, [_VP, _I, _VP, _VP]),
     "pff_diagonal": (_I, [_VP, _I, _I, _VP]),
     "pff_level_state": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pff_restrict": (_I, [_VP, _I, _I, _VP, _VP]),
@@ -245,6 +246,13 @@ def residual(h, R):
 
 def apply_jacobian(h, level, x, y):
     return _check(h, load().pff_apply_jacobian(h, level, _ptr(x), _ptr(y)), "pff_apply_jacobian")
+
+
+def apply_jacobian_host(h, level, x, y):
+    """x, y: CPU tensors (pinned for overlap) of the level's n_dofs doubles."""
+    if hasattr(x, "device") and (x.device.type != "cpu" or y.device.type != "cpu"):
+        raise ValueError("apply_jacobian_host takes host (CPU) tensors")
+    return _check(h, load().pff_apply_jacobian_host(h, level, _ptr(x), _ptr(y)), "pff_apply_jacobian_host")
 
 
 def apply_jacobian_f32(h, level, x, y):
