@@ -58,7 +58,7 @@ def build(verbose: bool = False, extra: list | None = None) -> str:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if jobs or not os.path.exists(LIB) or _needs(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        cmd = [nvcc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

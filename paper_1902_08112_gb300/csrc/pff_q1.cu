@@ -1737,8 +1737,8 @@ k_q1_resdiag(Geom g, ResConsts rk, DiagConsts dk, const double* __restrict__ U, 
 // Residual -A(U) in 3D, one thread per cell in df64 with the layout of k_q1_apply_cell: U and phi~
 // staged in shared memory as df64, the 4 distinct Gauss-point values of each displacement
 // derivative and the Gauss-point values of phi and phi~ in per-cell shared slots, the 36 flux
-// sums in registers, element vectors added to R with FP64 atomics.  Arithmetic as in
-// k_q1_resdiag<3, 0>.
+// sums in registers, element vectors added to R with FP64 atomics.  Arithmetic as in the residual
+// branch of k_q1_resdiag (which serves 2D).
 __global__ void __launch_bounds__(128, 3)
 k_q1_residual_cell(Geom g, ResConsts rk, const double* __restrict__ U, const double* __restrict__ pt,
                    double* __restrict__ y) {
@@ -1949,7 +1949,7 @@ static constexpr size_t residual_cell_smem_bytes() {
 // Gauss-point linearisation data in 3D with the tile layout of k_q1_apply_cell: U and phi~ staged
 // in shared memory as df64 (one conversion per tile node), the displacement derivatives at the
 // Gauss points in per-cell shared slots; one thread per cell writes its 8 x NK coefficients.
-// Arithmetic as in k_q1_linearize<3>.
+// Arithmetic as in k_q1_linearize (which serves 2D).
 __global__ void __launch_bounds__(128, 4)
 k_q1_linearize_cell(Geom g, LinConsts k, const double* __restrict__ U, const double* __restrict__ pt,
                     float* __restrict__ q32, float2* __restrict__ q64) {
@@ -2137,7 +2137,13 @@ static cudaError_t launch_resdiag(const Geom& g, const Phys& ph, const double* U
                                   const float2* q64, const uint8_t* mask, double* y, cudaStream_t s) {
     const DiagConsts dk = make_diag_consts(g, ph);
     const ResConsts rk = make_res_consts(g, ph);
-    if (OP == 0 && g.dim == 3) {
+    if constexpr (OP == 0) {
+        if (g.dim != 3) {
+            using T = RDTile<2>;
+            dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, 1);
+            k_q1_resdiag<2, 0><<<grid, T::TX * T::TY, 0, s>>>(g, rk, dk, U, pt, q64, mask, y);
+            return count_launch(cudaGetLastError());
+        }
         static bool done[64] = {};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -2152,8 +2158,7 @@ static cudaError_t launch_resdiag(const Geom& g, const Phys& ph, const double* U
         dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
         k_q1_residual_cell<<<grid, T::TX * T::TY * T::TZ, residual_cell_smem_bytes(), s>>>(g, rk, U, pt, y);
         return count_launch(cudaGetLastError());
-    }
-    if (g.dim == 3) {
+    } else if (g.dim == 3) {
         using T = RDTile<3>;
         dim3 grid((g.nc[0] + T::TX - 1) / T::TX, (g.nc[1] + T::TY - 1) / T::TY, (g.nc[2] + T::TZ - 1) / T::TZ);
         k_q1_resdiag<3, OP><<<grid, T::TX * T::TY * T::TZ, 0, s>>>(g, rk, dk, U, pt, q64, mask, y);
