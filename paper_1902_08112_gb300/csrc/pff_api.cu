@@ -224,6 +224,10 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
     if (e == cudaSuccess) e = dalloc(h, &h->d_counts, 16);
     if (e == cudaSuccess) e = dalloc(h, &h->d_scal, 4096);
     if (e == cudaSuccess) e = dalloc(h, &h->d_scratch, (size_t)dot_partials() * 64);
+    if (e == cudaSuccess) e = dalloc(h, &h->d_scal_lv, (size_t)kLevelScal * h->L);
+    if (e == cudaSuccess) e = dalloc(h, &h->d_scratch_lv, (size_t)kLevelScratch * h->L);
+    for (int l = 0; l < h->L && e == cudaSuccess; ++l) e = cudaStreamCreateWithFlags(&h->lv_stream[l], cudaStreamNonBlocking);
+    for (int l = 0; l <= h->L && e == cudaSuccess; ++l) e = cudaEventCreateWithFlags(&h->lv_event[l], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         st = (e == cudaErrorMemoryAllocation) ? PFF_ENOMEM : PFF_ECUDA;
         cudaGetLastError();
@@ -286,6 +290,10 @@ extern "C" pff_status pff_destroy_hierarchy(pff_hierarchy* h) {
     drop_graph(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : h->slab_ev) cudaEventDestroy(e);
+    for (cudaStream_t st : h->lv_stream)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : h->lv_event)
+        if (e) cudaEventDestroy(e);
     if (h->cs_in) cudaStreamDestroy(h->cs_in);
     if (h->cs_out) cudaStreamDestroy(h->cs_out);
     free_all(h);
@@ -323,7 +331,8 @@ extern "C" int64_t pff_hierarchy_bytes(const pff_mesh* mesh, int restart) {
         nd_f = nd;
     }
     total += (nn_f + pad) + 2 * (nn_f * 8 + pad) + (nd_f * 8 + pad) + 4 * (nd_f * 8 + pad) + (nn_f + pad) +
-             (16 * 4 + pad) + (4096 * 8 + pad) + ((int64_t)dot_partials() * 64 * 8 + pad);
+             (16 * 4 + pad) + (4096 * 8 + pad) + ((int64_t)dot_partials() * 64 * 8 + pad) +
+             ((int64_t)kLevelScal * mesh->n_levels * 8 + pad) + ((int64_t)kLevelScratch * mesh->n_levels * 8 + pad);
     if (restart > 0) total += ((int64_t)(restart + 1) * nd_f * 8 + pad) + ((int64_t)restart * nd_f * 8 + pad) +
                               ((int64_t)(2 * (restart + 1) + 2) * 8 + pad);
     return total;

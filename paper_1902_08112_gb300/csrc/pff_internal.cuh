@@ -190,6 +190,8 @@ cudaError_t launch_gemv_add(int64_t n, const double* Z, int64_t ld, int k, const
 }  // namespace pff
 
 // The opaque hierarchy of the C ABI.
+constexpr int kLevelScal = 256, kLevelScratch = 1024;
+
 // Smallest 3D level that the per-cell applies with shared-memory derivatives serve by default: below
 // about two waves of their CTAs the lane and per-cell-gather kernels finish sooner.
 constexpr int64_t kCell64MinCells = 100000;
@@ -211,6 +213,12 @@ struct pff_hierarchy {
     uint8_t* prev_active = nullptr;
     int* d_counts = nullptr;         // device counters
     double* d_scal = nullptr;        // device scalars (dots, CG coefficients)
+    // setup runs the levels concurrently: one stream per level, a private region of CG scalars
+    // (kLevelScal doubles) and of dot partials (kLevelScratch doubles) per level
+    double* d_scal_lv = nullptr;
+    double* d_scratch_lv = nullptr;
+    cudaStream_t lv_stream[16] = {};
+    cudaEvent_t lv_event[17] = {};
     double* d_scratch = nullptr;     // per-CTA partial sums
     // Krylov workspace
     int kr_m = 0;

@@ -276,21 +276,23 @@ static cudaError_t eigen_estimate(pff_hierarchy* h, int l, double* d_out) {
     T* z = work<T>(L, 3);
     T* q = work<T>(L, 4);
     T* p = work<T>(L, 5);
-    double* sc = h->d_scal;
+    double* sc = h->d_scal_lv + (size_t)kLevelScal * l;         // per level: setup runs levels concurrently
+    double* scratch = h->d_scratch_lv + (size_t)kLevelScratch * l;
+    static_assert(S_HIST + 4 * MAX_CG <= kLevelScal, "CG scalars exceed the per-level region");
     const int steps = std::min(h->prm.cg_steps, MAX_CG);
     CK(cudaMemsetAsync(sc, 0, sizeof(double) * (S_HIST + 4 * MAX_CG), s));
     CK(launch_start_vector<T>(L.g, L.mask, h->prm.seed, l, r, s));
     // z = dinv r (an update with the zeroed alpha), p = z
     CK(launch_cg_update_r<T>(L.g, r, r, dinv<T>(L), z, sc + S_AL, s));
     CK(cudaMemcpyAsync(p, z, sizeof(T) * n_dofs(L.g), cudaMemcpyDeviceToDevice, s));
-    CK(launch_block_dots<T>(L.g, r, z, (const T*)nullptr, h->d_scratch, sc + S_RZ, s));
+    CK(launch_block_dots<T>(L.g, r, z, (const T*)nullptr, scratch, sc + S_RZ, s));
     for (int it = 0; it < steps; ++it) {
         CK(apply_level<T>(h, l, OP_APPLY_BLOCKDIAG, p, q, PHI_BITS_ALL));
-        CK(launch_block_dots<T>(L.g, p, q, (const T*)nullptr, h->d_scratch, sc + S_PQ, s));
+        CK(launch_block_dots<T>(L.g, p, q, (const T*)nullptr, scratch, sc + S_PQ, s));
         k_cg_alpha<<<1, 32, 0, s>>>(sc);
         CK(count_launch(cudaGetLastError()));
         CK(launch_cg_update_r<T>(L.g, r, q, dinv<T>(L), z, sc + S_AL, s));
-        CK(launch_block_dots<T>(L.g, r, z, (const T*)nullptr, h->d_scratch, sc + S_RZN, s));
+        CK(launch_block_dots<T>(L.g, r, z, (const T*)nullptr, scratch, sc + S_RZN, s));
         k_cg_beta<<<1, 32, 0, s>>>(sc, it);
         CK(count_launch(cudaGetLastError()));
         CK(launch_cg_update_p<T>(L.g, p, z, sc + S_BE, s));
@@ -311,14 +313,26 @@ cudaError_t setup(pff_hierarchy* h) {
     drop_graph(h);
     const bool f32 = h->prm.mg_precision == 32;
     double* d_eigs = h->d_scal + 512;   // 4 per level
+    // The levels' diagonals and eigenvalue estimates are independent (each level has its own
+    // vectors, diagonal, CG scalars and partial sums): fork one stream per level from the library
+    // stream and join them before the bounds are read.  The small levels' launch latencies then
+    // overlap the fine level's work.
+    CK(cudaEventRecord(h->lv_event[h->L], s));
     for (int l = 0; l < h->L; ++l) {
         Level& L = h->lv[l];
-        CK(diagonal_level<double>(h, l, L.dinv64));
-        CK(launch_invert_diag<double>(L.dinv64, n_dofs(L.g), s));
-        CK(launch_cast_f64_f32(L.dinv64, L.dinv32, n_dofs(L.g), s));
+        cudaStream_t ls = h->lv_stream[l];
+        CK(cudaStreamWaitEvent(ls, h->lv_event[h->L], 0));
+        h->stream = ls;   // every launch of this level's setup goes to its stream
+        cudaError_t e = diagonal_level<double>(h, l, L.dinv64);
+        if (e == cudaSuccess) e = launch_invert_diag<double>(L.dinv64, n_dofs(L.g), ls);
+        if (e == cudaSuccess) e = launch_cast_f64_f32(L.dinv64, L.dinv32, n_dofs(L.g), ls);
         // the coarsest level's bounds feed the FP64 coarse solver; the others the smoother
-        if (f32 && l > 0) CK(eigen_estimate<float>(h, l, d_eigs + 4 * l));
-        else CK(eigen_estimate<double>(h, l, d_eigs + 4 * l));
+        if (e == cudaSuccess) e = (f32 && l > 0) ? eigen_estimate<float>(h, l, d_eigs + 4 * l)
+                                                 : eigen_estimate<double>(h, l, d_eigs + 4 * l);
+        if (e == cudaSuccess) e = cudaEventRecord(h->lv_event[l], ls);
+        h->stream = s;
+        if (e != cudaSuccess) return e;
+        CK(cudaStreamWaitEvent(s, h->lv_event[l], 0));
     }
     std::vector<double> eig(4 * h->L);
     CK(cudaMemcpyAsync(eig.data(), d_eigs, sizeof(double) * 4 * h->L, cudaMemcpyDeviceToHost, s));
