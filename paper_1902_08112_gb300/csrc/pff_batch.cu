@@ -36,6 +36,7 @@ struct pff_batch {
     int* d_tiles = nullptr;                  // [(l * 2 + style) * (n + 1)], l = Lmax is the fine table
     std::vector<int> tot;                    // totals per (l, style)
     std::vector<int> blocks;                 // grid width per level (elementwise); blocks[Lmax] = fine
+    std::vector<int64_t> cells;              // cells per level over the valid instances
     double* d_part = nullptr;                // partial sums
     double* d_vals = nullptr;                // per-instance scalars
     double* d_coef = nullptr;                // Chebyshev tables (smoother and coarse)
@@ -106,6 +107,7 @@ cudaError_t upload(pff_batch* b) {
     std::vector<int> tiles((size_t)(b->Lmax + 1) * 2 * (n + 1), 0);
     b->tot.assign((size_t)(b->Lmax + 1) * 2, 0);
     b->blocks.assign(b->Lmax + 1, 1);
+    b->cells.assign(b->Lmax + 1, 0);
     for (int l = 0; l <= b->Lmax; ++l) {
         for (int i = 0; i < n; ++i) {
             pff_hierarchy* h = b->hs[i];
@@ -119,7 +121,10 @@ cudaError_t upload(pff_batch* b) {
                 const int t = d.valid ? q1_tiles(d.g, st == kStyleF64, st == kStyleF64) : 0;
                 pre[i + 1] = pre[i] + t;
             }
-            if (d.valid) b->blocks[l] = std::max(b->blocks[l], grid_w(n_dofs(d.g)));
+            if (d.valid) {
+                b->blocks[l] = std::max(b->blocks[l], grid_w(n_dofs(d.g)));
+                b->cells[l] += d.g.n_cells;
+            }
         }
         for (int st = 0; st < 2; ++st) b->tot[(size_t)l * 2 + st] = tiles[((size_t)l * 2 + st) * (n + 1) + n];
     }
@@ -137,14 +142,17 @@ const BLevel* tab(pff_batch* b, int l) { return l == b->Lmax ? b->d_fine : b->d_
 // y(sy) = G~ x(sx) on level l (l == Lmax: each instance's finest level), precision by fp64
 cudaError_t b_apply(pff_batch* b, int l, bool fp64, bool blockdiag, int sx, int sy, int phi_bits, bool preset = true) {
     const BLevel* L = tab(b, l);
-    const int st = fp64 ? kStyleF64 : kStyleF32;
+    // 3D levels of at least kCell64MinCells cells over the batch: the per-cell kernel with
+    // shared-memory derivatives, on the tiles of the FP32 per-cell style
+    const bool cell = b->dim == 3 && b->cells[l] >= kCell64MinCells && q1_cell_tiles_match_f32();
+    const int st = (fp64 && !cell) ? kStyleF64 : kStyleF32;
     if (preset) {
         if (fp64) BCK(bl_init_masked<double>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.0, b->stream));
         else BCK(bl_init_masked<float>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.f, b->stream));
     }
     return launch_q1_apply_batched(b->dim, fp64, blockdiag, fp64, L, b->n,
                                    b->d_tiles + ((size_t)l * 2 + st) * (b->n + 1), b->tot[(size_t)l * 2 + st], sx, sy,
-                                   phi_bits, b->stream);
+                                   phi_bits, b->stream, cell);
 }
 
 double* smooth_coef(pff_batch* b, int l, int step) { return b->d_coef + ((size_t)l * b->cheb_k + step) * b->n * 4; }

@@ -45,9 +45,12 @@ __device__ __forceinline__ T* bvec(const BLevel& L, int sel) {
 
 // batched Q1 applies: y(sy) = G~ x(sx) on every valid instance of a level (eliminated rows of y must
 // be preset); tile_start: prefix sums of the instances' tile counts for this kernel style
+// cell = true (3D): the per-cell kernel with shared-memory derivatives (tiles of the FP32 per-cell
+// style, q1_cell_tiles_match_f32())
 cudaError_t launch_q1_apply_batched(int dim, bool fp64, bool blockdiag, bool lanes, const BLevel* L, int n,
                                     const int* tile_start, int total_tiles, int sx, int sy, int phi_bits,
-                                    cudaStream_t s);
+                                    cudaStream_t s, bool cell = false);
+bool q1_cell_tiles_match_f32();
 // tile count of one instance for a kernel style (host)
 int q1_tiles(const Geom& g, bool fp64, bool lanes);
 

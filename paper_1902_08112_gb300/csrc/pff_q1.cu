@@ -1020,9 +1020,12 @@ __global__ void __launch_bounds__(256) k_q1_apply_lanes(Q1ApplyArgs<typename Sca
 // instruction fetch).  Arithmetic as in q1_apply_tile.
 struct CellTile { static constexpr int TX = 16, TY = 4, TZ = 2; };
 
+// The work of one CTA: tile (bx, by, bz) of the level; K: the Gauss-point scalings (kernel
+// parameters, or the instance's descriptor in a batched launch); cell_smem: the dynamic shared
+// memory of cell_smem_bytes<S>().
 template <typename S, bool BLOCKDIAG>
-__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 3 : 4)
-k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
+__device__ __forceinline__ void q1_cell_tile(const Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type>& a,
+                                             const Q1Consts& K, int bx, int by, int bz, unsigned char* cell_smem) {
     using T = CellTile;
     constexpr int NV = 8, NC = 4, NH = 4, NK = Q1Dims<3>::NK;
     constexpr int NCELL = T::TX * T::TY * T::TZ;
@@ -1032,14 +1035,13 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
 
     // dynamic shared memory (above the 48 KB static limit): nodal x, derivatives / flux sums
     // [(c * 3 + d) * 4 + class][cell], phi-row Gauss-point values [q][cell], node masks
-    extern __shared__ __align__(16) unsigned char cell_smem[];
     S* sx = reinterpret_cast<S*>(cell_smem);
     S* sgrad = sx + NC * NT;
     S* sfq = sgrad + 9 * NH * NCELL;
     uint8_t* smask = reinterpret_cast<uint8_t*>(sfq + NV * NCELL);
 
     const Geom& g = a.g;
-    const int ci0 = blockIdx.x * T::TX, cj0 = blockIdx.y * T::TY, ck0 = (blockIdx.z + a.tz0) * T::TZ;
+    const int ci0 = bx * T::TX, cj0 = by * T::TY, ck0 = bz * T::TZ;
     const int64_t nn = g.n_nodes;
     for (int t = threadIdx.x; t < NT; t += NCELL) {
         const int ti = t % NTX, tj = (t / NTX) % NTY, tk = t / (NTX * NTY);
@@ -1065,9 +1067,9 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
     const int tb = li + NTX * (lj + NTY * lk);
     auto tnode = [&](int n) { return tb + (n & 1) + NTX * (((n >> 1) & 1) + NTY * ((n >> 2) & 1)); };
     auto cls = [](int q, int d) { return (q & ((1 << d) - 1)) | ((q >> (d + 1)) << d); };   // q without bit d
-    auto cv = [&](int j) { return cpair<S>(a.k.cv[j]); };
-    auto cg = [&](int d, int j) { return cpair<S>(a.k.cg[d][j]); };
-    const S mu = cpair<S>(a.k.mu), lam = cpair<S>(a.k.lam);
+    auto cv = [&](int j) { return cpair<S>(K.cv[j]); };
+    auto cg = [&](int d, int j) { return cpair<S>(K.cg[d][j]); };
+    const S mu = cpair<S>(K.mu), lam = cpair<S>(K.lam);
 
     // displacement derivatives at the Gauss points -> shared memory
 #pragma unroll (sizeof(S) == 4 ? 3 : 1)
@@ -1192,12 +1194,19 @@ k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type
         S Y[NV];
         Y[0] = fq[0] * cv(0);
 #pragma unroll
-        for (int k = 1; k < NV; ++k) Y[k] = fq[k] * cv(popc(k)) + v[k] * cpair<S>(a.k.gk[k]);
+        for (int k = 1; k < NV; ++k) Y[k] = fq[k] * cv(popc(k)) + v[k] * cpair<S>(K.gk[k]);
         inv<3>(Y);
 #pragma unroll
         for (int n = 0; n < NV; ++n)
             if (!(smask[tnode(n)] & a.phi_bits)) atomicAdd(&a.y[3 * nn + gn0 + noff(n)], Scalar<S>::store(Y[n]));
     }
+}
+
+template <typename S, bool BLOCKDIAG>
+__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 3 : 4)
+k_q1_apply_cell(Q1ApplyArgs<typename Scalar<S>::storage, typename QData<S>::type> a) {
+    extern __shared__ __align__(16) unsigned char cell_smem[];
+    q1_cell_tile<S, BLOCKDIAG>(a, a.k, blockIdx.x, blockIdx.y, blockIdx.z + a.tz0, cell_smem);
 }
 
 // ---- batched: one launch over the tiles of all instances of a level
@@ -1260,10 +1269,75 @@ static void launch_b(const BLevel* L, const int* ts, int n, int total, int sx, i
     k_q1_apply_batched<DIM, S, BD, LANES><<<total, threads, 0, s>>>(L, ts, n, sx, sy, pb);
 }
 
+template <typename S>
+static constexpr size_t cell_smem_bytes() {
+    using T = CellTile;
+    constexpr int NCELL = T::TX * T::TY * T::TZ, NT = (T::TX + 1) * (T::TY + 1) * (T::TZ + 1);
+    return sizeof(S) * (4 * NT + 9 * 4 * NCELL + 8 * NCELL) + NT;
+}
+
+// Batched per-cell apply (3D): one launch over the 16x4x2-cell tiles of all instances of a level,
+// the instance found from the tile prefix; the tile work of k_q1_apply_cell with the instance's
+// Gauss-point scalings read from its descriptor.
+template <typename S, bool BLOCKDIAG>
+__global__ void __launch_bounds__(128, 4)
+k_q1_apply_batched_cell(const BLevel* __restrict__ L, const int* __restrict__ tile_start, int n, int sx, int sy,
+                        int phi_bits) {
+    int lo = 0, hi = n - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_start[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const BLevel& d = L[lo];
+    using St = typename Scalar<S>::storage;
+    using QT = typename QData<S>::type;
+    Q1ApplyArgs<St, QT> a;
+    a.g = d.g;
+    a.qd = sizeof(St) == 8 ? reinterpret_cast<const QT*>(d.qpd64) : reinterpret_cast<const QT*>(d.qpd32);
+    a.x = bvec<St>(d, sx);
+    a.y = bvec<St>(d, sy);
+    a.mask = d.mask;
+    a.phi_bits = phi_bits;
+    const int local = b - tile_start[lo];
+    const int tx = (d.g.nc[0] + CellTile::TX - 1) / CellTile::TX, ty = (d.g.nc[1] + CellTile::TY - 1) / CellTile::TY;
+    extern __shared__ __align__(16) unsigned char cell_smem[];
+    q1_cell_tile<S, BLOCKDIAG>(a, d.k, local % tx, (local / tx) % ty, local / (tx * ty), cell_smem);
+}
+
+template <typename S, bool BD>
+static cudaError_t launch_batched_cell(const BLevel* L, const int* ts, int n, int total, int sx, int sy, int pb,
+                                       cudaStream_t s) {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!(dev >= 0 && dev < 64 && done[dev])) {
+        e = cudaFuncSetAttribute(k_q1_apply_batched_cell<S, BD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cell_smem_bytes<S>());
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    k_q1_apply_batched_cell<S, BD><<<total, CellTile::TX * CellTile::TY * CellTile::TZ, cell_smem_bytes<S>(), s>>>(
+        L, ts, n, sx, sy, pb);
+    return count_launch(cudaGetLastError());
+}
+
+bool q1_cell_tiles_match_f32() {
+    return CellTile::TX == Q1Tile<3, float>::TX && CellTile::TY == Q1Tile<3, float>::TY &&
+           CellTile::TZ == Q1Tile<3, float>::TZ;
+}
+
 cudaError_t launch_q1_apply_batched(int dim, bool fp64, bool blockdiag, bool lanes, const BLevel* L, int n,
                                     const int* tile_start, int total_tiles, int sx, int sy, int phi_bits,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, bool cell) {
     if (total_tiles <= 0) return cudaSuccess;
+    if (cell && dim == 3) {
+        if (fp64) return blockdiag ? launch_batched_cell<df64, true>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s)
+                                   : launch_batched_cell<df64, false>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s);
+        return blockdiag ? launch_batched_cell<float, true>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s)
+                         : launch_batched_cell<float, false>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s);
+    }
 #define PFF_B(D, S, BD, LN) launch_b<D, S, BD, LN>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s)
     if (dim == 3) {
         if (fp64) {
@@ -1323,12 +1397,6 @@ static void fill_consts(Q1ApplyArgs<St, QT>& a, const Phys& ph) {
     a.k = make_q1_consts(a.g, ph);
 }
 
-template <typename S>
-static constexpr size_t cell_smem_bytes() {
-    using T = CellTile;
-    constexpr int NCELL = T::TX * T::TY * T::TZ, NT = (T::TX + 1) * (T::TY + 1) * (T::TZ + 1);
-    return sizeof(S) * (4 * NT + 9 * 4 * NCELL + 8 * NCELL) + NT;
-}
 // opt in to the dynamic shared memory of k_q1_apply_cell (once per instantiation and device)
 template <typename S, bool BD>
 static cudaError_t cell_prepare() {
