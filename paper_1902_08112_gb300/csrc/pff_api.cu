@@ -536,7 +536,7 @@ extern "C" pff_status pff_apply_jacobian_host(pff_hierarchy* h, int level, const
         CUDA_OR_FAIL(h, dalloc(h, &h->hy, (size_t)nmax));
     }
     const bool slabs = g.dim == 3 && g.deg == 1 && h->fast_q1 && !h->ph.split &&
-                       ((h->q1_style & 64) != 0 || ((h->q1_style & 16) != 0 && g.n_cells >= kCell64MinCells));
+                       ((h->q1_style & 64) != 0 || ((h->q1_style & 16) != 0 && g.n_cells >= kCellMinCells));
     if (!slabs) {
         CUDA_OR_FAIL(h, cudaMemcpyAsync(h->hx, x, nd * sizeof(double), cudaMemcpyHostToDevice, s));
         CUDA_OR_FAIL(h, apply_level<double>(h, l, OP_APPLY, h->hx, h->hy, PHI_BITS_ALL));

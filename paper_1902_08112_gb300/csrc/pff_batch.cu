@@ -142,9 +142,9 @@ const BLevel* tab(pff_batch* b, int l) { return l == b->Lmax ? b->d_fine : b->d_
 // y(sy) = G~ x(sx) on level l (l == Lmax: each instance's finest level), precision by fp64
 cudaError_t b_apply(pff_batch* b, int l, bool fp64, bool blockdiag, int sx, int sy, int phi_bits, bool preset = true) {
     const BLevel* L = tab(b, l);
-    // 3D levels of at least kCell64MinCells cells over the batch: the per-cell kernel with
+    // 3D levels of at least kCellMinCells cells over the batch: the per-cell kernel with
     // shared-memory derivatives, on the tiles of the FP32 per-cell style
-    const bool cell = b->dim == 3 && b->cells[l] >= kCell64MinCells && q1_cell_tiles_match_f32();
+    const bool cell = b->dim == 3 && b->cells[l] >= kCellMinCells && q1_cell_tiles_match_f32();
     const int st = (fp64 && !cell) ? kStyleF64 : kStyleF32;
     if (preset) {
         if (fp64) BCK(bl_init_masked<double>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.0, b->stream));

@@ -194,7 +194,7 @@ constexpr int kLevelScal = 256, kLevelScratch = 1024;
 
 // Smallest 3D level that the per-cell applies with shared-memory derivatives serve by default: below
 // about two waves of their CTAs the lane and per-cell-gather kernels finish sooner.
-constexpr int64_t kCell64MinCells = 100000;
+constexpr int64_t kCellMinCells = 100000;
 
 struct pff_hierarchy {
     pff_mesh mesh;
@@ -229,7 +229,7 @@ struct pff_hierarchy {
     bool fast_q1 = true;             // Q1 levels use the linearisation-data kernels of pff_q1.cu
     int q1_style = 52;               // bit 0/1: lanes for FP64/FP32; bit 2/3: lanes with global atomics for FP64/FP32;
                                      // bit 4/6 (FP64), 5/7 (FP32): per cell with shared-memory derivatives and
-                                     // global atomics on 3D levels of at least kCell64MinCells cells / on every
+                                     // global atomics on 3D levels of at least kCellMinCells cells / on every
                                      // 3D level
     bool use_graphs = true;          // replay the V-cycle body from a captured CUDA graph
     cudaGraphExec_t vgraph = nullptr;   // captured V-cycle body (valid until the next setup)

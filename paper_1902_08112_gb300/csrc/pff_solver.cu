@@ -72,12 +72,12 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
             CK(launch_q1_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd,
                                  (h->q1_style & 1) != 0, h->stream, (h->q1_style & 4) != 0,
                                  (h->q1_style & 64) != 0 ||
-                                     ((h->q1_style & 16) != 0 && L.g.n_cells >= kCell64MinCells)));
+                                     ((h->q1_style & 16) != 0 && L.g.n_cells >= kCellMinCells)));
         else
             CK(launch_q1_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd,
                                  (h->q1_style & 2) != 0, h->stream, (h->q1_style & 8) != 0,
                                  (h->q1_style & 128) != 0 ||
-                                     ((h->q1_style & 32) != 0 && L.g.n_cells >= kCell64MinCells)));
+                                     ((h->q1_style & 32) != 0 && L.g.n_cells >= kCellMinCells)));
     } else {
         CellArgs<T> a;
         a.g = L.g;
