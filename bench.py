@@ -40,8 +40,8 @@ def _peaks():
 
 
 # DRAM bytes per cell of the FP64-accurate apply k_q1_apply_cell<df64, false> from one ncu capture at
-# 64^3 (157.2 MB per launch over 262,144 cells): the df64 Gauss-point data plus x, mask and y
-TRAFFIC_DF64_PER_CELL = 157.190912e6 / 262144
+# 64^3 (157.5 MB per launch over 262,144 cells): the df64 Gauss-point data plus x, mask and y
+TRAFFIC_DF64_PER_CELL = 157.498368e6 / 262144
 # Algorithmic work of that kernel per cell, counted from its operations: 572 double-float adds
 # (8 FP32 flops each: TwoSum and two low-part adds) and 223 double-float multiplies (7 flops:
 # product and three fused multiply-adds).  Displacement transforms 144 adds + 36 multiplies, phi
