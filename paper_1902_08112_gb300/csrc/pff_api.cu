@@ -114,9 +114,24 @@ static const char* check_params(const pff_params* p) {
     return nullptr;
 }
 
+// Device memory, the library-owned streams and the events of a hierarchy (also on the error
+// paths of pff_create_hierarchy, where some of them may not exist yet).
 static void free_all(pff_hierarchy* h) {
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
+    for (cudaStream_t& st : h->lv_stream) {
+        if (st) cudaStreamDestroy(st);
+        st = nullptr;
+    }
+    for (cudaEvent_t& e : h->lv_event) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    for (cudaEvent_t e : h->slab_ev) cudaEventDestroy(e);
+    h->slab_ev.clear();
+    if (h->cs_in) cudaStreamDestroy(h->cs_in);
+    if (h->cs_out) cudaStreamDestroy(h->cs_out);
+    h->cs_in = h->cs_out = nullptr;
 }
 
 template <typename T>
@@ -289,13 +304,6 @@ extern "C" pff_status pff_destroy_hierarchy(pff_hierarchy* h) {
     cudaStreamSynchronize(h->stream);
     drop_graph(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    for (cudaEvent_t e : h->slab_ev) cudaEventDestroy(e);
-    for (cudaStream_t st : h->lv_stream)
-        if (st) cudaStreamDestroy(st);
-    for (cudaEvent_t e : h->lv_event)
-        if (e) cudaEventDestroy(e);
-    if (h->cs_in) cudaStreamDestroy(h->cs_in);
-    if (h->cs_out) cudaStreamDestroy(h->cs_out);
     free_all(h);
     delete h;
     return PFF_OK;
