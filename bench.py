@@ -82,26 +82,34 @@ def job_gdofs(ws, n_dofs, apply_ms):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling (every 50 ms, timestamped).  Start it before the warm-up
+    so that it is sampling when the timed region opens; mark() records the region's host times and
+    summary() keeps the samples inside it."""
 
-    def __init__(self, index: int):
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, path: str | None = None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.window = None
+        self.path = path or os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}",
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", f"--id={self.index}", "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
+
+    def mark(self, t0: float, t1: float):
+        """Host wall-clock bounds (time.time()) of the timed region."""
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc:
@@ -112,22 +120,34 @@ class ClockSampler:
                 self.proc.kill()
             self.fh.close()
 
-    def summary(self):
-        if not self.proc:
+    def summary(self, running: bool = True):
+        if running and not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
         rows = []
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
-            if len(p) >= 9:
-                rows.append(p)
-        if not rows:
+            if len(p) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, p[1:]))
+        inside = rows
+        if self.window and rows:
+            lo, hi = self.window[0] - 0.05, self.window[1] + 0.05
+            sel = [r for r in rows if r[0] is not None and lo <= r[0] <= hi]
+            inside = sel if sel else rows
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        vals = [r[1] for r in inside]
+        sm = [float(v[1]) for v in vals if v[1].replace(".", "").isdigit()]
+        mx = [float(v[2]) for v in vals if v[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for v in vals for i in range(4) if v[5 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(vals)}
 
 
 def cpu_baseline(n: int = 24, seconds: float = 3.0):
@@ -468,24 +488,27 @@ def main():
         li = pff.load_step(h, U, phi2, p4, max_newton=1, allow_noconv=True)
         return li.last
 
-    for _ in range(args.warmup):
-        step()
-    stream.synchronize()
-    barrier()
-    pff.profile(h, True)
-    launches0 = pff.launch_count()
     infos = []
+    # the clock sampler runs from the warm-up on, so it is sampling when the timed region opens
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        barrier()
+        pff.profile(h, True)
+        launches0 = pff.launch_count()
         barrier()
         torch.cuda.synchronize(dev)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         _nvtx("timed_steps", True)
+        t_wall0 = time.time()
         ev0.record(stream)
         for _ in range(args.steps):
             infos.append(step())
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark(t_wall0, time.time())
         _nvtx("timed_steps", False)
         barrier()
     launches = pff.launch_count() - launches0
