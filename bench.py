@@ -21,6 +21,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -94,7 +95,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.window = None
-        self.path = path or os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"pff_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -3,7 +3,7 @@
 All calls go through the C ABI (paper_1902_08112_gb300.pff).  Inputs come from the seeded
 generators of paper_1902_08112_gb300.workloads; expected values from oracle/ only.
 
-Tolerances: FP64 operators 1e-12 relative (normwise, the spec bar); FP32 operators 2e-5
+Tolerances: FP64 operators 1e-12 relative (normwise, the required parity); FP32 operators 2e-5
 (FP32 unit roundoff 6e-8 times the ~100-term sums of a cell evaluation, with margin); solver
 pieces built on the FP64 operators 1e-9 (eigenvalue estimates enter through Chebyshev
 coefficients; 10 CG steps amplify rounding).

@@ -1,5 +1,5 @@
 """GPU solver parity against the oracle: FGMRES + V-cycle iteration counts (within 10%, the
-spec bar; +-1 allowed for the FP32 V-cycle whose smoother runs in FP32), true residual
+required parity; +-1 allowed for the FP32 V-cycle whose smoother runs in FP32), true residual
 at 1e-8, one active-set step of Algorithm 1 (same active set, same residual norm, solution
 satisfying the oracle's eliminated system), and sampled full-size apply parity."""
 import math
