@@ -165,7 +165,8 @@ def test_fgmres_mg_matches_dense_solve(dim, n, levels, deg):
 
 def test_mg_iterations_bounded_under_refinement():
     """h-robustness of the monolithic MG preconditioner (Sec. 5: iteration counts insensitive
-    to refinement); 2D single crack, FGMRES to 1e-8."""
+    to refinement); 2D single crack, FGMRES to 1e-8.  The counts also lie in the range the paper
+    reports per linear solve for its examples (about 2-7 in 2D and 4-10 in 3D, Sec. 5.3)."""
     counts = []
     for n, L in ((16, 2), (32, 3), (64, 4)):
         w = W.small(W.config_2d_single_crack(), n, L)
@@ -183,7 +184,7 @@ def test_mg_iterations_bounded_under_refinement():
                                              lambda v: mg.precondition(lv, v, mg.MGParams()), rtol=1e-8)
         assert res <= 1e-8 * res0 * 1.0001
         counts.append(its)
-    assert max(counts) <= 25
+    assert 2 <= min(counts) and max(counts) <= 10
     assert counts[-1] <= 2 * counts[0] + 2
 
 
