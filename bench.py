@@ -586,31 +586,40 @@ def main():
     torch.cuda.synchronize()   # x32 is written on torch's stream, read on the library's
     ms32_fine = timed(lambda: pff.apply_jacobian_f32(h, -1, x32, y32), reps=10)
 
-    # ---- rooflines.  The applies are arithmetic-bound on GB300: the FP64-accurate apply runs as
-    # double-float on the FP32 pipes.  Peak = FP32 pipe from unit counts and the max clock:
-    # 152 SMs x 128 lanes x 2 flops x 2.07 GHz.  Algorithmic FP32 flops per cell of the
-    # double-float per-cell apply: 572 adds x 8 + 223 multiplies x 7 = 6137; the FP32 per-cell
-    # apply runs the same operations in FP32: 572 + 223 = 795.
+    # ---- rooflines.  Headline: the FP64-accurate fine apply against HBM with the algorithmic bytes
+    # of the on-the-fly linearisation (x, U, phi~, y and the mask: 105 B per node in 3D), over the
+    # measured copy bandwidth.  Secondary: its arithmetic, which is what bounds it on GB300 -- the
+    # FP64-accurate apply runs as double-float on the FP32 pipes -- over the FP32 FMA rate measured
+    # by pff_fp32_fma_tflops.  Algorithmic FP32 flops per cell of the double-float per-cell apply:
+    # 572 adds x 8 + 223 multiplies x 7 = 6137; the FP32 per-cell apply runs the same operations in
+    # FP32: 572 + 223 = 795.
     classes = {"apply64_fine": (cnt64, ms64), "apply64_coarse": (cnt64c, ms64c), "apply32": (cnt32, ms32),
                "vcycle_graph": (cntv, msv)}
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    try:
+        fp32_peak = pff.fp32_fma_tflops(stream)
+        fp32_note = "peak: FP32 FMA rate measured on this GPU by pff_fp32_fma_tflops"
+    except pff.PffError:
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        fp32_note = "peak: FP32 pipe derived from unit counts (152 SMs x 128 lanes x 2 flops x 2.07 GHz)"
     cells = w.n_cells_total
     fl64 = (8.0 * DF64_ADDS_PER_CELL + 7.0 * DF64_MULS_PER_CELL) * cells
     fl32 = float(DF64_ADDS_PER_CELL + DF64_MULS_PER_CELL) * cells
+    bytes64 = 105.0 * nn
+    gbs64 = bytes64 / (apply_ms * 1e-3) / 1e9
     roof = {"kernel": "k_q1_apply_cell<df64, false> (FP64-accurate fine-level Jacobian apply)",
-            "bound": "alu", "achieved": fl64 / (apply_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+            "bound": "hbm", "achieved": gbs64, "peak": hbm, "unit": "GB/s", "frac": gbs64 / hbm,
+            "peak_note": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+            "algorithmic_bytes_per_launch": bytes64,
+            "bytes_note": "105 B per node: x, U (4 x 8 B each), phi~ and y (8 B, 32 B) and the 1-byte mask",
             "traffic": TRAFFIC_DF64_PER_CELL * cells if TRAFFIC_DF64_PER_CELL else None,
-            "algorithmic_flops_per_launch": fl64,
             "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 64^3 "
                             "(%.1f MB), scaled by cells" % (TRAFFIC_DF64_PER_CELL * 262144 / 1e6),
-            "note": "peak: FP32 pipe derived from unit counts and 2.07 GHz; double-float arithmetic on FP32 pipes",
-            "hbm": {"achieved": 105.0 * nn / (apply_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                    "frac": 105.0 * nn / (apply_ms * 1e-3) / 1e9 / hbm,
-                    "algorithmic_bytes_per_launch": 105.0 * nn, "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "alu": {"achieved": fl64 / (apply_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": fl64 / (apply_ms * 1e-3) / 1e12 / fp32_peak, "algorithmic_flops_per_launch": fl64,
+                    "note": fp32_note + "; double-float arithmetic on the FP32 pipes (the kernel's bound)"},
             "fp64_equivalent_tflops": (DF64_ADDS_PER_CELL + DF64_MULS_PER_CELL) * cells / (apply_ms * 1e-3) / 1e12}
-    roof["frac"] = roof["achieved"] / roof["peak"]
     roof32 = {"kernel": "k_q1_apply_cell<float, false> (FP32 fine-level V-cycle operator)", "ms": ms32_fine,
               "bound": "alu", "achieved": fl32 / (ms32_fine * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
               "frac": fl32 / (ms32_fine * 1e-3) / 1e12 / fp32_peak,
@@ -618,7 +627,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+        "dtype_note": "double-float (pairs of FP32) arithmetic, FP64 vectors in memory; matches the FP64 "
+                      "oracle's assembled product to 1e-12 relative",
         "config": {"workload": f"3d_penny_q1_{args.n}", "n_dofs": nd, "levels": w.n_levels,
                    "step": "one active-set Newton step (FP32 V-cycle in FP64 FGMRES to 1e-8)",
                    "state": "U^3 after load steps p_n = n p / 3, n = 1..3; the step is the first of load step 4",

@@ -58,8 +58,10 @@ enum {
  * n_cells[a] must be divisible by 2^(n_levels-1)).
  * dirichlet_faces: bit 2a clamps all displacement components on the lower face of axis a,
  * bit 2a+1 on the upper face (0x3F = every face, the pressurised-crack setting of Sec. 2.1).
- * dirichlet_mask: optional HOST array of fine-level node masks (PFF_MASK_U* bits) OR-ed into
- * the face mask; NULL for none.  Coarse levels inherit masks from the coincident fine nodes.
+ * dirichlet_mask: optional HOST array of fine-level node masks (PFF_MASK_U* and PFF_MASK_PHI_DIR
+ * bits) OR-ed into the face mask; NULL for none.  A PFF_MASK_PHI_DIR node keeps the phase-field
+ * value of the state (it is eliminated like an active node but never enters the active set).
+ * Coarse levels inherit masks from the coincident fine nodes.
  * cell_mask: optional HOST array of fine-level cells (x fastest), nonzero = in the domain, for
  * domains cut from the box such as the L-shaped panels of Sec. 5.2/5.3; NULL = the whole box.
  * Cells outside contribute nothing; nodes on no cell of the domain are fixed in every component
@@ -336,6 +338,17 @@ pff_status pff_batch_gmres_solve(pff_batch* b, const double* const* rhs, double*
 /* One active-set step (Algorithm 1) of every instance at U_i (host array of n device pointers,
  * updated in place), the linear solves batched.  infos: host array of n entries or NULL. */
 pff_status pff_batch_newton_step(pff_batch* b, double* const* U, pff_newton_info* infos);
+/* y_i = G~_i x_i on one level of every instance (Sec. 4.1), batched: level -1 = each instance's finest
+ * level, level l >= 0 = the instance's level l (0 = coarsest; instances with fewer levels are
+ * skipped and their y left untouched).  precision 64: FP64-accurate operators, x/y double*;
+ * 32: FP32 operators, x/y float*.  x, y: host arrays of n device pointers (n_dofs of the
+ * instance's level each).  Errors: PFF_EINVAL, PFF_ESTATE (an instance without state). */
+pff_status pff_batch_apply_jacobian(pff_batch* b, int level, int precision, const void* const* x, void* const* y);
+/* Kernel family of the batched level operators: 0 (default) = chosen per level (3D levels whose
+ * cells over the batch reach 100,000 run the per-cell kernels with shared-memory derivatives, smaller
+ * levels the Gauss-point-lane FP64-accurate and per-cell-gather FP32 kernels), 1 = the small-level
+ * kernels on every level, 2 = the per-cell kernels on every 3D level.  Errors: PFF_EINVAL. */
+pff_status pff_batch_set_kernel_style(pff_batch* b, int style);
 const char* pff_batch_last_error(const pff_batch* b);
 
 /* Kernel timing (tracing).  pff_profile(h, 1) clears the counters and starts recording CUDA
@@ -355,23 +368,36 @@ pff_status pff_profile_read(pff_hierarchy* h, int cls, int* count, double* total
  * example a process whose GPU memory belongs to another allocator, or code that may not call
  * cudaMalloc and so cannot create a hierarchy).  The paper has no counterpart: this is the
  * decision of pff_update_active_set (Algorithm 1, step 3: active iff
- * R_i / M_ii + c (phi_i - phi_old_i) > tol_as with the Gauss-Lobatto lumped mass M) on caller
- * buffers, without a hierarchy and without any device allocation.
+ * R_i / M_ii + c (phi_i - phi_old_i) > tol_as with the Gauss-Lobatto lumped mass M; nodes whose
+ * phi is prescribed -- PFF_MASK_PHI_DIR set, or on no cell of the domain -- are never active) on
+ * caller buffers, without a hierarchy and without any device allocation.
  *   mesh     the fine mesh (dim, degree, n_cells, lo, hi are used; n_levels is ignored).
  *   params   c_as and tol_as are used.
+ *   cell_mask  device uint8, n_cells, nonzero = in the domain, or NULL for the whole box.  The
+ *            lumped mass of a node sums over its domain cells only, as the hierarchy's does.
+ *            mesh->cell_mask is a HOST array this call cannot read: a mesh that has one needs
+ *            the same cells passed here (PFF_EINVAL otherwise).
  *   R        device FP64, n_dofs: the residual -A(U), e.g. from pff_residual.
  *   U        device FP64, n_dofs: the state [u | phi].   phi_old: device FP64, n_nodes.
- *   mask     device uint8, n_nodes, in/out: PFF_MASK_ACTIVE is rewritten, other bits kept.
+ *   mask     device uint8, n_nodes, in/out: PFF_MASK_ACTIVE is rewritten, other bits kept
+ *            (PFF_MASK_PHI_DIR is read, e.g. the fine mask from pff_level_state).
  *   n_active, n_changed  host outputs (may be NULL); the call synchronises cuda_stream.
  * Scratch: a file-scope device array of 2 * 65536 + 2 ints (about 512 KB) that every GPU which
  * loads the library holds until the process exits; meshes with more than 65536 * 1024 nodes
  * are rejected with PFF_EINVAL.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream
  * capture.  All calls share the array, so calls that overlap on the GPU race.
- * Errors: PFF_EINVAL (NULL, bad mesh, too many nodes), PFF_ECUDA. */
-pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_params* params, const double* R,
-                                  const double* U, const double* phi_old, uint8_t* mask, int* n_active,
-                                  int* n_changed, void* cuda_stream);
+ * Errors: PFF_EINVAL (NULL, bad mesh, host-only cell mask, too many nodes), PFF_ECUDA. */
+pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_params* params, const uint8_t* cell_mask,
+                                  const double* R, const double* U, const double* phi_old, uint8_t* mask,
+                                  int* n_active, int* n_changed, void* cuda_stream);
+
+/* Measured FP32 fused-multiply-add rate of the current GPU in TFLOP/s (2 flops per FMA), the
+ * denominator of the arithmetic roofline of the double-float operators, which run on the FP32 pipes
+ * (the paper measures on CPUs and gives no counterpart).  Runs a register-only FMA kernel three
+ * times on cuda_stream after a warm-up and reports the fastest; allocates and frees one small
+ * device buffer; synchronises.  Errors: PFF_EINVAL (NULL), PFF_ENOMEM, PFF_ECUDA. */
+pff_status pff_fp32_fma_tflops(void* cuda_stream, double* tflops);
 
 /* Number of kernel launches this library has issued in the process so far (tracing). */
 long long pff_launch_count(void);

@@ -43,6 +43,7 @@ struct pff_batch {
     uint64_t* d_seeds = nullptr;
     int cheb_k = 4, coarse_k = 1;
     bool mg64 = false;                       // FP64 V-cycle (mg_precision 64 in every instance)
+    int style = 0;                           // level-operator kernels: 0 by level size, 1 small-level, 2 per-cell
     bool stale = true;
     std::vector<void*> allocs;
     std::string err;
@@ -144,7 +145,8 @@ cudaError_t b_apply(pff_batch* b, int l, bool fp64, bool blockdiag, int sx, int 
     const BLevel* L = tab(b, l);
     // 3D levels of at least kCellMinCells cells over the batch: the per-cell kernel with
     // shared-memory derivatives, on the tiles of the FP32 per-cell style
-    const bool cell = b->dim == 3 && b->cells[l] >= kCellMinCells && q1_cell_tiles_match_f32();
+    const bool cell = b->dim == 3 && q1_cell_tiles_match_f32() &&
+                      (b->style == 2 || (b->style == 0 && b->cells[l] >= kCellMinCells));
     const int st = (fp64 && !cell) ? kStyleF64 : kStyleF32;
     if (preset) {
         if (fp64) BCK(bl_init_masked<double>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.0, b->stream));
@@ -800,6 +802,45 @@ extern "C" pff_status pff_batch_newton_step(pff_batch* b, double* const* U, pff_
     }
     BCUDA_OR_FAIL(b, cudaStreamSynchronize(b->stream));
     return st;
+}
+
+extern "C" pff_status pff_batch_set_kernel_style(pff_batch* b, int style) {
+    if (!b) return PFF_EINVAL;
+    if (style < 0 || style > 2) return b_fail(b, PFF_EINVAL, "kernel style must be 0, 1 or 2");
+    b->style = style;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_batch_apply_jacobian(pff_batch* b, int level, int precision, const void* const* x,
+                                               void* const* y) {
+    if (!b || !x || !y) return PFF_EINVAL;
+    if (precision != 32 && precision != 64) return b_fail(b, PFF_EINVAL, "precision must be 32 or 64");
+    if (level < -1 || level >= b->Lmax) return b_fail(b, PFF_EINVAL, "level out of range");
+    for (auto* h : b->hs)
+        if (!h->has_state) return b_fail(b, PFF_ESTATE, "batch apply before pff_set_state of every instance");
+    for (auto* h : b->hs) BCUDA_OR_FAIL(b, refresh_state(h));
+    const int l = level < 0 ? b->Lmax : level;
+    const size_t es = precision == 64 ? sizeof(double) : sizeof(float);
+    const int W = precision == 64 ? BV_W64 : BV_W32;
+    b->valid.assign(b->n, 1);
+    BCUDA_OR_FAIL(b, upload(b));
+    auto vec_of = [&](int i, int k) -> std::pair<void*, size_t> {
+        pff_hierarchy* h = b->hs[i];
+        const int li = level < 0 ? h->L - 1 : level;
+        if (li >= h->L) return {nullptr, 0};
+        Level& L = h->lv[li];
+        return {L.w[precision == 64 ? 1 : 0][k], (size_t)n_dofs(L.g) * es};
+    };
+    for (int i = 0; i < b->n; ++i) {
+        auto v = vec_of(i, 3);
+        if (v.first) BCUDA_OR_FAIL(b, cudaMemcpyAsync(v.first, x[i], v.second, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    BCUDA_OR_FAIL(b, b_apply(b, l, precision == 64, false, bsel(W + 3), bsel(W + 4), PHI_BITS_ALL));
+    for (int i = 0; i < b->n; ++i) {
+        auto v = vec_of(i, 4);
+        if (v.first) BCUDA_OR_FAIL(b, cudaMemcpyAsync(y[i], v.first, v.second, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    return PFF_OK;
 }
 
 extern "C" const char* pff_batch_last_error(const pff_batch* b) { return b ? b->err.c_str() : "null batch"; }

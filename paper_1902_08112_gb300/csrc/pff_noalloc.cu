@@ -24,39 +24,54 @@ static __device__ __align__(256) int g_noalloc_counts[2 * kNoAllocMaxCtas + 2];
 std::mutex g_noalloc_mutex;
 int* g_noalloc_ptr[128] = {nullptr};   // device address of the array, per device ordinal
 
-// Gauss-Lobatto lumped mass of one node on a uniform tensor grid (Q1: h/2 per adjacent cell;
-// Q2: h/6 at cell vertices, 2h/3 at midpoints), the same product as the library's
-// lumped-mass kernel.
-__device__ __forceinline__ double lumped_mass_node(const pff::Geom& g, int64_t n) {
+// Gauss-Lobatto lumped mass of one node on a uniform tensor grid: the sum over the node's cells in
+// the domain (cm == nullptr: every cell) of the cell's tensor weight (Q1: h/2 per axis; Q2: h/6 at
+// cell vertices, 2h/3 at midpoints), in the summation order of the library's lumped-mass kernel so
+// that both give the same bits.  0 for a node on no domain cell.
+__device__ __forceinline__ double lumped_mass_node(const pff::Geom& g, const uint8_t* __restrict__ cm, int64_t n) {
     int idx[3];
     idx[0] = (int)(n % g.nn[0]);
     const int64_t r = n / g.nn[0];
     idx[1] = (int)(r % g.nn[1]);
     idx[2] = (int)(r / g.nn[1]);
-    double w = 1.0;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (int a = 0; a < g.dim; ++a) {
-        const int i = idx[a], last = g.nn[a] - 1;
-        double wa;
-        if (g.deg == 1) wa = (i == 0 || i == last) ? 0.5 : 1.0;
-        else if (i % 2 == 1) wa = 2.0 / 3.0;
-        else wa = (i == 0 || i == last) ? 1.0 / 6.0 : 2.0 / 6.0;
-        w *= wa * g.h[a];
+        lo[a] = idx[a] >= g.deg ? (idx[a] - 1) / g.deg : 0;
+        hi[a] = min(g.nc[a] - 1, idx[a] / g.deg);
     }
+    double w = 0.0;
+    for (int ck = lo[2]; ck <= hi[2]; ++ck)
+        for (int cj = lo[1]; cj <= hi[1]; ++cj)
+            for (int ci = lo[0]; ci <= hi[0]; ++ci) {
+                const int64_t cell = (int64_t)ci + (int64_t)g.nc[0] * ((int64_t)cj + (int64_t)g.nc[1] * ck);
+                if (cm && cm[cell] == 0) continue;
+                const int c3[3] = {ci, cj, ck};
+                double wc = 1.0;
+                for (int a = 0; a < g.dim; ++a) {
+                    const int loc = idx[a] - g.deg * c3[a];
+                    const double wa = g.deg == 1 ? 0.5 : (loc == 1 ? 2.0 / 3.0 : 1.0 / 6.0);
+                    wc *= wa * g.h[a];
+                }
+                w += wc;
+            }
     return w;
 }
 
-__global__ void k_active_set_noalloc(pff::Geom g, const double* __restrict__ R, const double* __restrict__ U,
-                                     const double* __restrict__ phi_old, double c, double thr,
-                                     uint8_t* __restrict__ mask, int* __restrict__ counts) {
+__global__ void k_active_set_noalloc(pff::Geom g, const uint8_t* __restrict__ cm, const double* __restrict__ R,
+                                     const double* __restrict__ U, const double* __restrict__ phi_old, double c,
+                                     double thr, uint8_t* __restrict__ mask, int* __restrict__ counts) {
     const int64_t nn = g.n_nodes;
     const int64_t base = (int64_t)blockIdx.x * kNoAllocNodesPerCta;
     int na = 0, nch = 0;
     for (int k = threadIdx.x; k < kNoAllocNodesPerCta; k += blockDim.x) {
         const int64_t n = base + k;
         if (n >= nn) break;
-        const double lam = R[g.dim * nn + n] / lumped_mass_node(g, n);
-        const bool act = lam + c * (U[g.dim * nn + n] - phi_old[n]) > thr;
         const uint8_t m = mask[n];
+        // prescribed phi (phi Dirichlet bit, nodes on no domain cell) never enters the active set
+        const double M = lumped_mass_node(g, cm, n);
+        const bool fixed = (m & PFF_MASK_PHI_DIR) != 0 || !(M > 0.0);
+        const double lam = fixed ? 0.0 : R[g.dim * nn + n] / M;
+        const bool act = !fixed && lam + c * (U[g.dim * nn + n] - phi_old[n]) > thr;
         const bool was = (m & PFF_MASK_ACTIVE) != 0;
         mask[n] = (uint8_t)((m & ~PFF_MASK_ACTIVE) | (act ? PFF_MASK_ACTIVE : 0));
         na += act;
@@ -96,10 +111,13 @@ __global__ void k_sum_counts_noalloc(int* __restrict__ counts, int nctas) {
 
 }  // namespace
 
-extern "C" pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_params* params, const double* R,
-                                             const double* U, const double* phi_old, uint8_t* mask, int* n_active,
-                                             int* n_changed, void* cuda_stream) {
+extern "C" pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_params* params, const uint8_t* cell_mask,
+                                             const double* R, const double* U, const double* phi_old, uint8_t* mask,
+                                             int* n_active, int* n_changed, void* cuda_stream) {
     if (!mesh || !params || !R || !U || !phi_old || !mask) return PFF_EINVAL;
+    // a cut domain needs its cell mask in device memory: the host copy in the mesh cannot be read
+    // by the kernel, and copying it would need a device allocation
+    if (mesh->cell_mask && !cell_mask) return PFF_EINVAL;
     if (mesh->dim != 2 && mesh->dim != 3) return PFF_EINVAL;
     if (mesh->degree != 1 && mesh->degree != 2) return PFF_EINVAL;
     pff::Geom g;
@@ -139,7 +157,7 @@ extern "C" pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_par
         counts = g_noalloc_ptr[dev];
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-    k_active_set_noalloc<<<(unsigned)nctas, kNoAllocThreads, 0, s>>>(g, R, U, phi_old, params->c_as,
+    k_active_set_noalloc<<<(unsigned)nctas, kNoAllocThreads, 0, s>>>(g, cell_mask, R, U, phi_old, params->c_as,
                                                                       params->tol_as, mask, counts);
     if (cudaGetLastError() != cudaSuccess) return PFF_ECUDA;
     k_sum_counts_noalloc<<<1, kNoAllocThreads, 0, s>>>(counts, (int)nctas);

@@ -83,7 +83,7 @@ __global__ void k_face_mask(Geom g, unsigned faces, const uint8_t* __restrict__ 
             if ((faces >> (2 * a + 1)) & 1u) on |= idx[a] == g.nn[a] - 1;
         }
         uint8_t m = on ? ubits : 0;
-        if (extra) m |= (uint8_t)(extra[n] & ubits);
+        if (extra) m |= (uint8_t)(extra[n] & (ubits | PFF_MASK_PHI_DIR));
         mask[n] = m;
     }
 }

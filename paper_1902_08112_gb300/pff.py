@@ -88,7 +88,7 @@ SIGNATURES = {
     "pff_load_step": (_I, [_VP, _VP, _VP, _D, _I, ctypes.POINTER(LoadInfo)]),
     "pff_profile": (_I, [_VP, _I]),
     "pff_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
-    "pff_active_set_noalloc": (_I, [ctypes.POINTER(Mesh), ctypes.POINTER(Params), _VP, _VP, _VP, _VP,
+    "pff_active_set_noalloc": (_I, [ctypes.POINTER(Mesh), ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _VP]),
     "pff_batch_create": (_I, [_I, ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)]),
     "pff_batch_destroy": (_I, [_VP]),
@@ -96,7 +96,10 @@ SIGNATURES = {
     "pff_batch_vcycle": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "pff_batch_gmres_solve": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _I, ctypes.POINTER(SolveInfo)]),
     "pff_batch_newton_step": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(NewtonInfo)]),
+    "pff_batch_apply_jacobian": (_I, [_VP, _I, _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "pff_batch_set_kernel_style": (_I, [_VP, _I]),
     "pff_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "pff_fp32_fma_tflops": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pff_launch_count": (ctypes.c_longlong, []),
     "pff_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -156,8 +159,10 @@ def default_params(**kw) -> Params:
     return p
 
 
-def make_mesh(dim, degree, n_cells, n_levels, lo, hi, dirichlet_faces=0x3F, cell_mask=None) -> Mesh:
-    """cell_mask: optional host uint8 array of the finest level's cells (x fastest), 1 = in the domain."""
+def make_mesh(dim, degree, n_cells, n_levels, lo, hi, dirichlet_faces=0x3F, cell_mask=None,
+              dirichlet_mask=None) -> Mesh:
+    """cell_mask: optional host uint8 array of the finest level's cells (x fastest), 1 = in the domain.
+    dirichlet_mask: optional host uint8 array of the finest level's nodes (MASK_U* / MASK_PHI_DIR bits)."""
     m = Mesh()
     m.dim, m.degree, m.n_levels = dim, degree, n_levels
     for a in range(3):
@@ -172,6 +177,11 @@ def make_mesh(dim, degree, n_cells, n_levels, lo, hi, dirichlet_faces=0x3F, cell
         arr = np.ascontiguousarray(cell_mask, dtype=np.uint8)
         m._cell_mask_keep = arr          # the library copies it during pff_create_hierarchy
         m.cell_mask = arr.ctypes.data
+    if dirichlet_mask is not None:
+        import numpy as np
+        arr = np.ascontiguousarray(dirichlet_mask, dtype=np.uint8)
+        m._dirichlet_mask_keep = arr     # copied during pff_create_hierarchy
+        m.dirichlet_mask = arr.ctypes.data
     return m
 
 
@@ -331,13 +341,13 @@ def profile_read(h, cls: int):
     return n.value, ms.value
 
 
-def active_set_noalloc(mesh: Mesh, params: Params, R, U, phi_old, mask, stream=None):
+def active_set_noalloc(mesh: Mesh, params: Params, R, U, phi_old, mask, stream=None, cell_mask=None):
     """Allocation-free active-set decision on caller buffers (no hierarchy); returns
-    (n_active, n_changed)."""
+    (n_active, n_changed).  cell_mask: device uint8 tensor of the fine cells for a cut domain."""
     na, nc = ctypes.c_int(), ctypes.c_int()
     s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
-    st = load().pff_active_set_noalloc(ctypes.byref(mesh), ctypes.byref(params), _ptr(R), _ptr(U), _ptr(phi_old),
-                                       _ptr(mask), ctypes.byref(na), ctypes.byref(nc), s)
+    st = load().pff_active_set_noalloc(ctypes.byref(mesh), ctypes.byref(params), _ptr(cell_mask), _ptr(R), _ptr(U),
+                                       _ptr(phi_old), _ptr(mask), ctypes.byref(na), ctypes.byref(nc), s)
     _check(None, st, "pff_active_set_noalloc")
     return na.value, nc.value
 
@@ -389,6 +399,28 @@ def batch_newton_step(b, Us, allow_noconv=False):
     allow = (ENOCONV,) if allow_noconv else ()
     _bcheck(b, load().pff_batch_newton_step(b, _ptr_array(Us), infos), "pff_batch_newton_step", allow)
     return list(infos)
+
+
+def batch_apply_jacobian(b, level, precision, xs, ys):
+    """y_i = G~_i x_i on 'level' (-1: each instance's finest) of every instance; precision 64 or 32."""
+    return _bcheck(b, load().pff_batch_apply_jacobian(b, level, precision, _ptr_array(xs), _ptr_array(ys)),
+                   "pff_batch_apply_jacobian")
+
+
+def batch_set_kernel_style(b, style: int):
+    return _bcheck(b, load().pff_batch_set_kernel_style(b, style), "pff_batch_set_kernel_style")
+
+
+def batch_last_error(b) -> str:
+    return load().pff_batch_last_error(b).decode()
+
+
+def fp32_fma_tflops(stream=None) -> float:
+    """Measured FP32 FMA rate of the GPU (TFLOP/s), the arithmetic roofline of the df64 operators."""
+    out = ctypes.c_double()
+    s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+    _check(None, load().pff_fp32_fma_tflops(s, ctypes.byref(out)), "pff_fp32_fma_tflops")
+    return out.value
 
 
 def launch_count() -> int:

@@ -46,6 +46,7 @@ class Result:
     solve_latency: list = field(default_factory=list)     # per Newton step (linear solve)
     converged: list = field(default_factory=list)         # per load step
     U: np.ndarray | None = None
+    cancelled: bool = False
 
 
 class PffBackend:
@@ -121,6 +122,25 @@ class Server:
     def submit(self, req: Request):
         self.waiting.append(req)
         self.results[req.rid] = Result(req.rid, arrival=req.arrival)
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a request between ticks: a waiting request leaves the queue; an admitted one has
+        its instance destroyed and its device bytes returned to the budget.  False if the request
+        already finished or is unknown."""
+        for i, req in enumerate(self.waiting):
+            if req.rid == rid:
+                self.waiting.pop(i)
+                self.results[rid].cancelled = True
+                return True
+        for i, s in enumerate(self.active):
+            if s["req"].rid == rid:
+                self.backend.destroy(s["inst"])
+                self.used -= s["bytes"]
+                self.active.pop(i)
+                self.results[rid].cancelled = True
+                self.results[rid].finished = self.now()
+                return True
+        return False
 
     def _pressure(self, req, step):
         return req.workload.pressure * step / req.load_steps
@@ -200,7 +220,7 @@ def summarize(results: dict, wall: float) -> dict:
     """p50/p99 latency per linear solve, per load step and per request, and solves/s."""
     solves = [x for r in results.values() for x in r.solve_latency]
     steps = [x for r in results.values() for x in r.load_step_latency]
-    reqs = [r.finished - r.arrival for r in results.values() if r.finished]
+    reqs = [r.finished - r.arrival for r in results.values() if r.finished and not r.cancelled]
 
     def pct(v, q):
         return float(np.percentile(v, q)) * 1e3 if v else None

@@ -111,3 +111,29 @@ def test_summary_percentiles():
     assert s["linear_solves"] == 3 and s["solves_per_s"] == pytest.approx(6.0)
     assert s["solve_ms_p50"] == pytest.approx(2.0)
     assert s["request_ms_p99"] == pytest.approx(19.9, rel=1e-3)
+
+
+def test_cancel_releases_bytes():
+    """A request cancelled while admitted gives its device bytes back and lets a waiting one in;
+    a cancelled waiting request never runs."""
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    rs = reqs(4)
+    per = be.bytes_for(rs[0].workload)
+    srv = serve.Server(be, hbm_budget=2 * per, clock=clk)
+    for r in rs:
+        srv.submit(r)
+    srv.tick()
+    assert {s["req"].rid for s in srv.active} == {0, 1} and srv.used == 2 * per
+    assert srv.cancel(0)
+    assert srv.used == per and len(be.live) == 1
+    assert srv.cancel(3)                       # still waiting
+    assert not srv.cancel(99)
+    while srv.waiting or srv.active:
+        srv.tick()
+        assert srv.used <= srv.budget
+    assert srv.used == 0 and not be.live
+    assert srv.results[0].cancelled and srv.results[3].cancelled
+    assert srv.results[3].admitted == 0.0 and srv.results[3].U is None
+    assert srv.results[2].admitted > 0.0 and not srv.results[2].cancelled
+    assert serve.summarize(srv.results, 1.0)["requests"] == 4
