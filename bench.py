@@ -179,13 +179,16 @@ def cpu_baseline(n: int = 24, seconds: float = 3.0):
 
 
 def bench_batch(count: int, dev):
-    """Batching pattern: 'count' instances of the batch recipe (N in {16,24,32,48,64}), one active-set
-    step each (one linear solve to 1e-8).  Solves/s of the batched solver with the FP32 and with the
-    FP64 V-cycle against the same instances solved one after another by the single-instance solver
-    with the same V-cycles."""
+    """Batching pattern: 'count' instances of the batch recipe (N in {16,24,32,48,64}, 1-6 cracks), one
+    active-set step each (one linear solve to 1e-8).  Solves/s of the batched solver (one persistent
+    launch per level and operation, device-side FGMRES state, the Arnoldi step replayed from a captured
+    graph, autotuned level kernels) with the FP32 V-cycle (instances that stall switch to the FP64
+    V-cycle after 10 iterations) and with the FP64 V-cycle, against the same instances solved one after
+    another by the single-instance solver."""
     import torch
     from paper_1902_08112_gb300 import pff, workloads as W
     ws = W.batch_instances(count)
+    stream = torch.cuda.Stream(device=dev)
 
     def build(mgp):
         hs, Us = [], []
@@ -193,7 +196,7 @@ def bench_batch(count: int, dev):
             U, po, pt = W.initial_state(w, displacement="smooth")
             prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
                                      mg_precision=mgp, seed=w.seed)
-            h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm)
+            h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm, stream)
             Ud = torch.from_numpy(U).to(dev)
             pff.set_state(h, Ud, torch.from_numpy(po).to(dev), torch.from_numpy(pt).to(dev))
             hs.append(h)
@@ -201,58 +204,72 @@ def bench_batch(count: int, dev):
         torch.cuda.synchronize()
         return hs, Us
 
-    hs, Us = build(32)
-    U0 = [u.clone() for u in Us]
-    b = pff.batch_create(hs)
-    pff.batch_newton_step(b, Us, allow_noconv=True)          # warm-up
-    for u, u0 in zip(Us, U0):
-        u.copy_(u0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    infos = pff.batch_newton_step(b, Us, allow_noconv=True)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
-    pff.batch_destroy(b)
-    single = {}
-    for mgp in (32, 64):
-        if mgp == 64:
-            for h in hs:
-                pff.destroy_hierarchy(h)
-            hs, _ = build(64)
-            # batched FP64 V-cycle on the same instances
-            b64 = pff.batch_create(hs)
-            for u, u0 in zip(Us, U0):
-                u.copy_(u0)
-            pff.batch_newton_step(b64, Us, allow_noconv=True)     # warm-up
-            for u, u0 in zip(Us, U0):
-                u.copy_(u0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            infos64 = pff.batch_newton_step(b64, Us, allow_noconv=True)
-            torch.cuda.synchronize()
-            tb64 = time.perf_counter() - t0
-            pff.batch_destroy(b64)
+    def batched(hs, Us, U0):
+        b = pff.batch_create(hs)
+        for u, u0 in zip(Us, U0):
+            u.copy_(u0)
+        torch.cuda.synchronize()
+        pff.batch_newton_step(b, Us, allow_noconv=True)          # warm-up: tuning, graph capture
+        for u, u0 in zip(Us, U0):
+            u.copy_(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = pff.batch_newton_step(b, Us, allow_noconv=True)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        precs = pff.batch_mg_precisions(b, len(hs))
+        Lmax = max(w.n_levels for w in ws)
+        tune = {}
+        for level in list(range(Lmax)) + [-1]:
+            for prec in (32, 64):
+                try:
+                    st, cps, ms = pff.batch_tuning(b, level, prec)
+                except pff.PffError:
+                    continue
+                if st:
+                    tune[f"{'fine' if level < 0 else 'l%d' % level}_fp{prec}"] = {
+                        "kernels": "per_cell" if st == 2 else "small_level", "ctas_per_sm": cps, "ms": ms}
+        pff.batch_destroy(b)
+        return el, infos, precs, tune
+
+    def single(hs, Us, U0):
         for u, u0 in zip(Us, U0):
             u.copy_(u0)
         pff.newton_step(hs[0], Us[0].clone(), allow_noconv=True)   # warm-up
+        for u, u0 in zip(Us, U0):
+            u.copy_(u0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sinfos = [pff.newton_step(h, u, allow_noconv=True) for h, u in zip(hs, Us)]
         torch.cuda.synchronize()
-        single[mgp] = (time.perf_counter() - t0, [i.solve.iterations for i in sinfos])
+        return time.perf_counter() - t0, [i.solve.iterations for i in sinfos]
+
+    out = {"instances": count, "dofs": int(sum(w.n_dofs for w in ws)), "sizes": sorted({w.n_cells[0] for w in ws}),
+           "stream": "non-default (captured Arnoldi step replayed)"}
+    hs, Us = build(32)
+    U0 = [u.clone() for u in Us]
+    tb32, infos32, precs32, tune32 = batched(hs, Us, U0)
+    ts32, its_s32 = single(hs, Us, U0)
     for h in hs:
         pff.destroy_hierarchy(h)
-    dofs = sum(w.n_dofs for w in ws)
-    return {"instances": count, "dofs": dofs, "sizes": sorted({w.n_cells[0] for w in ws}),
-            "batched_fp32mg_solves_per_s": count / tb,
-            "batched_fp64mg_solves_per_s": count / tb64,
-            "gmres_its_batched_fp64mg": [i.solve.iterations for i in infos64],
-            "single_fp32mg_solves_per_s": count / single[32][0],
-            "single_fp64mg_solves_per_s": count / single[64][0],
-            "speedup_vs_single_fp32mg": single[32][0] / tb,
-            "gmres_its_batched": [i.solve.iterations for i in infos],
-            "gmres_its_single_fp32mg": single[32][1], "gmres_its_single_fp64mg": single[64][1],
-            "all_converged": all(i.solve.converged for i in infos)}
+    hs, _ = build(64)
+    tb64, infos64, _, tune64 = batched(hs, Us, U0)
+    ts64, its_s64 = single(hs, Us, U0)
+    for h in hs:
+        pff.destroy_hierarchy(h)
+    out.update({
+        "batched_fp32mg_solves_per_s": count / tb32,
+        "batched_fp64mg_solves_per_s": count / tb64,
+        "single_fp32mg_solves_per_s": count / ts32,
+        "single_fp64mg_solves_per_s": count / ts64,
+        "batched_fp32mg_vs_single_fp64mg": ts64 / tb32,
+        "gmres_its_batched_fp32mg": [i.solve.iterations for i in infos32],
+        "switched_to_fp64mg": int(sum(p == 64 for p in precs32)),
+        "gmres_its_batched_fp64mg": [i.solve.iterations for i in infos64],
+        "gmres_its_single_fp32mg": its_s32, "gmres_its_single_fp64mg": its_s64,
+        "all_converged": all(i.solve.converged for i in infos32 + infos64),
+        "autotuner_fp32mg": tune32, "autotuner_fp64mg": tune64})
+    return out
 
 
 def bench_multi(n: int, dev):
@@ -366,25 +383,30 @@ def bench_variants(n: int, dev):
 
 
 def bench_serve(count: int):
-    """Serving pattern: Poisson arrivals of random pressurised-crack requests (N in {16,24,32}) mixed
-    with 3D L-shaped panels (every 4th request), 2 load steps each, served by the
+    """Serving pattern: Poisson arrivals of random pressurised-crack requests (the batch recipe with
+    N in {16,24,32}, 2 pressure load steps) mixed with displacement-driven 3D L-shaped panels (every 4th
+    request, 2^k cells per edge for k = 4..7, a 20-step displacement ramp), served by the
     continuous-batching loop at 50, 80 and 95 % of the measured closed-loop capacity."""
     from paper_1902_08112_gb300 import serve
     # capacity: all requests queued at once
     cal = serve.poisson_requests(max(4, count // 4), 1.0, seed=99, lshape_every=4)
-    srv = serve.Server(serve.PffBackend(), hbm_budget=64 << 30)
+    be = serve.PffBackend()
+    srv = serve.Server(be, hbm_budget=64 << 30)
     t0 = srv.now()
     srv.run(cal, realtime=False)
     cap = len(cal) / (srv.now() - t0)       # requests per second
-    out = {"capacity_requests_per_s": cap, "load_steps": 2, "mix": "batch recipe + 3D L-shape every 4th"}
+    out = {"capacity_requests_per_s": cap, "load_steps": {"crack": 2, "lshape": 20},
+           "mix": "batch recipe (N 16/24/32) + displacement-driven 3D L-shape (edge 16..128) every 4th"}
     for frac in (0.5, 0.8, 0.95):
         reqs = serve.poisson_requests(count, frac * cap, seed=12345, lshape_every=4)
-        srv = serve.Server(serve.PffBackend(), hbm_budget=64 << 30)
+        be = serve.PffBackend()
+        srv = serve.Server(be, hbm_budget=64 << 30)
         t0 = srv.now()
         srv.run(reqs, realtime=True)
         wall = srv.now() - t0
         res = serve.summarize(srv.results, wall)
-        res.update({"arrival_rate_per_s": frac * cap, "ticks": srv.ticks})
+        res.update({"arrival_rate_per_s": frac * cap, "ticks": srv.ticks, "batches_built": be.batches_built,
+                    "lshape_sizes": sorted({r.workload.n_cells[0] for r in reqs if r.workload.domain == "lshape"})})
         out[f"load_{int(frac * 100)}"] = res
     return out
 
@@ -431,7 +453,7 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="cells per edge of the 3D penny workload")
     ap.add_argument("--levels", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", type=int, default=32, help="instances in the batching measurement (0: skip)")
+    ap.add_argument("--batch", type=int, default=256, help="instances in the batching measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving measurement (0: skip)")
     ap.add_argument("--multi", type=int, default=256, help="cells per edge of the multi-crack measurement (0: skip)")
     ap.add_argument("--variants", type=int, default=64, help="cells per edge of the variant measurements (0: skip)")

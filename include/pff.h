@@ -191,9 +191,23 @@ pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant);
  * irreversibility bound, phi_tilde: FP64 (n_nodes) = the extrapolation used in the
  * displacement equation (Eq. (semilinear)).  The library copies them, restricts U and
  * phi_tilde to every coarser level by coincident nodes (Sec. 4.2), and keeps FP32 copies.
- * The current active set is kept.  Errors: PFF_EINVAL (NULL). */
-pff_status pff_set_state(pff_hierarchy* h, const double* U, const double* phi_old,
-                         const double* phi_tilde);
+ * The current active set is kept.
+ * u_dirichlet (nullable): device FP64 of at least dim * n_nodes entries in the layout of U's
+ * displacement blocks: prescribed displacement values on the Dirichlet DoFs (the faces of
+ * pff_mesh.dirichlet_faces and the PFF_MASK_U* bits of pff_mesh.dirichlet_mask; entries elsewhere
+ * are not read), as in the displacement-driven loading of the L-shaped panels (Sec. 5.2, 5.3).  The
+ * stored state and, in every later pff_newton_step / pff_load_step, the caller's U take these values
+ * on those DoFs, so the Newton increments vanish there (the eliminated rows of Algorithm 1, step 4,
+ * stay homogeneous).  The values are copied and kept until the next pff_set_state; NULL means no
+ * prescribed values (the state keeps whatever U holds on Dirichlet DoFs).
+ * Errors: PFF_EINVAL (NULL U, phi_old or phi_tilde), PFF_ENOMEM. */
+pff_status pff_set_state(pff_hierarchy* h, const double* U, const double* phi_old, const double* phi_tilde,
+                         const double* u_dirichlet);
+
+/* Replace the prescribed displacement values of pff_set_state (same layout and meaning; NULL removes
+ * them) without resetting the state, e.g. at each step of a displacement ramp before pff_load_step.
+ * The stored state takes the new values on the Dirichlet DoFs.  Errors: PFF_ENOMEM, PFF_ECUDA. */
+pff_status pff_set_dirichlet_values(pff_hierarchy* h, const double* u_dirichlet);
 
 /* Set the active set from a device array of n_nodes bytes (nonzero = active) and carry it to
  * every coarser level by coincident nodes (Sec. 4.2).  Marks the preconditioner stale. */
@@ -315,7 +329,10 @@ typedef struct {
 pff_status pff_load_step(pff_hierarchy* h, double* U, const double* phi_prev, double pressure, int max_newton,
                          pff_load_info* info);
 
-/* ---- Batches of independent instances (one launch per level and operation across instances).
+/* ---- Batches of independent instances (one persistent launch per level and operation across
+ * instances; the batched FGMRES keeps every instance's Hessenberg matrix, Givens rotations and
+ * stopping test on the device, and on a non-default stream replays its Arnoldi step -- V-cycle,
+ * apply, Gram-Schmidt, norm, scalar update, for all instances at once -- from one captured CUDA graph).
  * A batch is a view over n existing hierarchies created on the same stream, all Q1 with the same
  * dimension, one mg_precision (32 or 64), preconditioner 0, split 0 and cheb_degree; instances may differ in mesh size, number of levels
  * and physical parameters.  The batch owns only descriptor tables and reduction scratch; the
@@ -349,6 +366,28 @@ pff_status pff_batch_apply_jacobian(pff_batch* b, int level, int precision, cons
  * levels the Gauss-point-lane FP64-accurate and per-cell-gather FP32 kernels), 1 = the small-level
  * kernels on every level, 2 = the per-cell kernels on every 3D level.  Errors: PFF_EINVAL. */
 pff_status pff_batch_set_kernel_style(pff_batch* b, int style);
+/* FP32 V-cycle batches (mg_precision 32): an instance whose FGMRES solve is still above its tolerance
+ * after 'iterations' iterations continues with the all-FP64 V-cycle (flexible GMRES admits a different
+ * preconditioner in every iteration, so the Krylov basis built so far is kept).  In a few instances --
+ * crack zones where kappa = 1e-10 leaves displacement DoFs with nearly no stiffness -- the FP32
+ * V-cycle's rounding limits the achievable reduction and the solve stalls at many times the usual
+ * iteration count; the switch bounds what such an instance costs the whole batch.  The decision is
+ * taken on the device per instance; the batch then replays a second captured Arnoldi step whose
+ * V-cycle runs in FP32 and in FP64 on the two subsets.  Default 10; 0 never switches.
+ * Errors: PFF_EINVAL (negative). */
+pff_status pff_batch_set_precision_switch(pff_batch* b, int iterations);
+/* The V-cycle precision (32 or 64) each instance used at the end of the last batched solve (host
+ * array of n ints).  Synchronises.  Errors: PFF_EINVAL, PFF_ECUDA. */
+pff_status pff_batch_mg_precisions(pff_batch* b, int* precisions);
+/* The autotuner's choice for one level (-1: the instances' finest levels) and precision (32 or 64):
+ * style 1 = small-level kernels, 2 = per-cell kernels, 0 = not tuned (the size rule applies);
+ * ctas_per_sm = the persistent grid of the batched launch in CTAs per SM (0 = one CTA per tile);
+ * ms = the measured time of one apply.  With style 0 (pff_batch_set_kernel_style) the first
+ * pff_batch_setup times every candidate on the batch's own data with CUDA events and keeps the
+ * fastest; choices are cached for the process by dimension, precision and the binary orders of the
+ * level's cells and instances.  Host outputs, any may be NULL.  Errors: PFF_EINVAL, PFF_ESTATE
+ * (not tuned yet). */
+pff_status pff_batch_tuning(pff_batch* b, int level, int precision, int* style, int* ctas_per_sm, double* ms);
 const char* pff_batch_last_error(const pff_batch* b);
 
 /* Kernel timing (tracing).  pff_profile(h, 1) clears the counters and starts recording CUDA

@@ -67,11 +67,28 @@ def eliminated_rhs(mesh, phys, U, ptil, phi_old, dir_mask, active, R):
     return Rt, mask
 
 
+def lift_dirichlet(mesh, U, dir_mask, u_dirichlet):
+    """The iterate with prescribed displacements on the Dirichlet DoFs (u-components whose mask bit is
+    set); other entries of u_dirichlet are not read."""
+    U = np.array(U, dtype=np.float64)
+    nn = mesh.n_nodes
+    for c in range(mesh.dim):
+        on = (np.asarray(dir_mask) & fem.BIT_U[c]) != 0
+        U[c * nn:(c + 1) * nn][on] = np.asarray(u_dirichlet)[c * nn:(c + 1) * nn][on]
+    return U
+
+
 def newton_step(mesh, phys, n_levels, U, phi_old, ptil, dir_mask, prev_active, c_as=100.0,
                 tol_as=1e-10, rtol=1e-8, restart=30, maxit=500, seed=12345, cg_steps=10,
-                prm: multigrid.MGParams | None = None):
+                prm: multigrid.MGParams | None = None, u_dirichlet=None):
+    """u_dirichlet: prescribed displacement values (displacement-driven loading, Sec. 5.2/5.3).  The
+    iterate takes them on the Dirichlet DoFs before step 1, so R, G and the active set are evaluated at
+    a state that satisfies the boundary condition and the increment of step 5 vanishes there (those rows
+    are eliminated with a zero right-hand side, step 4)."""
     prm = prm or multigrid.MGParams()
     U = np.asarray(U, dtype=np.float64)
+    if u_dirichlet is not None:
+        U = lift_dirichlet(mesh, U, dir_mask, u_dirichlet)
     R = -fem.residual_A(mesh, phys, U, ptil)
     M = fem.lumped_mass(mesh)
     act = active_set(mesh, R, M, U, phi_old, c_as, tol_as, fixed=(dir_mask & fem.BIT_PHI_DIR) != 0)

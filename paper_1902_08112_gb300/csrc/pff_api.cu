@@ -417,16 +417,44 @@ extern "C" pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant) {
 }
 
 extern "C" pff_status pff_set_state(pff_hierarchy* h, const double* U, const double* phi_old,
-                                    const double* phi_tilde) {
+                                    const double* phi_tilde, const double* u_dirichlet) {
     if (!h) return PFF_EINVAL;
     REQUIRE(h, U && phi_old && phi_tilde, PFF_EINVAL, "pff_set_state: NULL vector");
     Level& F = h->lv[h->L - 1];
     const size_t nn = (size_t)F.g.n_nodes, nd = (size_t)n_dofs(F.g);
+    if (u_dirichlet) {
+        if (!h->udir) CUDA_OR_FAIL(h, dalloc(h, &h->udir, (size_t)F.g.dim * nn));
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->udir, u_dirichlet, (size_t)F.g.dim * nn * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, h->stream));
+        h->has_udir = true;
+    } else {
+        h->has_udir = false;
+    }
     CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->has_udir) CUDA_OR_FAIL(h, launch_lift_dirichlet(F.g, h->dir_mask, h->udir, F.U64, h->stream));
     CUDA_OR_FAIL(h, cudaMemcpyAsync(F.pt64, phi_tilde, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CUDA_OR_FAIL(h, cudaMemcpyAsync(h->phi_old, phi_old, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CUDA_OR_FAIL(h, propagate_state(h));
     h->has_state = true;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_set_dirichlet_values(pff_hierarchy* h, const double* u_dirichlet) {
+    if (!h) return PFF_EINVAL;
+    Level& F = h->lv[h->L - 1];
+    const size_t nu = (size_t)F.g.dim * (size_t)F.g.n_nodes;
+    if (!u_dirichlet) {
+        h->has_udir = false;
+        return PFF_OK;
+    }
+    if (!h->udir) CUDA_OR_FAIL(h, dalloc(h, &h->udir, nu));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->udir, u_dirichlet, nu * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    h->has_udir = true;
+    if (h->has_state) {
+        CUDA_OR_FAIL(h, launch_lift_dirichlet(F.g, h->dir_mask, h->udir, F.U64, h->stream));
+        h->derived_dirty = true;
+        h->stale = true;
+    }
     return PFF_OK;
 }
 
@@ -775,6 +803,8 @@ pff_status pff_internal_newton_prepare(pff_hierarchy* h, double* U, int* n_act, 
     Level& F = h->lv[h->L - 1];
     const int64_t nd = n_dofs(F.g);
     cudaStream_t s = h->stream;
+    // prescribed displacements: the iterate takes the boundary values, the increments vanish there
+    if (h->has_udir) CUDA_OR_FAIL(h, launch_lift_dirichlet(F.g, h->dir_mask, h->udir, U, s));
     CUDA_OR_FAIL(h, cudaMemcpyAsync(F.U64, U, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CUDA_OR_FAIL(h, propagate_state(h));
     pff_status st = update_active(h, n_act, n_chg);

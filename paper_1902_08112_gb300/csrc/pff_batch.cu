@@ -13,8 +13,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "pff_batch.cuh"
@@ -40,8 +43,37 @@ struct pff_batch {
     double* d_part = nullptr;                // partial sums
     double* d_vals = nullptr;                // per-instance scalars
     double* d_coef = nullptr;                // Chebyshev tables (smoother and coarse)
+    size_t coef_cap = 0;                     // allocated doubles of d_coef
     uint64_t* d_seeds = nullptr;
     int cheb_k = 4, coarse_k = 1;
+    // batched FGMRES state on the device (per instance): flags read by every batched kernel, the
+    // Hessenberg matrices, Givens rotations and right-hand sides, iteration counts and targets
+    int* d_on = nullptr;                     // n: instance active in the current Arnoldi step
+    int* d_cyc = nullptr;                    // n: instance takes part in the current restart cycle
+    int* d_col = nullptr;                    // 1: Krylov column j of the next Arnoldi step
+    int* d_its = nullptr;                    // n
+    int* d_k = nullptr;                      // n: Krylov dimension of the cycle
+    int* d_flags = nullptr;                  // n: bit 0 non-finite residual, bit 1 non-finite Arnoldi norm
+    int* d_count = nullptr;                  // [0] instances on after the last step, [1] maxit, [2] instances on with
+                                             // the FP64 V-cycle, [3] iterations before an FP32-MG instance switches
+    int* d_prec = nullptr;                   // n: V-cycle precision of the instance in the current solve (32 / 64)
+    int* d_save = nullptr;                   // n: the FGMRES flags while a V-cycle runs on a precision's subset
+    int switch_its = 10;                     // FP32 V-cycle batches: FP64 V-cycle after this many iterations (0: never)
+    double* d_fg = nullptr;                  // per instance: beta, target, g (m + 1), cs, sn, y (m each), H
+    int* h_status = nullptr;                 // pinned host mirror: [0] count, [1 ..] flags / its
+    cudaEvent_t ev_step[2] = {nullptr, nullptr};
+    cudaGraphExec_t step_graph = nullptr;    // one captured Arnoldi step (every column j)
+    cudaGraphExec_t step_graph_mixed = nullptr;   // the same with the V-cycle split by instance precision
+    int graph_key = -1;                      // coarse_k the graph was captured with
+    bool use_graphs = true;
+    long long graph_nodes = 0, graph_nodes_mixed = 0;
+    // autotuned level operators: per lockstep level (Lmax = the fine table) and precision (0 FP32,
+    // 1 FP64) the kernel family (1 small-level kernels, 2 per-cell kernels) and the persistent grid
+    // (CTAs per SM; 0 = one CTA per tile), with the measured time of one apply
+    struct Tune { int style = 0, cps = 0; double ms = 0.0; };
+    std::vector<Tune> tune;                  // (Lmax + 1) * 2
+    bool tuned = false;
+    int sms = 0;
     bool mg64 = false;                       // FP64 V-cycle (mg_precision 64 in every instance)
     int style = 0;                           // level-operator kernels: 0 by level size, 1 small-level, 2 per-cell
     bool stale = true;
@@ -70,12 +102,14 @@ cudaError_t balloc(pff_batch* b, T** p, size_t count) {
     return cudaMemsetAsync(q, 0, count * sizeof(T) + 16, b->stream);
 }
 
-BLevel make_desc(pff_hierarchy* h, int l, bool valid) {
+BLevel make_desc(pff_hierarchy* h, int l, bool valid, const int* on, const int* col) {
     BLevel d;
     memset(&d, 0, sizeof(d));
     Level& L = h->lv[l];
     d.g = L.g;
     d.valid = valid ? 1 : 0;
+    d.on = on;
+    d.col = col;
     d.mask = L.mask;
     d.qpd32 = L.qpd32;
     d.qpd64 = L.qpd64;
@@ -102,6 +136,16 @@ int grid_w(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1024));
 }
 
+__global__ void kb_set_flags(int n, int v, int* __restrict__ on) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) on[i] = v;
+}
+
+// every instance on (the state between batched FGMRES solves)
+cudaError_t set_all_on(pff_batch* b) {
+    kb_set_flags<<<std::max(1, std::min(64, (b->n + 255) / 256)), 256, 0, b->stream>>>(b->n, 1, b->d_on);
+    return count_launch(cudaGetLastError());
+}
+
 // rebuild and upload descriptor tables and tile prefixes for the instances flagged in b->valid
 cudaError_t upload(pff_batch* b) {
     const int n = b->n;
@@ -115,7 +159,7 @@ cudaError_t upload(pff_batch* b) {
             const bool fine = l == b->Lmax;
             const int li = fine ? h->L - 1 : l;
             const bool has = li < h->L;
-            BLevel d = make_desc(h, has ? li : 0, has && b->valid[i]);
+            BLevel d = make_desc(h, has ? li : 0, has && b->valid[i], b->d_on ? b->d_on + i : nullptr, b->d_col);
             if (fine) b->h_fine[i] = d; else b->h_lv[l][i] = d;
             for (int st = 0; st < 2; ++st) {
                 int* pre = &tiles[((size_t)l * 2 + st) * (n + 1)];
@@ -134,27 +178,37 @@ cudaError_t upload(pff_batch* b) {
                             b->stream));
     BCK(cudaMemcpyAsync(b->d_fine, b->h_fine.data(), sizeof(BLevel) * n, cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, b->stream));
+    if (b->d_on) BCK(set_all_on(b));
     // the host vectors are reused at the next upload: make the copies complete first
     return cudaStreamSynchronize(b->stream);
 }
 
 const BLevel* tab(pff_batch* b, int l) { return l == b->Lmax ? b->d_fine : b->d_lv + (size_t)l * b->n; }
 
-// y(sy) = G~ x(sx) on level l (l == Lmax: each instance's finest level), precision by fp64
-cudaError_t b_apply(pff_batch* b, int l, bool fp64, bool blockdiag, int sx, int sy, int phi_bits, bool preset = true) {
+// y(sy) = G~ x(sx) on level l (l == Lmax: each instance's finest level), precision by fp64.  The
+// kernel family and persistent grid come from the autotuner (style 0), else from the fixed rule
+// (3D levels of at least kCellMinCells cells over the batch run the per-cell kernel with
+// shared-memory derivatives) or the forced style.
+cudaError_t b_apply(pff_batch* b, int l, bool fp64, bool blockdiag, int sx, int sy, int phi_bits, bool preset = true,
+                    int force_style = 0, int force_cps = -1) {
     const BLevel* L = tab(b, l);
-    // 3D levels of at least kCellMinCells cells over the batch: the per-cell kernel with
-    // shared-memory derivatives, on the tiles of the FP32 per-cell style
+    int style = force_style ? force_style : b->style;
+    int cps = force_cps >= 0 ? force_cps : 0;
+    if (!force_style && style == 0 && b->tuned) {
+        const pff_batch::Tune& t = b->tune[(size_t)l * 2 + (fp64 ? 1 : 0)];
+        style = t.style;
+        if (force_cps < 0) cps = t.cps;
+    }
     const bool cell = b->dim == 3 && q1_cell_tiles_match_f32() &&
-                      (b->style == 2 || (b->style == 0 && b->cells[l] >= kCellMinCells));
+                      (style == 2 || (style == 0 && b->cells[l] >= kCellMinCells));
     const int st = (fp64 && !cell) ? kStyleF64 : kStyleF32;
     if (preset) {
         if (fp64) BCK(bl_init_masked<double>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.0, b->stream));
         else BCK(bl_init_masked<float>(L, b->n, b->blocks[l], sx, sy, phi_bits, 0.f, b->stream));
     }
-    return launch_q1_apply_batched(b->dim, fp64, blockdiag, fp64, L, b->n,
+    return launch_q1_apply_batched(b->dim, fp64, blockdiag, fp64 && !cell, L, b->n,
                                    b->d_tiles + ((size_t)l * 2 + st) * (b->n + 1), b->tot[(size_t)l * 2 + st], sx, sy,
-                                   phi_bits, b->stream, cell);
+                                   phi_bits, b->stream, cell, cps > 0 ? cps * b->sms : 0);
 }
 
 double* smooth_coef(pff_batch* b, int l, int step) { return b->d_coef + ((size_t)l * b->cheb_k + step) * b->n * 4; }
@@ -378,6 +432,98 @@ int host_coarse_steps(double alpha, double beta, double rtol, int maxit) {
     return std::max(1, (int)std::min<double>(k, (double)maxit));
 }
 
+void drop_step_graph(pff_batch* b);
+
+// ---------------------------------------------------------------- autotuner
+// Choices are cached for the process by (dimension, precision, log2 of the level's cells over the
+// batch, log2 of its instances), so batches of a similar make-up (e.g. successive compositions of a
+// serving loop) reuse them.
+struct TuneKey {
+    int dim, prec, lc, ln;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dim, prec, lc, ln) < std::tie(o.dim, o.prec, o.lc, o.ln);
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, pff_batch::Tune> g_tune_cache;
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while (v > 1) { v >>= 1; ++r; }
+    return r;
+}
+
+// Time every candidate (kernel family x persistent grid) of the level operator on each level and
+// precision the batch uses, with CUDA events over a few launches on the level's scratch vectors
+// (work vectors 3 -> 4, free at setup time), and keep the fastest.
+cudaError_t b_autotune(pff_batch* b) {
+    const int n = b->n;
+    b->tune.assign((size_t)(b->Lmax + 1) * 2, pff_batch::Tune());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCK(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return err;
+    }
+    for (int l = 0; l <= b->Lmax && err == cudaSuccess; ++l) {
+        if (b->cells[l] == 0) continue;
+        for (int prec = 0; prec < 2 && err == cudaSuccess; ++prec) {
+            // FP64 operators run on the fine table and the coarse level (FGMRES, coarse solve) or, with
+            // the FP64 V-cycle, everywhere; FP32 operators on the V-cycle levels of an FP32 V-cycle
+            const bool used = prec == 1 ? (l == b->Lmax || l == 0 || b->mg64) : (!b->mg64 && l > 0 && l < b->Lmax);
+            if (!used) continue;
+            const TuneKey key{b->dim, prec, ilog2(b->cells[l]), ilog2(n)};
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                auto it = g_tune_cache.find(key);
+                if (it != g_tune_cache.end()) {
+                    b->tune[(size_t)l * 2 + prec] = it->second;
+                    continue;
+                }
+            }
+            const int W = prec ? BV_W64 : BV_W32;
+            pff_batch::Tune best;
+            best.ms = -1.0;
+            const int nstyles = b->dim == 3 ? 2 : 1;
+            for (int style = 1; style <= nstyles && err == cudaSuccess; ++style) {
+                const bool cell = style == 2;
+                const int res = q1_batched_ctas_per_sm(b->dim, prec == 1, cell);
+                const int tiles = b->tot[(size_t)l * 2 + ((prec == 1 && !cell) ? kStyleF64 : kStyleF32)];
+                std::vector<int> cands{0};
+                for (int c : {std::max(1, res / 2), res})
+                    if ((int64_t)c * b->sms < tiles && std::find(cands.begin(), cands.end(), c) == cands.end())
+                        cands.push_back(c);
+                for (int c : cands) {
+                    err = b_apply(b, l, prec == 1, false, bsel(W + 3), bsel(W + 4), PHI_BITS_ALL, true, style, c);
+                    if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+                    for (int r = 0; r < 3 && err == cudaSuccess; ++r)
+                        err = b_apply(b, l, prec == 1, false, bsel(W + 3), bsel(W + 4), PHI_BITS_ALL, true, style, c);
+                    if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+                    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                    if (err != cudaSuccess) break;
+                    if (best.ms < 0.0 || ms / 3.0 < best.ms) {
+                        best.style = style;
+                        best.cps = c;
+                        best.ms = ms / 3.0;
+                    }
+                }
+            }
+            if (err == cudaSuccess) {
+                b->tune[(size_t)l * 2 + prec] = best;
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                g_tune_cache[key] = best;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err == cudaSuccess) b->tuned = true;
+    return err;
+}
+
 // diagonals per instance, batched eigenvalue estimates, coefficient tables
 cudaError_t b_setup(pff_batch* b) {
     const int n = b->n;
@@ -390,6 +536,7 @@ cudaError_t b_setup(pff_batch* b) {
             BCK(launch_cast_f64_f32(L.dinv64, L.dinv32, n_dofs(L.g), b->stream));
         }
     }
+    if (!b->tuned && b->style == 0) BCK(b_autotune(b));
     const int steps = std::min(b->hs[0]->prm.cg_steps, kMaxCG);
     double* d_eig = b->d_vals + 12 * (size_t)n + (size_t)kMaxCG * 4 * n;   // [l][inst][4]
     for (int l = 0; l < b->Lmax; ++l) {
@@ -445,12 +592,20 @@ cudaError_t b_setup(pff_batch* b) {
                 b->hs[i]->lv[l].lam_max[blk] = eig[((size_t)l * n + i) * 4 + 2 * blk + 1];
             }
     }
-    if (b->d_coef) {
-        for (auto it = b->allocs.begin(); it != b->allocs.end(); ++it)
-            if (*it == b->d_coef) { cudaFree(*it); b->allocs.erase(it); break; }
-        b->d_coef = nullptr;
+    // the table keeps its address across setups (the captured Arnoldi step reads it); it is only
+    // reallocated, and the graph dropped, when it has to grow
+    if (coef.size() > b->coef_cap) {
+        drop_step_graph(b);
+        BCK(cudaStreamSynchronize(b->stream));
+        if (b->d_coef) {
+            for (auto it = b->allocs.begin(); it != b->allocs.end(); ++it)
+                if (*it == b->d_coef) { cudaFree(*it); b->allocs.erase(it); break; }
+            b->d_coef = nullptr;
+        }
+        const size_t cap = coef.size() + coef.size() / 2;
+        BCK(balloc(b, &b->d_coef, cap));
+        b->coef_cap = cap;
     }
-    BCK(balloc(b, &b->d_coef, coef.size()));
     BCK(cudaMemcpyAsync(b->d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
     for (auto* h : b->hs) h->stale = false;
@@ -459,17 +614,255 @@ cudaError_t b_setup(pff_batch* b) {
 }
 
 // ---------------------------------------------------------------- batched FGMRES
-// solve G~ x = b per instance: b in T64[1], x in T64[2] (fine selectors)
+// Per-instance FGMRES scalars live on the device (layout of d_fg per instance, stride fg_stride):
+// [0] beta (current true residual), [1] target, [2] beta_0, [3, m + 4) g, then cs (m), sn (m),
+// y (m), H ((m + 1) x m, row-major).
+__host__ __device__ inline int fg_stride(int m) { return 3 + (m + 1) + 3 * m + (m + 1) * m; }
+constexpr int kFgG = 3;
+
+// Start of a restart cycle: instance i iterates while its true residual beta_i is finite and above
+// target_i and its iteration budget lasts; g = beta e_1, column counter 0, count of active instances.
+__global__ void kb_fg_begin(int n, int m, int maxit, double rtol, int first, int base_prec, int switch_its,
+                            double* __restrict__ fg, int* __restrict__ its, int* __restrict__ cyc,
+                            int* __restrict__ on, int* __restrict__ k, int* __restrict__ flags,
+                            int* __restrict__ prec, int* __restrict__ col, int* __restrict__ count) {
+    __shared__ int cnt, c64;
+    if (threadIdx.x == 0) cnt = c64 = 0;
+    __syncthreads();
+    const int st = fg_stride(m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double* f = fg + (size_t)i * st;
+        const double beta = f[0];
+        if (first) {
+            f[1] = rtol * beta;
+            f[2] = beta;
+            its[i] = 0;
+            flags[i] = 0;
+            prec[i] = base_prec;
+        }
+        const bool finite = isfinite(beta);
+        if (!finite) flags[i] |= 1;
+        const int need = finite && !(beta <= f[1] || its[i] >= maxit || beta == 0.0);
+        cyc[i] = need;
+        on[i] = need;
+        k[i] = 0;
+        double* g = f + kFgG;
+        g[0] = beta;
+        for (int r = 1; r <= m; ++r) g[r] = 0.0;
+        if (need) atomicAdd(&cnt, 1);
+        if (need && prec[i] == 64) atomicAdd(&c64, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *col = 0;
+        count[0] = cnt;
+        count[1] = maxit;        // read by the captured Arnoldi steps
+        count[2] = c64;
+        count[3] = switch_its;
+    }
+}
+
+// One Arnoldi step's scalar work for every active instance (column j = *col): the new Hessenberg
+// column from the two Gram-Schmidt passes and the norm, the previous Givens rotations, a new one,
+// the updated residual estimate |g_{j+1}|; an instance that reaches its target or its iteration cap
+// is switched off.  Then the column counter advances.
+// A still-active FP32-MG instance that has taken count[3] iterations switches to the FP64 V-cycle
+// (flexible GMRES admits a different preconditioner in every iteration).
+__global__ void kb_fg_arnoldi(int n, int m, const double* __restrict__ h, const double* __restrict__ nrm,
+                              double* __restrict__ fg, int* __restrict__ its, int* __restrict__ on,
+                              int* __restrict__ k, int* __restrict__ flags, int* __restrict__ prec,
+                              int* __restrict__ col, int* __restrict__ count) {
+    __shared__ int cnt, c64;
+    const int j = *col, maxit = count[1], sw = count[3];
+    if (threadIdx.x == 0) cnt = c64 = 0;
+    __syncthreads();
+    const int st = fg_stride(m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (!on[i] || j >= m) {
+            if (j >= m) on[i] = 0;
+            continue;
+        }
+        double* f = fg + (size_t)i * st;
+        double* g = f + kFgG;
+        double* cs = g + (m + 1);
+        double* sn = cs + m;
+        double* H = sn + 2 * m;
+        const double* hi = h + (size_t)i * 2 * (m + 1);
+        for (int r = 0; r <= j; ++r) H[(size_t)r * m + j] = hi[r] + hi[(m + 1) + r];
+        const double hn = nrm[i];
+        if (!isfinite(hn)) {
+            flags[i] |= 2;
+            on[i] = 0;
+            continue;
+        }
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int r = 0; r < j; ++r) {
+            const double a = H[(size_t)r * m + j], bb = H[(size_t)(r + 1) * m + j];
+            H[(size_t)r * m + j] = cs[r] * a + sn[r] * bb;
+            H[(size_t)(r + 1) * m + j] = -sn[r] * a + cs[r] * bb;
+        }
+        const double den = hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+        cs[j] = H[(size_t)j * m + j] / den;
+        sn[j] = H[(size_t)(j + 1) * m + j] / den;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        its[i] += 1;
+        k[i] = j + 1;
+        if (fabs(g[j + 1]) <= f[1] || its[i] >= maxit || j + 1 >= m) {
+            on[i] = 0;
+        } else {
+            atomicAdd(&cnt, 1);
+            if (prec[i] == 32 && sw > 0 && its[i] >= sw) prec[i] = 64;
+            if (prec[i] == 64) atomicAdd(&c64, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *col = j + 1;
+        count[0] = cnt;
+        count[2] = c64;
+    }
+}
+
+// V-cycle of one precision's subset: mode 0 keeps the FGMRES flags and leaves the FP32-MG instances
+// on, mode 1 the FP64-MG ones, mode 2 restores the flags
+__global__ void kb_prec_subset(int n, int mode, int* __restrict__ on, int* __restrict__ save,
+                               const int* __restrict__ prec) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (mode == 0) save[i] = on[i];
+        const int o = save[i];
+        on[i] = mode == 2 ? o : (o && prec[i] == (mode == 0 ? 32 : 64));
+    }
+}
+
+// y = H_k^-1 g_k (back substitution) for every instance of the cycle; then the cycle's instances
+// are switched on again for the update x += Z y
+__global__ void kb_fg_solve(int n, int m, double* __restrict__ fg, const int* __restrict__ k,
+                            const int* __restrict__ cyc, int* __restrict__ on) {
+    const int st = fg_stride(m);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double* f = fg + (size_t)i * st;
+        const double* g = f + kFgG;
+        double* y = f + kFgG + (m + 1) + 2 * m;
+        const double* H = y + m;
+        const int ki = cyc[i] ? k[i] : 0;
+        for (int r = m - 1; r >= ki; --r) y[r] = 0.0;
+        for (int r = ki - 1; r >= 0; --r) {
+            double acc = g[r];
+            for (int c = r + 1; c < ki; ++c) acc -= H[(size_t)r * m + c] * y[c];
+            y[r] = acc / H[(size_t)r * m + r];
+        }
+        on[i] = cyc[i];
+    }
+}
+
+// beta_i (the fg slot 0) from the norms of a batched reduction
+__global__ void kb_fg_take_beta(int n, int m, const double* __restrict__ nrm, double* __restrict__ fg) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        fg[(size_t)i * fg_stride(m)] = nrm[i];
+}
+
+cudaError_t fg_launch_checked(cudaError_t e) { return count_launch(e == cudaSuccess ? cudaGetLastError() : e); }
+
+// One Arnoldi step of every active instance at column j = *col (all selectors through the device
+// counter, so the same launches serve every j): z_j = MG(v_j), w = G~ z_j, classical Gram-Schmidt
+// twice, v_{j+1} = w / |w|, then the scalar step on the device.
+cudaError_t b_arnoldi_step(pff_batch* b, bool mixed) {
+    const int n = b->n, m = b->m, F = b->Lmax;
+    cudaStream_t s = b->stream;
+    double* d_nrm = b->d_vals;
+    double* d_h = b->d_vals + n;
+    const int vj = bsel(BV_KV, kColJ), zj = bsel(BV_KZ, kColJ), vn = bsel(BV_KV, kColJ1);
+    if (mixed) {
+        const int tb = std::max(1, std::min(64, (n + 255) / 256));
+        kb_prec_subset<<<tb, 256, 0, s>>>(n, 0, b->d_on, b->d_save, b->d_prec);
+        BCK(fg_launch_checked(cudaSuccess));
+        BCK(b_vcycle_t<float>(b, vj, zj));
+        kb_prec_subset<<<tb, 256, 0, s>>>(n, 1, b->d_on, b->d_save, b->d_prec);
+        BCK(fg_launch_checked(cudaSuccess));
+        BCK(b_vcycle_t<double>(b, vj, zj));
+        kb_prec_subset<<<tb, 256, 0, s>>>(n, 2, b->d_on, b->d_save, b->d_prec);
+        BCK(fg_launch_checked(cudaSuccess));
+    } else {
+        BCK(b_vcycle(b, vj, zj));
+    }
+    BCK(b_apply(b, F, true, false, zj, vn, PHI_BITS_ALL));
+    BCK(bl_multidot(tab(b, F), n, -1, vn, b->d_part, m + 1, d_h, 2 * (m + 1), s, b->d_col));
+    BCK(bl_multi_axpy(tab(b, F), n, b->blocks[F], -1, d_h, 2 * (m + 1), vn, s, b->d_col));
+    BCK(bl_multidot(tab(b, F), n, -1, vn, b->d_part, m + 1, d_h + (m + 1), 2 * (m + 1), s, b->d_col));
+    BCK(bl_multi_axpy(tab(b, F), n, b->blocks[F], -1, d_h + (m + 1), 2 * (m + 1), vn, s, b->d_col));
+    BCK(bl_norm(tab(b, F), n, vn, b->d_part, d_nrm, s));
+    BCK(bl_axpby64(tab(b, F), n, b->blocks[F], d_nrm, vn, 0.0, vn, 1, s));
+    kb_fg_arnoldi<<<1, 256, 0, s>>>(n, m, d_h, d_nrm, b->d_fg, b->d_its, b->d_on, b->d_k, b->d_flags, b->d_prec,
+                                    b->d_col, b->d_count);
+    return fg_launch_checked(cudaSuccess);
+}
+
+void drop_step_graph(pff_batch* b) {
+    if (b->step_graph) cudaGraphExecDestroy(b->step_graph);
+    if (b->step_graph_mixed) cudaGraphExecDestroy(b->step_graph_mixed);
+    b->step_graph = b->step_graph_mixed = nullptr;
+    b->graph_key = -1;
+    b->graph_nodes = 0;
+}
+
+cudaError_t capture_step(pff_batch* b, bool mixed, cudaGraphExec_t* out, long long* nodes) {
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const long long c0 = launch_count();
+    cudaError_t e = b_arnoldi_step(b, mixed);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && !g) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    *nodes = launch_count() - c0;
+    add_launches(-*nodes);        // captured kernels run only when replayed
+    return e;
+}
+
+// The Arnoldi step, captured once into a CUDA graph (and once more with the V-cycle split by instance
+// precision) and replayed for every column, restart cycle and later solve of the batch: every
+// argument of its launches is fixed (descriptor tables, vector selectors, coefficient tables) or read
+// from device memory (column, flags, precisions).  Re-captured when the coarse solver's step count
+// changes (the shape of the V-cycle).  Direct launches on the legacy default stream, which cannot be
+// captured.
+cudaError_t b_run_step(pff_batch* b, bool mixed) {
+    if (!b->use_graphs || b->stream == nullptr) return b_arnoldi_step(b, mixed);
+    if ((b->step_graph || b->step_graph_mixed) && b->graph_key != b->coarse_k) drop_step_graph(b);
+    cudaGraphExec_t* ge = mixed ? &b->step_graph_mixed : &b->step_graph;
+    long long* nodes = mixed ? &b->graph_nodes_mixed : &b->graph_nodes;
+    if (!*ge) {
+        cudaError_t e = capture_step(b, mixed, ge, nodes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *ge = nullptr;
+            b->use_graphs = false;        // direct launches from now on
+            return b_arnoldi_step(b, mixed);
+        }
+        b->graph_key = b->coarse_k;
+    }
+    BCK(cudaGraphLaunch(*ge, b->stream));
+    add_launches(*nodes);
+    return cudaSuccess;
+}
+
+// solve G~ x = b per instance: b in T64[1], x in T64[2] (fine selectors).  The host launches the
+// steps and reads one counter per step (one step behind, so the GPU never waits for the host); every
+// scalar of the method stays on the device.
 pff_status b_fgmres(pff_batch* b, double rtol, int maxit, pff_solve_info* info) {
     const int n = b->n, m = b->m, F = b->Lmax;
     cudaStream_t s = b->stream;
     const int sb = bsel(BV_T64 + 1), sx = bsel(BV_T64 + 2), sw = bsel(BV_T64 + 0);
-    double* d_nrm = b->d_vals;                              // n
-    double* d_h = b->d_vals + n;                            // n * 2(m+1)  (h1 | h2)
-    double* d_y = d_h + (size_t)n * 2 * (m + 1);            // n * m
-    std::vector<double> beta0(n), beta(n), target(n), hv((size_t)n * 2 * (m + 1)), nrm(n);
-    std::vector<int> its(n, 0);
-    std::vector<char> all(n, 1);
+    double* d_nrm = b->d_vals;
+    // host mirror: [0] active after a cycle start, [1 + 2 (j & 1)] active and [2 + 2 (j & 1)] active with the
+    // FP64 V-cycle after step j (alternating slots), [5 ..) flags
+    int* hs = b->h_status;
+    const int base_prec = b->mg64 ? 64 : 32;
+    bool mixed = false;
+    for (int q = 1; q < 5; ++q) hs[q] = 0;
     auto fail = [&](cudaError_t e) {
         b->err = std::string("batched FGMRES: ") + cudaGetErrorString(e);
         return PFF_ECUDA;
@@ -479,142 +872,90 @@ pff_status b_fgmres(pff_batch* b, double rtol, int maxit, pff_solve_info* info) 
         cudaError_t e_ = (__VA_ARGS__);     \
         if (e_ != cudaSuccess) return fail(e_); \
     } while (0)
-    auto true_res = [&](std::vector<double>& out) -> cudaError_t {
+    const int tb = std::max(1, std::min(64, (n + 255) / 256));
+    // true residual of every instance -> beta (fg slot 0)
+    auto true_res = [&]() -> cudaError_t {
+        kb_set_flags<<<tb, 256, 0, s>>>(n, 1, b->d_on);
+        BCK(fg_launch_checked(cudaSuccess));
         BCK(b_apply(b, F, true, false, sx, sw, PHI_BITS_ALL));
         BCK(bl_sub<double>(tab(b, F), n, b->blocks[F], sb, sw, sw, s));
         BCK(bl_norm(tab(b, F), n, sw, b->d_part, d_nrm, s));
-        BCK(cudaMemcpyAsync(out.data(), d_nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        kb_fg_take_beta<<<tb, 256, 0, s>>>(n, m, d_nrm, b->d_fg);
+        return fg_launch_checked(cudaSuccess);
+    };
+    auto begin = [&](int first) -> cudaError_t {
+        kb_fg_begin<<<1, 256, 0, s>>>(n, m, maxit, rtol, first, base_prec, b->mg64 ? 0 : b->switch_its, b->d_fg,
+                                      b->d_its, b->d_cyc, b->d_on, b->d_k, b->d_flags, b->d_prec, b->d_col,
+                                      b->d_count);
+        BCK(fg_launch_checked(cudaSuccess));
+        BCK(cudaMemcpyAsync(hs, b->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BCK(cudaMemcpyAsync(hs + 5, b->d_flags, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
         return cudaStreamSynchronize(s);
     };
-    b->valid = all;
-    BKC(upload(b));
-    BKC(true_res(beta0));
-    for (int i = 0; i < n; ++i) {
-        if (!std::isfinite(beta0[i])) {
-            b->err = "non-finite initial residual in instance " + std::to_string(i);
-            return PFF_ENONFINITE;
-        }
-        target[i] = rtol * beta0[i];
-    }
-    beta = beta0;
-    std::vector<std::vector<double>> H(n), g(n), cs(n), sn(n);
-    bool first = true;
-    while (true) {
-        if (!first) {
-            b->valid = all;
-            BKC(upload(b));
-            BKC(true_res(beta));
-        }
-        first = false;
-        std::vector<char> act(n, 0);
-        int nact = 0;
-        for (int i = 0; i < n; ++i) {
-            if (!std::isfinite(beta[i])) {
-                b->err = "non-finite residual in instance " + std::to_string(i);
-                return PFF_ENONFINITE;
+    auto check_flags = [&](const char* what) -> bool {
+        for (int i = 0; i < n; ++i)
+            if (hs[5 + i]) {
+                b->err = std::string("non-finite ") + what + " in instance " + std::to_string(i);
+                set_all_on(b);
+                return true;
             }
-            act[i] = !(beta[i] <= target[i] || its[i] >= maxit || beta[i] == 0.0);
-            nact += act[i];
-        }
-        if (!nact) break;
-        b->valid = act;
-        BKC(upload(b));
-        BKC(bl_axpby64(tab(b, F), n, b->blocks[F], d_nrm, sw, 0.0, bsel(BV_KV, 0), 1, s));   // V0 = w / beta
-        std::vector<int> k(n, 0);
-        for (int i = 0; i < n; ++i) {
-            H[i].assign((size_t)(m + 1) * m, 0.0);
-            g[i].assign(m + 1, 0.0);
-            cs[i].assign(m, 0.0);
-            sn[i].assign(m, 0.0);
-            g[i][0] = beta[i];
-        }
-        std::vector<char> inner = act;
+        return false;
+    };
+    b->valid.assign(n, 1);
+    BKC(upload(b));
+    BKC(true_res());
+    BKC(begin(1));
+    if (check_flags("initial residual")) return PFF_ENONFINITE;
+    while (hs[0] > 0) {
+        // V_0 = w / beta on the active instances (w = b - G x from the true residual)
+        BKC(bl_axpby64(tab(b, F), n, b->blocks[F], d_nrm, sw, 0.0, bsel(BV_KV, 0), 1, s));
         for (int j = 0; j < m; ++j) {
-            BKC(b_vcycle(b, bsel(BV_KV, j), bsel(BV_KZ, j)));
-            BKC(b_apply(b, F, true, false, bsel(BV_KZ, j), bsel(BV_KV, j + 1), PHI_BITS_ALL));
-            const int vn = bsel(BV_KV, j + 1);
-            BKC(bl_multidot(tab(b, F), n, j + 1, vn, b->d_part, m + 1, d_h, 2 * (m + 1), s));
-            BKC(bl_multi_axpy(tab(b, F), n, b->blocks[F], j + 1, d_h, 2 * (m + 1), vn, s));
-            BKC(bl_multidot(tab(b, F), n, j + 1, vn, b->d_part, m + 1, d_h + (m + 1), 2 * (m + 1), s));
-            BKC(bl_multi_axpy(tab(b, F), n, b->blocks[F], j + 1, d_h + (m + 1), 2 * (m + 1), vn, s));
-            BKC(bl_norm(tab(b, F), n, vn, b->d_part, d_nrm, s));
-            BKC(bl_axpby64(tab(b, F), n, b->blocks[F], d_nrm, vn, 0.0, vn, 1, s));
-            BKC(cudaMemcpyAsync(hv.data(), d_h, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, s));
-            BKC(cudaMemcpyAsync(nrm.data(), d_nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+            BKC(b_run_step(b, mixed && !b->mg64));
+            BKC(cudaMemcpyAsync(hs + 1 + 2 * (j & 1), b->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BKC(cudaMemcpyAsync(hs + 2 + 2 * (j & 1), b->d_count + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BKC(cudaEventRecord(b->ev_step[j & 1], s));
+            if (j >= 1) {
+                BKC(cudaEventSynchronize(b->ev_step[(j - 1) & 1]));
+                if (hs[1 + 2 * ((j - 1) & 1)] == 0) break;   // every instance stopped at step j - 1
+                if (hs[2 + 2 * ((j - 1) & 1)] > 0) mixed = true;   // an instance switched to the FP64 V-cycle
+            }
+        }
+        if (hs[0] > 0 && !mixed) {
             BKC(cudaStreamSynchronize(s));
-            bool changed = false;
-            int left = 0;
-            for (int i = 0; i < n; ++i) {
-                if (!inner[i]) continue;
-                const double* hi = &hv[(size_t)i * 2 * (m + 1)];
-                std::vector<double>& Hi = H[i];
-                for (int r = 0; r <= j; ++r) Hi[(size_t)r * m + j] = hi[r] + hi[(m + 1) + r];
-                if (!std::isfinite(nrm[i])) {
-                    b->err = "non-finite Arnoldi norm in instance " + std::to_string(i);
-                    return PFF_ENONFINITE;
-                }
-                Hi[(size_t)(j + 1) * m + j] = nrm[i];
-                for (int r = 0; r < j; ++r) {
-                    const double t = cs[i][r] * Hi[(size_t)r * m + j] + sn[i][r] * Hi[(size_t)(r + 1) * m + j];
-                    Hi[(size_t)(r + 1) * m + j] = -sn[i][r] * Hi[(size_t)r * m + j] + cs[i][r] * Hi[(size_t)(r + 1) * m + j];
-                    Hi[(size_t)r * m + j] = t;
-                }
-                const double den = hypot(Hi[(size_t)j * m + j], Hi[(size_t)(j + 1) * m + j]);
-                cs[i][j] = Hi[(size_t)j * m + j] / den;
-                sn[i][j] = Hi[(size_t)(j + 1) * m + j] / den;
-                Hi[(size_t)j * m + j] = den;
-                Hi[(size_t)(j + 1) * m + j] = 0.0;
-                g[i][j + 1] = -sn[i][j] * g[i][j];
-                g[i][j] = cs[i][j] * g[i][j];
-                ++its[i];
-                k[i] = j + 1;
-                if (fabs(g[i][j + 1]) <= target[i] || its[i] >= maxit) {
-                    inner[i] = 0;
-                    changed = true;
-                } else {
-                    ++left;
-                }
-            }
-            if (!left) break;
-            if (changed) {
-                b->valid = inner;
-                BKC(upload(b));
-            }
+            // a switch decided in the last step of the cycle
+            for (int q = 0; q < 2; ++q)
+                if (hs[2 + 2 * q] > 0) mixed = true;
         }
-        // x += Z y for the instances of this cycle
-        std::vector<double> y((size_t)n * m, 0.0);
-        for (int i = 0; i < n; ++i) {
-            if (!act[i]) continue;
-            for (int r = k[i] - 1; r >= 0; --r) {
-                double acc = g[i][r];
-                for (int c = r + 1; c < k[i]; ++c) acc -= H[i][(size_t)r * m + c] * y[(size_t)i * m + c];
-                y[(size_t)i * m + r] = acc / H[i][(size_t)r * m + r];
-            }
-        }
-        b->valid = act;
-        BKC(upload(b));
-        BKC(cudaMemcpyAsync(d_y, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, s));
-        int kmax = 0;
-        for (int i = 0; i < n; ++i) kmax = std::max(kmax, act[i] ? k[i] : 0);
-        BKC(bl_gemv_add(tab(b, F), n, b->blocks[F], kmax, d_y, m, sx, s));
-        BKC(cudaStreamSynchronize(s));
+        kb_fg_solve<<<tb, 256, 0, s>>>(n, m, b->d_fg, b->d_k, b->d_cyc, b->d_on);
+        BKC(fg_launch_checked(cudaSuccess));
+        const int ldy = fg_stride(m);
+        BKC(bl_gemv_add(tab(b, F), n, b->blocks[F], m, b->d_fg + kFgG + (m + 1) + 2 * m, ldy, sx, s, b->d_k));
+        BKC(true_res());
+        BKC(begin(0));
+        if (check_flags("residual or Arnoldi norm")) return PFF_ENONFINITE;
     }
-    std::vector<double> res(n);
-    b->valid = all;
-    BKC(upload(b));
-    BKC(true_res(res));
+    BKC(set_all_on(b));
 #undef BKC
+    // final true residuals (fg slot 0), targets and iteration counts
+    std::vector<double> fgh((size_t)n * fg_stride(m));
+    std::vector<int> its(n);
+    if (cudaMemcpyAsync(fgh.data(), b->d_fg, sizeof(double) * fgh.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(its.data(), b->d_its, sizeof(int) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(cudaGetLastError());
     pff_status st = PFF_OK;
     for (int i = 0; i < n; ++i) {
-        const bool conv = res[i] <= target[i] * (1.0 + 1e-12) || beta0[i] == 0.0;
+        const double* f = &fgh[(size_t)i * fg_stride(m)];
+        const double res = f[0], target = f[1], res0 = f[2];
+        const bool conv = res <= target * (1.0 + 1e-12) || res0 == 0.0;
         if (info) {
             info[i].iterations = its[i];
-            info[i].res0 = beta0[i];
-            info[i].res_final = res[i];
+            info[i].res0 = res0;
+            info[i].res_final = res;
             info[i].converged = conv ? 1 : 0;
         }
-        if (!std::isfinite(res[i])) {
-            b->err = "non-finite final residual";
+        if (!std::isfinite(res)) {
+            b->err = "non-finite final residual in instance " + std::to_string(i);
             st = PFF_ENONFINITE;
         } else if (!conv && st == PFF_OK) {
             b->err = "batched FGMRES reached maxit";
@@ -622,6 +963,15 @@ pff_status b_fgmres(pff_batch* b, double rtol, int maxit, pff_solve_info* info) 
         }
     }
     return st;
+}
+
+void free_batch(pff_batch* b) {
+    drop_step_graph(b);
+    for (cudaEvent_t& e : b->ev_step)
+        if (e) cudaEventDestroy(e);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    for (void* p : b->allocs) cudaFree(p);
+    delete b;
 }
 
 pff_status b_fail(pff_batch* b, pff_status st, const std::string& msg) {
@@ -677,6 +1027,24 @@ extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int rest
         if (e == cudaSuccess) e = balloc(b, &b->d_part, (size_t)n * (restart + 2) * kBPartials * 2);
         if (e == cudaSuccess) e = balloc(b, &b->d_vals, (size_t)n * (12 + 4 * kMaxCG + 4 * b->Lmax + 4 * (restart + 2)));
         if (e == cudaSuccess) e = balloc(b, &b->d_seeds, (size_t)n);
+        if (e == cudaSuccess) e = balloc(b, &b->d_on, (size_t)n);
+        if (e == cudaSuccess) e = balloc(b, &b->d_cyc, (size_t)n);
+        if (e == cudaSuccess) e = balloc(b, &b->d_col, (size_t)4);
+        if (e == cudaSuccess) e = balloc(b, &b->d_its, (size_t)n);
+        if (e == cudaSuccess) e = balloc(b, &b->d_k, (size_t)n);
+        if (e == cudaSuccess) e = balloc(b, &b->d_flags, (size_t)n);
+        if (e == cudaSuccess) e = balloc(b, &b->d_count, (size_t)4);
+        if (e == cudaSuccess) e = balloc(b, &b->d_fg, (size_t)n * fg_stride(restart));
+        if (e == cudaSuccess) e = balloc(b, &b->d_prec, (size_t)n);
+        if (e == cudaSuccess) e = balloc(b, &b->d_save, (size_t)n);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * (size_t)(n + 5));
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev_step[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = q1_batched_prepare();
+        if (e == cudaSuccess) {
+            int dev = 0;
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+        }
         if (e == cudaSuccess) {
             std::vector<uint64_t> seeds(n);
             for (int i = 0; i < n; ++i) seeds[i] = b->hs[i]->prm.seed;
@@ -687,8 +1055,7 @@ extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int rest
     }
     if (st != PFF_OK) {
         cudaGetLastError();
-        for (void* p : b->allocs) cudaFree(p);
-        delete b;
+        free_batch(b);
         return st;
     }
     *out = b;
@@ -698,8 +1065,7 @@ extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int rest
 extern "C" pff_status pff_batch_destroy(pff_batch* b) {
     if (!b) return PFF_OK;
     cudaStreamSynchronize(b->stream);
-    for (void* p : b->allocs) cudaFree(p);
-    delete b;
+    free_batch(b);
     return PFF_OK;
 }
 
@@ -808,6 +1174,35 @@ extern "C" pff_status pff_batch_set_kernel_style(pff_batch* b, int style) {
     if (!b) return PFF_EINVAL;
     if (style < 0 || style > 2) return b_fail(b, PFF_EINVAL, "kernel style must be 0, 1 or 2");
     b->style = style;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_batch_set_precision_switch(pff_batch* b, int iterations) {
+    if (!b) return PFF_EINVAL;
+    if (iterations < 0) return b_fail(b, PFF_EINVAL, "iterations must be >= 0");
+    b->switch_its = iterations;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_batch_mg_precisions(pff_batch* b, int* precisions) {
+    if (!b || !precisions) return PFF_EINVAL;
+    BCUDA_OR_FAIL(b, cudaMemcpyAsync(precisions, b->d_prec, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream));
+    BCUDA_OR_FAIL(b, cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i)
+        if (precisions[i] != 32 && precisions[i] != 64) precisions[i] = b->mg64 ? 64 : 32;   // before any solve
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_batch_tuning(pff_batch* b, int level, int precision, int* style, int* ctas_per_sm,
+                                       double* ms) {
+    if (!b) return PFF_EINVAL;
+    if (precision != 32 && precision != 64) return b_fail(b, PFF_EINVAL, "precision must be 32 or 64");
+    if (level < -1 || level >= b->Lmax) return b_fail(b, PFF_EINVAL, "level out of range");
+    if (!b->tuned) return b_fail(b, PFF_ESTATE, "the batch has not been tuned (pff_batch_setup with style 0)");
+    const pff_batch::Tune& t = b->tune[(size_t)(level < 0 ? b->Lmax : level) * 2 + (precision == 64 ? 1 : 0)];
+    if (style) *style = t.style;
+    if (ctas_per_sm) *ctas_per_sm = t.cps;
+    if (ms) *ms = t.ms;
     return PFF_OK;
 }
 

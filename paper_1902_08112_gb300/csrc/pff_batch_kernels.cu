@@ -19,7 +19,7 @@ __device__ __forceinline__ bool belim(uint8_t m, int c, int dim, int phi_bits) {
 template <typename T>
 __global__ void kb_init_masked(const BLevel* __restrict__ L, int sx, int sy, int phi_bits, T elim_val) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nn = d.g.n_nodes, nd = n_dofs(d.g);
     const T* x = sx >= 0 ? bvec<T>(d, sx) : nullptr;
     T* y = bvec<T>(d, sy);
@@ -36,7 +36,7 @@ template <typename T>
 __global__ void kb_cheb(const BLevel* __restrict__ L, int sr, int st, int sd, int sx, const double* __restrict__ coef,
                         int first, int stn) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nd = n_dofs(d.g), nu = d.g.n_nodes * d.g.dim;
     const double* cf = coef + 4 * blockIdx.y;
     const T c1u = (T)cf[0], c1p = (T)cf[1], c2u = (T)cf[2], c2p = (T)cf[3];
@@ -71,7 +71,7 @@ __global__ void kb_cheb(const BLevel* __restrict__ L, int sr, int st, int sd, in
 template <typename T>
 __global__ void kb_sub(const BLevel* __restrict__ L, int sa, int sb, int sc) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nd = n_dofs(d.g);
     const T* a = bvec<T>(d, sa);
     const T* b = bvec<T>(d, sb);
@@ -82,7 +82,7 @@ __global__ void kb_sub(const BLevel* __restrict__ L, int sa, int sb, int sc) {
 template <typename T>
 __global__ void kb_copy(const BLevel* __restrict__ L, int ss, int sd, int block) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nd = n_dofs(d.g), nu = d.g.n_nodes * d.g.dim;
     const T* s = bvec<T>(d, ss);
     T* t = bvec<T>(d, sd);
@@ -97,7 +97,7 @@ __global__ void kb_copy(const BLevel* __restrict__ L, int ss, int sd, int block)
 template <typename Ti, typename To>
 __global__ void kb_convert(const BLevel* __restrict__ L, int ss, int sd, int mode) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nn = d.g.n_nodes, nd = n_dofs(d.g);
     const Ti* s = bvec<Ti>(d, ss);
     To* t = bvec<To>(d, sd);
@@ -114,7 +114,7 @@ __global__ void kb_convert(const BLevel* __restrict__ L, int ss, int sd, int mod
 __global__ void kb_axpby64(const BLevel* __restrict__ L, const double* __restrict__ a, int sx, double b, int sy,
                            int invert_a) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nd = n_dofs(d.g);
     double ai = a ? a[blockIdx.y] : 1.0;
     if (invert_a) ai = ai > 0.0 ? 1.0 / ai : 0.0;
@@ -138,7 +138,7 @@ template <typename T>
 __global__ void kb_restrict(const BLevel* __restrict__ Lc, const BLevel* __restrict__ Lf, int sf, int sc) {
     const BLevel& F = Lf[blockIdx.y];
     const BLevel& C = Lc[blockIdx.y];
-    if (!F.valid || !C.valid) return;
+    if (!bon(F) || !bon(C)) return;
     const Geom& gc = C.g;
     const Geom& gf = F.g;
     const T* rf = bvec<T>(F, sf);
@@ -173,7 +173,7 @@ template <typename T>
 __global__ void kb_prolongate_add(const BLevel* __restrict__ Lc, const BLevel* __restrict__ Lf, int sc, int sf) {
     const BLevel& F = Lf[blockIdx.y];
     const BLevel& C = Lc[blockIdx.y];
-    if (!F.valid || !C.valid) return;
+    if (!bon(F) || !bon(C)) return;
     const Geom& gc = C.g;
     const Geom& gf = F.g;
     const T* ec = bvec<T>(C, sc);
@@ -242,7 +242,7 @@ template <typename T>
 __global__ void kb_dots2_partial(const BLevel* __restrict__ L, int sa, int sb, double* __restrict__ part) {
     const BLevel& d = L[blockIdx.y];
     double su = 0.0, sp = 0.0;
-    if (d.valid) {
+    if (bon(d)) {
         const int64_t nd = n_dofs(d.g), nu = d.g.n_nodes * d.g.dim;
         const T* a = bvec<T>(d, sa);
         const T* b = bvec<T>(d, sb);
@@ -274,18 +274,22 @@ __global__ void kb_dots2_final(const double* __restrict__ part, int P, double* _
 
 // FGMRES on the finest levels: h[inst * ldh + j] = V_j . w for j < k (two stages)
 // <V_j, w> for j < k, eight basis vectors per pass over w (their sums kept in registers)
-__global__ void kb_multidot_partial(const BLevel* __restrict__ L, int k, int sw, double* __restrict__ part, int kmax) {
+// k < 0: k = (*kcol) + 1, the column counter of the batch (captured Arnoldi steps)
+__global__ void kb_multidot_partial(const BLevel* __restrict__ L, int k, const int* __restrict__ kcol, int sw,
+                                    double* __restrict__ part, int kmax) {
     constexpr int G = 8;
     const BLevel& d = L[blockIdx.y];
-    const int64_t nd = d.valid ? n_dofs(d.g) : 0;
-    const double* w = d.valid ? bvec<double>(d, sw) : nullptr;
-    const double* V = d.valid ? bvec<double>(d, bsel(BV_KV, 0)) : nullptr;
+    if (k < 0) k = *kcol + 1;
+    const bool on = bon(d);
+    const int64_t nd = on ? n_dofs(d.g) : 0;
+    const double* w = on ? bvec<double>(d, sw) : nullptr;
+    const double* V = on ? bvec<double>(d, bsel(BV_KV, 0)) : nullptr;
     for (int j0 = 0; j0 < k; j0 += G) {
         const int kk = min(G, k - j0);
         double s[G];
 #pragma unroll
         for (int t = 0; t < G; ++t) s[t] = 0.0;
-        if (d.valid) {
+        if (on) {
             BSTRIDE(i, nd) {
                 const double wi = w[i];
 #pragma unroll
@@ -299,9 +303,10 @@ __global__ void kb_multidot_partial(const BLevel* __restrict__ L, int k, int sw,
         }
     }
 }
-__global__ void kb_multidot_final(const double* __restrict__ part, int P, int k, int kmax, double* __restrict__ h,
-                                  int ldh) {
+__global__ void kb_multidot_final(const double* __restrict__ part, int P, int k, const int* __restrict__ kcol, int kmax,
+                                  double* __restrict__ h, int ldh) {
     const int wid = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (k < 0) k = *kcol + 1;
     for (int j = wid; j < k; j += nw) {
         double s = 0.0;
         for (int i = l; i < P; i += 32) s += part[((int64_t)blockIdx.x * kmax + j) * P + i];
@@ -309,9 +314,11 @@ __global__ void kb_multidot_final(const double* __restrict__ part, int P, int k,
         if (l == 0) h[(int64_t)blockIdx.x * ldh + j] = s;
     }
 }
-__global__ void kb_multi_axpy(const BLevel* __restrict__ L, int k, const double* __restrict__ h, int ldh, int sw) {
+__global__ void kb_multi_axpy(const BLevel* __restrict__ L, int k, const int* __restrict__ kcol,
+                              const double* __restrict__ h, int ldh, int sw) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
+    if (k < 0) k = *kcol + 1;
     const int64_t nd = n_dofs(d.g);
     double* w = bvec<double>(d, sw);
     const double* hh = h + (int64_t)blockIdx.y * ldh;
@@ -325,7 +332,7 @@ __global__ void kb_multi_axpy(const BLevel* __restrict__ L, int k, const double*
 __global__ void kb_norm_partial(const BLevel* __restrict__ L, int sw, double* __restrict__ part) {
     const BLevel& d = L[blockIdx.y];
     double s = 0.0;
-    if (d.valid) {
+    if (bon(d)) {
         const int64_t nd = n_dofs(d.g);
         const double* w = bvec<double>(d, sw);
         BSTRIDE(i, nd) s += w[i] * w[i];
@@ -340,9 +347,12 @@ __global__ void kb_norm_final(const double* __restrict__ part, int P, double* __
     if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
 }
 // x += Z y_inst
-__global__ void kb_gemv_add(const BLevel* __restrict__ L, int k, const double* __restrict__ y, int ldy, int sx) {
+// kk (nullable): per-instance k
+__global__ void kb_gemv_add(const BLevel* __restrict__ L, int k, const int* __restrict__ kk, const double* __restrict__ y,
+                            int ldy, int sx) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
+    if (kk) k = kk[blockIdx.y];
     const int64_t nd = n_dofs(d.g);
     double* x = bvec<double>(d, sx);
     const double* yy = y + (int64_t)blockIdx.y * ldy;
@@ -359,7 +369,7 @@ __global__ void kb_gemv_add(const BLevel* __restrict__ L, int k, const double* _
 template <typename T>
 __global__ void kb_cg_r(const BLevel* __restrict__ L, int sr, int sq, int sz, const double* __restrict__ alpha2) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nd = n_dofs(d.g), nu = d.g.n_nodes * d.g.dim;
     const T au = (T)alpha2[2 * blockIdx.y], ap = (T)alpha2[2 * blockIdx.y + 1];
     T* r = bvec<T>(d, sr);
@@ -375,7 +385,7 @@ __global__ void kb_cg_r(const BLevel* __restrict__ L, int sr, int sq, int sz, co
 template <typename T>
 __global__ void kb_cg_p(const BLevel* __restrict__ L, int sp, int sz, const double* __restrict__ beta2) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nd = n_dofs(d.g), nu = d.g.n_nodes * d.g.dim;
     const T bu = (T)beta2[2 * blockIdx.y], bp = (T)beta2[2 * blockIdx.y + 1];
     T* p = bvec<T>(d, sp);
@@ -391,7 +401,7 @@ __device__ __forceinline__ uint64_t bsplitmix64(uint64_t x) {
 template <typename T>
 __global__ void kb_start_vector(const BLevel* __restrict__ L, int sv, const uint64_t* __restrict__ seeds, int level) {
     const BLevel& d = L[blockIdx.y];
-    if (!d.valid) return;
+    if (!bon(d)) return;
     const int64_t nn = d.g.n_nodes, nd = n_dofs(d.g);
     T* v = bvec<T>(d, sv);
     const uint64_t seed = seeds[blockIdx.y];
@@ -455,14 +465,15 @@ cudaError_t bl_dots2(const BLevel* L, int n, int sa, int sb, double* part, doubl
     return count_launch(cudaGetLastError());
 }
 cudaError_t bl_multidot(const BLevel* L, int n, int k, int sw, double* part, int kmax, double* h, int ldh,
-                        cudaStream_t s) {
-    kb_multidot_partial<<<bgrid(kBPartials, n), kT, 0, s>>>(L, k, sw, part, kmax);
+                        cudaStream_t s, const int* kcol) {
+    kb_multidot_partial<<<bgrid(kBPartials, n), kT, 0, s>>>(L, k, kcol, sw, part, kmax);
     count_launch(cudaGetLastError());
-    kb_multidot_final<<<n, 1024, 0, s>>>(part, kBPartials, k, kmax, h, ldh);
+    kb_multidot_final<<<n, 1024, 0, s>>>(part, kBPartials, k, kcol, kmax, h, ldh);
     return count_launch(cudaGetLastError());
 }
-cudaError_t bl_multi_axpy(const BLevel* L, int n, int blocks, int k, const double* h, int ldh, int sw, cudaStream_t s) {
-    kb_multi_axpy<<<bgrid(blocks, n), kT, 0, s>>>(L, k, h, ldh, sw);
+cudaError_t bl_multi_axpy(const BLevel* L, int n, int blocks, int k, const double* h, int ldh, int sw, cudaStream_t s,
+                          const int* kcol) {
+    kb_multi_axpy<<<bgrid(blocks, n), kT, 0, s>>>(L, k, kcol, h, ldh, sw);
     return count_launch(cudaGetLastError());
 }
 cudaError_t bl_norm(const BLevel* L, int n, int sw, double* part, double* out, cudaStream_t s) {
@@ -471,8 +482,9 @@ cudaError_t bl_norm(const BLevel* L, int n, int sw, double* part, double* out, c
     kb_norm_final<<<n, kT, 0, s>>>(part, kBPartials, out);
     return count_launch(cudaGetLastError());
 }
-cudaError_t bl_gemv_add(const BLevel* L, int n, int blocks, int k, const double* y, int ldy, int sx, cudaStream_t s) {
-    kb_gemv_add<<<bgrid(blocks, n), kT, 0, s>>>(L, k, y, ldy, sx);
+cudaError_t bl_gemv_add(const BLevel* L, int n, int blocks, int k, const double* y, int ldy, int sx, cudaStream_t s,
+                        const int* kk) {
+    kb_gemv_add<<<bgrid(blocks, n), kT, 0, s>>>(L, k, kk, y, ldy, sx);
     return count_launch(cudaGetLastError());
 }
 template <typename T>

@@ -26,11 +26,15 @@ template <typename T>
 cudaError_t bl_prolongate_add(const BLevel* Lc, const BLevel* Lf, int n, int blocks, int sc, int sf, cudaStream_t s);
 template <typename T>
 cudaError_t bl_dots2(const BLevel* L, int n, int sa, int sb, double* part, double* out, cudaStream_t s);
+// k < 0: the number of basis vectors is (*kcol) + 1 (device column counter)
 cudaError_t bl_multidot(const BLevel* L, int n, int k, int sw, double* part, int kmax, double* h, int ldh,
-                        cudaStream_t s);
-cudaError_t bl_multi_axpy(const BLevel* L, int n, int blocks, int k, const double* h, int ldh, int sw, cudaStream_t s);
+                        cudaStream_t s, const int* kcol = nullptr);
+cudaError_t bl_multi_axpy(const BLevel* L, int n, int blocks, int k, const double* h, int ldh, int sw, cudaStream_t s,
+                          const int* kcol = nullptr);
 cudaError_t bl_norm(const BLevel* L, int n, int sw, double* part, double* out, cudaStream_t s);
-cudaError_t bl_gemv_add(const BLevel* L, int n, int blocks, int k, const double* y, int ldy, int sx, cudaStream_t s);
+// kk (nullable): per-instance number of columns
+cudaError_t bl_gemv_add(const BLevel* L, int n, int blocks, int k, const double* y, int ldy, int sx, cudaStream_t s,
+                        const int* kk = nullptr);
 template <typename T>
 cudaError_t bl_cg_r(const BLevel* L, int n, int blocks, int sr, int sq, int sz, const double* alpha2, cudaStream_t s);
 template <typename T>

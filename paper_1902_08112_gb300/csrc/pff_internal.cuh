@@ -173,6 +173,8 @@ cudaError_t launch_face_sum(const Geom& g, int axis, int side, int comp, const d
                             cudaStream_t s);
 cudaError_t launch_extrapolate(int64_t n, const double* phi_nm1, const double* phi_nm2, double* out,
                                cudaStream_t s);
+// U = u_dirichlet on the Dirichlet displacement DoFs of mask (prescribed boundary values)
+cudaError_t launch_lift_dirichlet(const Geom& g, const uint8_t* mask, const double* ud, double* U, cudaStream_t s);
 cudaError_t launch_active_delta(const Geom& g, const double* U, const double* phi_old,
                                 const uint8_t* mask, double* delta, cudaStream_t s);
 
@@ -211,6 +213,8 @@ struct pff_hierarchy {
     double* R = nullptr;             // residual (n_dofs)
     double* tmp64[4] = {nullptr, nullptr, nullptr, nullptr};  // fine FP64 temporaries
     uint8_t* prev_active = nullptr;
+    double* udir = nullptr;          // prescribed displacement values on Dirichlet DoFs (dim * n_nodes), or none
+    bool has_udir = false;
     int* d_counts = nullptr;         // device counters
     double* d_scal = nullptr;        // device scalars (dots, CG coefficients)
     // setup runs the levels concurrently: one stream per level, a private region of CG scalars

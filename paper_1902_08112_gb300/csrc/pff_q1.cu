@@ -1217,35 +1217,47 @@ struct TileOf {
     static constexpr int TZ = LANES ? LaneTile<DIM>::TZ : Q1Tile<DIM, S>::TZ;
 };
 
+// instance of flattened tile b: the last i with tile_start[i] <= b
+__device__ __forceinline__ int tile_instance(const int* __restrict__ tile_start, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_start[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent: each CTA loops over the flattened tiles of all instances of a level (stride gridDim.x);
+// instances switched off (BLevel::on) are skipped.
 template <int DIM, typename S, bool BLOCKDIAG, bool LANES>
 __global__ void __launch_bounds__(LANES ? 256 : Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ,
                                   LANES ? 1 : Q1Tile<DIM, S>::MINB)
 k_q1_apply_batched(const BLevel* __restrict__ L, const int* __restrict__ tile_start, int n, int sx, int sy,
                    int phi_bits) {
-    // instance = last i with tile_start[i] <= blockIdx.x
-    int lo = 0, hi = n - 1;
-    const int b = blockIdx.x;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tile_start[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    const BLevel& d = L[lo];
     using St = typename Scalar<S>::storage;
     using QT = typename QData<S>::type;
     using TT = TileOf<DIM, S, LANES>;
-    Q1ApplyArgs<St, QT> a;
-    a.g = d.g;
-    a.qd = sizeof(St) == 8 ? reinterpret_cast<const QT*>(d.qpd64) : reinterpret_cast<const QT*>(d.qpd32);
-    a.x = bvec<St>(d, sx);
-    a.y = bvec<St>(d, sy);
-    a.mask = d.mask;
-    a.phi_bits = phi_bits;
-    a.k = d.k;
-    const int local = b - tile_start[lo];
-    const int tx = (d.g.nc[0] + TT::TX - 1) / TT::TX, ty = (d.g.nc[1] + TT::TY - 1) / TT::TY;
-    const int bx = local % tx, by = (local / tx) % ty, bz = local / (tx * ty);
-    if constexpr (LANES) q1_direct_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);   // atomic lanes, no barrier
-    else q1_apply_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz, &d.k);
+    const int total = tile_start[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = tile_instance(tile_start, n, b);
+        const BLevel& d = L[i];
+        if (bon(d)) {
+            Q1ApplyArgs<St, QT> a;
+            a.g = d.g;
+            a.qd = sizeof(St) == 8 ? reinterpret_cast<const QT*>(d.qpd64) : reinterpret_cast<const QT*>(d.qpd32);
+            a.x = bvec<St>(d, sx);
+            a.y = bvec<St>(d, sy);
+            a.mask = d.mask;
+            a.phi_bits = phi_bits;
+            a.k = d.k;
+            const int local = b - tile_start[i];
+            const int tx = (d.g.nc[0] + TT::TX - 1) / TT::TX, ty = (d.g.nc[1] + TT::TY - 1) / TT::TY;
+            const int bx = local % tx, by = (local / tx) % ty, bz = local / (tx * ty);
+            if constexpr (LANES) q1_direct_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz);   // atomic lanes, no barrier
+            else q1_apply_tile<DIM, S, BLOCKDIAG>(a, bx, by, bz, &d.k);
+        }
+        if constexpr (!LANES) __syncthreads();   // the next tile reuses the shared-memory stage
+    }
 }
 
 int q1_tiles(const Geom& g, bool fp64, bool lanes) {
@@ -1264,9 +1276,9 @@ int q1_tiles(const Geom& g, bool fp64, bool lanes) {
 }
 
 template <int DIM, typename S, bool BD, bool LANES>
-static void launch_b(const BLevel* L, const int* ts, int n, int total, int sx, int sy, int pb, cudaStream_t s) {
+static void launch_b(const BLevel* L, const int* ts, int n, int grid, int sx, int sy, int pb, cudaStream_t s) {
     constexpr int threads = LANES ? 256 : Q1Tile<DIM, S>::TX * Q1Tile<DIM, S>::TY * Q1Tile<DIM, S>::TZ;
-    k_q1_apply_batched<DIM, S, BD, LANES><<<total, threads, 0, s>>>(L, ts, n, sx, sy, pb);
+    k_q1_apply_batched<DIM, S, BD, LANES><<<grid, threads, 0, s>>>(L, ts, n, sx, sy, pb);
 }
 
 template <typename S>
@@ -1283,31 +1295,32 @@ template <typename S, bool BLOCKDIAG>
 __global__ void __launch_bounds__(128, 4)
 k_q1_apply_batched_cell(const BLevel* __restrict__ L, const int* __restrict__ tile_start, int n, int sx, int sy,
                         int phi_bits) {
-    int lo = 0, hi = n - 1;
-    const int b = blockIdx.x;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tile_start[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    const BLevel& d = L[lo];
     using St = typename Scalar<S>::storage;
     using QT = typename QData<S>::type;
-    Q1ApplyArgs<St, QT> a;
-    a.g = d.g;
-    a.qd = sizeof(St) == 8 ? reinterpret_cast<const QT*>(d.qpd64) : reinterpret_cast<const QT*>(d.qpd32);
-    a.x = bvec<St>(d, sx);
-    a.y = bvec<St>(d, sy);
-    a.mask = d.mask;
-    a.phi_bits = phi_bits;
-    const int local = b - tile_start[lo];
-    const int tx = (d.g.nc[0] + CellTile::TX - 1) / CellTile::TX, ty = (d.g.nc[1] + CellTile::TY - 1) / CellTile::TY;
     extern __shared__ __align__(16) unsigned char cell_smem[];
-    q1_cell_tile<S, BLOCKDIAG>(a, d.k, local % tx, (local / tx) % ty, local / (tx * ty), cell_smem);
+    const int total = tile_start[n];
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = tile_instance(tile_start, n, b);
+        const BLevel& d = L[i];
+        if (bon(d)) {
+            Q1ApplyArgs<St, QT> a;
+            a.g = d.g;
+            a.qd = sizeof(St) == 8 ? reinterpret_cast<const QT*>(d.qpd64) : reinterpret_cast<const QT*>(d.qpd32);
+            a.x = bvec<St>(d, sx);
+            a.y = bvec<St>(d, sy);
+            a.mask = d.mask;
+            a.phi_bits = phi_bits;
+            const int local = b - tile_start[i];
+            const int tx = (d.g.nc[0] + CellTile::TX - 1) / CellTile::TX, ty = (d.g.nc[1] + CellTile::TY - 1) / CellTile::TY;
+            q1_cell_tile<S, BLOCKDIAG>(a, d.k, local % tx, (local / tx) % ty, local / (tx * ty), cell_smem);
+        }
+        __syncthreads();   // the next tile reuses the shared-memory stage
+    }
 }
 
+// dynamic shared memory above 48 KB needs the attribute once per device (before any stream capture)
 template <typename S, bool BD>
-static cudaError_t launch_batched_cell(const BLevel* L, const int* ts, int n, int total, int sx, int sy, int pb,
-                                       cudaStream_t s) {
+static cudaError_t batched_cell_attr() {
     static bool done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1318,7 +1331,47 @@ static cudaError_t launch_batched_cell(const BLevel* L, const int* ts, int n, in
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) done[dev] = true;
     }
-    k_q1_apply_batched_cell<S, BD><<<total, CellTile::TX * CellTile::TY * CellTile::TZ, cell_smem_bytes<S>(), s>>>(
+    return cudaSuccess;
+}
+
+cudaError_t q1_batched_prepare() {
+    cudaError_t e = batched_cell_attr<df64, false>();
+    if (e == cudaSuccess) e = batched_cell_attr<df64, true>();
+    if (e == cudaSuccess) e = batched_cell_attr<float, false>();
+    if (e == cudaSuccess) e = batched_cell_attr<float, true>();
+    return e;
+}
+
+int q1_batched_ctas_per_sm(int dim, bool fp64, bool cell) {
+    int nb = 0;
+    cudaError_t e;
+    if (cell && dim == 3) {
+        if (fp64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_q1_apply_batched_cell<df64, false>, 128,
+                                                                    cell_smem_bytes<df64>());
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_q1_apply_batched_cell<float, false>, 128,
+                                                               cell_smem_bytes<float>());
+    } else if (dim == 3) {
+        if (fp64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_q1_apply_batched<3, df64, false, true>, 256, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_q1_apply_batched<3, float, false, false>,
+                                                               Q1Tile<3, float>::TX * Q1Tile<3, float>::TY * Q1Tile<3, float>::TZ, 0);
+    } else {
+        if (fp64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_q1_apply_batched<2, df64, false, true>, 256, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_q1_apply_batched<2, float, false, false>,
+                                                               Q1Tile<2, float>::TX * Q1Tile<2, float>::TY, 0);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+template <typename S, bool BD>
+static cudaError_t launch_batched_cell(const BLevel* L, const int* ts, int n, int grid, int sx, int sy, int pb,
+                                       cudaStream_t s) {
+    cudaError_t e = batched_cell_attr<S, BD>();
+    if (e != cudaSuccess) return e;
+    k_q1_apply_batched_cell<S, BD><<<grid, CellTile::TX * CellTile::TY * CellTile::TZ, cell_smem_bytes<S>(), s>>>(
         L, ts, n, sx, sy, pb);
     return count_launch(cudaGetLastError());
 }
@@ -1330,8 +1383,9 @@ bool q1_cell_tiles_match_f32() {
 
 cudaError_t launch_q1_apply_batched(int dim, bool fp64, bool blockdiag, bool lanes, const BLevel* L, int n,
                                     const int* tile_start, int total_tiles, int sx, int sy, int phi_bits,
-                                    cudaStream_t s, bool cell) {
+                                    cudaStream_t s, bool cell, int max_ctas) {
     if (total_tiles <= 0) return cudaSuccess;
+    if (max_ctas > 0 && total_tiles > max_ctas) total_tiles = max_ctas;   // persistent grid
     if (cell && dim == 3) {
         if (fp64) return blockdiag ? launch_batched_cell<df64, true>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s)
                                    : launch_batched_cell<df64, false>(L, tile_start, n, total_tiles, sx, sy, phi_bits, s);

@@ -612,6 +612,22 @@ cudaError_t launch_active_set(const Geom& g, const double* R, const double* M, c
     return count_launch(cudaGetLastError());
 }
 
+// U_c(n) = g_c(n) on the displacement DoFs clamped by the mask (Dirichlet bits): the state takes the
+// prescribed boundary values, so that the Newton increments vanish there (Algorithm 1 with
+// inhomogeneous Dirichlet data)
+__global__ void k_lift_dirichlet(Geom g, const uint8_t* __restrict__ mask, const double* __restrict__ ud,
+                                 double* __restrict__ U) {
+    const int64_t nn = g.n_nodes, nu = nn * g.dim;
+    GRID_STRIDE(i, nu) {
+        const int c = dof_comp(i, nn);
+        if ((mask[i - c * nn] >> c) & 1) U[i] = ud[i];
+    }
+}
+cudaError_t launch_lift_dirichlet(const Geom& g, const uint8_t* mask, const double* ud, double* U, cudaStream_t s) {
+    k_lift_dirichlet<<<grid_for((int64_t)g.dim * g.n_nodes), kThreads, 0, s>>>(g, mask, ud, U);
+    return count_launch(cudaGetLastError());
+}
+
 // delta = phi_old - phi on active phi DoFs, 0 elsewhere
 __global__ void k_active_delta(Geom g, const double* __restrict__ U, const double* __restrict__ phi_old,
                                const uint8_t* __restrict__ mask, double* __restrict__ delta) {

@@ -64,7 +64,8 @@ SIGNATURES = {
     "pff_set_params": (_I, [_VP, ctypes.POINTER(Params)]),
     "pff_set_modulus": (_I, [_VP, _VP]),
     "pff_set_kernel_variant": (_I, [_VP, _I]),
-    "pff_set_state": (_I, [_VP, _VP, _VP, _VP]),
+    "pff_set_state": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "pff_set_dirichlet_values": (_I, [_VP, _VP]),
     "pff_set_active_set": (_I, [_VP, _VP]),
     "pff_get_active_set": (_I, [_VP, _VP]),
     "pff_update_active_set": (_I, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -98,6 +99,10 @@ SIGNATURES = {
     "pff_batch_newton_step": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(NewtonInfo)]),
     "pff_batch_apply_jacobian": (_I, [_VP, _I, _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "pff_batch_set_kernel_style": (_I, [_VP, _I]),
+    "pff_batch_set_precision_switch": (_I, [_VP, _I]),
+    "pff_batch_mg_precisions": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "pff_batch_tuning": (_I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_double)]),
     "pff_batch_last_error": (ctypes.c_char_p, [_VP]),
     "pff_fp32_fma_tflops": (_I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "pff_launch_count": (ctypes.c_longlong, []),
@@ -216,8 +221,15 @@ def set_kernel_variant(h, variant: int):
     return _check(h, load().pff_set_kernel_variant(h, variant), "pff_set_kernel_variant")
 
 
-def set_state(h, U, phi_old, phi_tilde):
-    return _check(h, load().pff_set_state(h, _ptr(U), _ptr(phi_old), _ptr(phi_tilde)), "pff_set_state")
+def set_state(h, U, phi_old, phi_tilde, u_dirichlet=None):
+    """u_dirichlet: optional device tensor of prescribed displacements (dim * n_nodes or n_dofs entries,
+    the layout of U), read on the Dirichlet displacement DoFs only."""
+    return _check(h, load().pff_set_state(h, _ptr(U), _ptr(phi_old), _ptr(phi_tilde), _ptr(u_dirichlet)),
+                  "pff_set_state")
+
+
+def set_dirichlet_values(h, u_dirichlet):
+    return _check(h, load().pff_set_dirichlet_values(h, _ptr(u_dirichlet)), "pff_set_dirichlet_values")
 
 
 def set_active_set(h, active):
@@ -409,6 +421,24 @@ def batch_apply_jacobian(b, level, precision, xs, ys):
 
 def batch_set_kernel_style(b, style: int):
     return _bcheck(b, load().pff_batch_set_kernel_style(b, style), "pff_batch_set_kernel_style")
+
+
+def batch_set_precision_switch(b, iterations: int):
+    return _bcheck(b, load().pff_batch_set_precision_switch(b, int(iterations)), "pff_batch_set_precision_switch")
+
+
+def batch_mg_precisions(b, n: int):
+    out = (ctypes.c_int * n)()
+    _bcheck(b, load().pff_batch_mg_precisions(b, out), "pff_batch_mg_precisions")
+    return list(out)
+
+
+def batch_tuning(b, level: int, precision: int):
+    """(style, ctas_per_sm, ms) chosen by the batch's autotuner for a level (-1: finest) and precision."""
+    st, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _bcheck(b, load().pff_batch_tuning(b, level, precision, ctypes.byref(st), ctypes.byref(c), ctypes.byref(ms)),
+            "pff_batch_tuning")
+    return st.value, c.value, ms.value
 
 
 def batch_last_error(b) -> str:

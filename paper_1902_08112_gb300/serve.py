@@ -59,10 +59,13 @@ class PffBackend:
         self.dev = torch.device(device)
         self.stream = torch.cuda.Stream(device=self.dev)
         self.restart = restart
+        self._batch, self._batch_key = None, None
+        self.batches_built = 0
 
     def mesh(self, w):
         return self.pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi,
-                                  dirichlet_faces=w.dirichlet_faces, cell_mask=w.cell_mask())
+                                  dirichlet_faces=w.dirichlet_faces, cell_mask=w.cell_mask(),
+                                  dirichlet_mask=w.dirichlet_mask())
 
     def bytes_for(self, w) -> int:
         return self.pff.hierarchy_bytes(self.mesh(w), self.restart) + 3 * w.n_dofs * 8
@@ -80,26 +83,41 @@ class PffBackend:
         self.stream.synchronize()
         return {"h": h, "U": U, "phi_old": phi_old, "w": w}
 
-    def start_load_step(self, inst, pressure):
+    def start_load_step(self, inst, pressure, frac=1.0):
+        """Load step at the fraction 'frac' of the request's ramp: phi_old := phi, the pressure p_n and, for
+        displacement-driven instances, the prescribed boundary displacements of this step."""
         w = inst["w"]
         nn = w.n_nodes
+        ud = w.u_dirichlet(frac)
         with self.torch.cuda.stream(self.stream):
             inst["phi_old"].copy_(inst["U"][w.dim * nn:])
+            inst["ud"] = self.torch.from_numpy(ud).to(self.dev) if ud is not None else None
         self.pff.set_params(inst["h"], self.params(w, pressure))
-        self.pff.set_state(inst["h"], inst["U"], inst["phi_old"], inst["phi_old"])
+        self.pff.set_state(inst["h"], inst["U"], inst["phi_old"], inst["phi_old"], inst["ud"])
 
     def newton(self, insts):
-        b = self.pff.batch_create([i["h"] for i in insts], self.restart)
-        try:
-            return self.pff.batch_newton_step(b, [i["U"] for i in insts], allow_noconv=True)
-        finally:
-            self.pff.batch_destroy(b)
+        """One batched Newton step.  The batch (descriptor tables, device FGMRES state, captured Arnoldi
+        graph, tuned kernels) is kept across ticks and rebuilt only when the set of instances changes."""
+        key = tuple(i["h"].value for i in insts)
+        if self._batch is None or self._batch_key != key:
+            self.release()
+            self._batch = self.pff.batch_create([i["h"] for i in insts], self.restart)
+            self._batch_key = key
+            self.batches_built += 1
+        return self.pff.batch_newton_step(self._batch, [i["U"] for i in insts], allow_noconv=True)
+
+    def release(self):
+        if self._batch is not None:
+            self.pff.batch_destroy(self._batch)
+        self._batch, self._batch_key = None, None
 
     def fetch(self, inst):
         self.stream.synchronize()
         return inst["U"].cpu().numpy()
 
     def destroy(self, inst):
+        if self._batch_key is not None and inst["h"].value in self._batch_key:
+            self.release()        # the batch is a view over its hierarchies: drop it first
         self.pff.destroy_hierarchy(inst["h"])
 
 
@@ -145,6 +163,10 @@ class Server:
     def _pressure(self, req, step):
         return req.workload.pressure * step / req.load_steps
 
+    def _start(self, slot):
+        req, step = slot["req"], slot["step"]
+        self.backend.start_load_step(slot["inst"], self._pressure(req, step), frac=step / req.load_steps)
+
     def _admit(self):
         admitted = []
         while self.waiting and len(self.active) < self.max_active:
@@ -156,8 +178,8 @@ class Server:
                 break
             self.waiting.pop(0)
             inst = self.backend.create(req.workload, self._pressure(req, 1))
-            self.backend.start_load_step(inst, self._pressure(req, 1))
             slot = {"req": req, "inst": inst, "bytes": need, "step": 1, "newton": 0, "t_step": self.now()}
+            self._start(slot)
             self.active.append(slot)
             self.used += need
             self.results[req.rid].admitted = self.now()
@@ -190,7 +212,7 @@ class Server:
                 s["step"] += 1
                 s["newton"] = 0
                 s["t_step"] = t1
-                self.backend.start_load_step(s["inst"], self._pressure(s["req"], s["step"]))
+                self._start(s)
                 keep.append(s)
             else:
                 res.U = self.backend.fetch(s["inst"])
@@ -233,17 +255,31 @@ def summarize(results: dict, wall: float) -> dict:
 
 
 def poisson_requests(count: int, rate_per_s: float, sizes=(16, 24, 32), load_steps=2, seed: int = W.SEED,
-                     coarsest: int = 4, lshape_every: int = 0, lshape_sizes=(16, 32)) -> list:
-    """Seeded Poisson arrivals of random pressurised-crack instances (the batch recipe); with
-    lshape_every = k every k-th request is a 3D L-shaped panel (edge 2^j cells, j from lshape_sizes)."""
+                     coarsest: int = 4, lshape_every: int = 0, lshape_sizes=(16, 32, 64, 128),
+                     lshape_steps: int = 20) -> list:
+    """Seeded Poisson arrivals of random pressurised-crack instances (the batch recipe, 'load_steps'
+    pressure steps each); with lshape_every = k every k-th request is a 3D L-shaped panel (edge n cells,
+    n from lshape_sizes) loaded by a prescribed displacement ramp over 'lshape_steps' load steps."""
     rng = np.random.default_rng(seed)
     inst = W.batch_instances(count, sizes=sizes, seed=seed, coarsest=coarsest)
     t = 0.0
     out = []
     for i, w in enumerate(inst):
         t += rng.exponential(1.0 / rate_per_s)
+        steps = load_steps
         if lshape_every and i % lshape_every == lshape_every - 1:
             n = int(rng.choice(lshape_sizes))
-            w = W.config_3d_lshape(n, n_levels=3 if n <= 16 else 4)
-        out.append(Request(i, w, load_steps=load_steps, arrival=t))
+            w = W.config_3d_lshape(n, n_levels=lshape_levels(n))
+            steps = lshape_steps
+        out.append(Request(i, w, load_steps=steps, arrival=t))
     return out
+
+
+def lshape_levels(n: int) -> int:
+    """Levels of an L-shaped panel with n cells per edge (n/4 through the depth): down to 2 cells through
+    the depth, at most 5 levels."""
+    levels, m = 1, n // 4
+    while m % 2 == 0 and m // 2 >= 1 and levels < 5 and n // (1 << levels) >= 4:
+        m //= 2
+        levels += 1
+    return levels

@@ -54,6 +54,10 @@ class Workload:
     cracks: list = field(default_factory=list)
     seed: int = SEED
     domain: str = "box"            # "box" or "lshape" (the box minus its x >= mid, y >= mid quarter)
+    # displacement-driven loading: the vertical displacement is prescribed on the nodes of the strip
+    # {x0 <= x <= x1, y = y_s} (all z), growing linearly to u_ramp over the load steps
+    load_strip: tuple | None = None    # ((x0, x1), y_s)
+    u_ramp: float = 0.0
 
     def cell_mask(self):
         """uint8 per cell (x fastest), 1 = in the domain; None for the whole box."""
@@ -65,6 +69,33 @@ class Workload:
         plane = ~((i >= nx // 2) & (j >= ny // 2))
         nz = self.n_cells[2] if self.dim == 3 else 1
         return np.broadcast_to(plane, (nz, ny, nx)).ravel().astype(np.uint8)
+
+    def _strip_nodes(self):
+        (x0, x1), ys = self.load_strip
+        npa = self.nodes_per_axis()
+        idx = np.indices(npa[::-1]).reshape(self.dim, -1)[::-1]     # idx[a] = index along axis a
+        hx = (self.hi[0] - self.lo[0]) / (npa[0] - 1)
+        hy = (self.hi[1] - self.lo[1]) / (npa[1] - 1)
+        x = self.lo[0] + idx[0] * hx
+        y = self.lo[1] + idx[1] * hy
+        tol = 1e-9 * (self.hi[0] - self.lo[0])
+        return (np.abs(y - ys) <= tol) & (x >= x0 - tol) & (x <= x1 + tol)
+
+    def dirichlet_mask(self):
+        """uint8 per node with the u_y Dirichlet bit on the loading strip (None without one), OR-ed by the
+        library into the face mask."""
+        if self.load_strip is None:
+            return None
+        return np.where(self._strip_nodes(), 2, 0).astype(np.uint8)
+
+    def u_dirichlet(self, frac: float):
+        """Prescribed displacements (dim * n_nodes, component-blocked) at the fraction 'frac' of the load
+        ramp: u_y = frac * u_ramp on the strip, 0 elsewhere (the clamped faces); None without a strip."""
+        if self.load_strip is None:
+            return None
+        u = np.zeros(self.dim * self.n_nodes)
+        u[self.n_nodes:2 * self.n_nodes][self._strip_nodes()] = frac * self.u_ramp
+        return u
 
     @property
     def edge(self) -> float:
@@ -114,20 +145,27 @@ def config_2d_two_cracks(n: int = 128, n_levels: int = 4, deg: int = 1) -> Workl
     return w.finalize()
 
 
-def config_3d_lshape(n: int = 32, n_levels: int = 4, deg: int = 1) -> Workload:
-    """L-shaped panel of Sec. 5.3 as a serving instance: [0,2]^2 minus [1,2]^2 extruded to a depth
-    of 0.5 (n x n x n/4 cells of edge 2/n), clamped on the face y = 0, no initial crack, loaded by
-    the pressure term (phi~^2 p, div w), which with phi = 1 acts as a normal traction p on the free
-    faces; E = 1, nu = 0.2, Gc = 1e-3."""
+def config_3d_lshape(n: int = 32, n_levels: int = 4, deg: int = 1, loading: str = "displacement") -> Workload:
+    """L-shaped panel of Sec. 5.3 as a serving instance: [0,2]^2 minus [1,2]^2 extruded to a depth of 0.5
+    (n x n x n/4 cells of edge 2/n), clamped on the face y = 0, no initial crack, E = 1, nu = 0.2,
+    Gc = 1e-3.  loading 'displacement' (default): no pressure (p = 0, as in Sec. 5.2/5.3) and a
+    vertical displacement prescribed on the strip 1 <= x <= 1.25 of the face y = 1 (the top of the
+    lower arm, next to the re-entrant corner), growing to 1e-2 over the load steps; 'pressure': the
+    pressure term (phi~^2 p, div w) with p = 1e-3, which with phi = 1 is a normal traction on the free
+    faces."""
+    disp = loading == "displacement"
     w = Workload("3d_lshape", 3, deg, (n, n, n // 4), n_levels, (0.0, 0.0, 0.0), (2.0, 2.0, 0.5), Gc=1e-3,
-                 pressure=1e-3, dirichlet_faces=1 << 2, domain="lshape")
+                 pressure=0.0 if disp else 1e-3, dirichlet_faces=1 << 2, domain="lshape",
+                 load_strip=((1.0, 1.25), 1.0) if disp else None, u_ramp=1e-2 if disp else 0.0)
     return w.finalize()
 
 
-def config_2d_lshape(n: int = 32, n_levels: int = 4, deg: int = 1) -> Workload:
+def config_2d_lshape(n: int = 32, n_levels: int = 4, deg: int = 1, loading: str = "displacement") -> Workload:
     """2D L-shaped panel [0,2]^2 minus [1,2]^2, clamped on y = 0, loaded like config_3d_lshape."""
-    w = Workload("2d_lshape", 2, deg, (n, n), n_levels, (0.0, 0.0), (2.0, 2.0), Gc=1e-3, pressure=1e-3,
-                 dirichlet_faces=1 << 2, domain="lshape")
+    disp = loading == "displacement"
+    w = Workload("2d_lshape", 2, deg, (n, n), n_levels, (0.0, 0.0), (2.0, 2.0), Gc=1e-3,
+                 pressure=0.0 if disp else 1e-3, dirichlet_faces=1 << 2, domain="lshape",
+                 load_strip=((1.0, 1.25), 1.0) if disp else None, u_ramp=1e-2 if disp else 0.0)
     return w.finalize()
 
 

@@ -9,8 +9,8 @@ pressures and crack layouts) runs through the batch ABI; per instance:
   - two batched active-set Newton steps (Algorithm 1): the active set exactly, the residual norm,
     FGMRES iterations within 10 % (FP32 V-cycle: +-1), and the update solving the oracle's
     eliminated system to the 1e-8 tolerance.
-And two served requests (a crack instance and the L-shaped panel), two load steps each in one mix,
-against the oracle's load steps (Algorithm 1 to its stop test) to 1e-6."""
+And two served requests (a crack instance and the displacement-driven L-shaped panel), two load steps
+each in one mix, against the oracle's load steps (Algorithm 1 to its stop test) to 1e-6."""
 import math
 
 import numpy as np
@@ -56,12 +56,12 @@ def mix_workloads(seed=0):
 
 
 class Inst:
-    def __init__(self, w, k, mgp):
+    def __init__(self, w, k, mgp, stream=None):
         self.w = w
         self.seed = 100 + k
         self.U, self.po, self.pt = W.initial_state(w, displacement="smooth")
         self.prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, seed=self.seed, mg_precision=mgp)
-        self.h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), self.prm)
+        self.h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), self.prm, stream)
         self.Ud = t(self.U)
         pff.set_state(self.h, self.Ud, t(self.po), t(self.pt))
         self.mesh = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
@@ -78,8 +78,8 @@ class Inst:
         return act, Rt, lv
 
 
-def make_mix(mgp):
-    return [Inst(w, k, mgp) for k, w in enumerate(mix_workloads())]
+def make_mix(mgp, stream=None):
+    return [Inst(w, k, mgp, stream) for k, w in enumerate(mix_workloads())]
 
 
 def close(xs):
@@ -147,21 +147,44 @@ def test_batched_fp64_vcycle_matches_oracle(mix64):
         pff.batch_destroy(b)
 
 
-@pytest.mark.parametrize("mgp", [64, 32])
-def test_batched_newton_steps_match_oracle(mgp):
-    xs = make_mix(mgp)
+@pytest.mark.parametrize("mgp,graphs,switch", [(64, False, 10), (32, False, 10), (32, True, 10), (32, True, 2)],
+                         ids=["fp64mg", "fp32mg", "fp32mg_graph_autotuned", "fp32mg_graph_switch_to_fp64"])
+def test_batched_newton_steps_match_oracle(mgp, graphs, switch):
+    """graphs: the hierarchies live on a non-default stream, so the batched FGMRES replays its captured
+    Arnoldi step, and the level operators run the autotuner's choices.  switch: FGMRES iterations after
+    which an FP32-MG instance continues with the FP64 V-cycle (2: most instances switch mid-solve, so the
+    replayed step splits its V-cycle by precision)."""
+    stream = torch.cuda.Stream() if graphs else None
+    xs = make_mix(mgp, stream)
+    torch.cuda.synchronize()
     try:
         b = pff.batch_create([x.h for x in xs])
         try:
+            if not graphs:
+                pff.batch_set_kernel_style(b, 1)
+            pff.batch_set_precision_switch(b, switch)
             Uo = [x.U.copy() for x in xs]
             prev = [None] * len(xs)
             for step in range(2):
                 Ud = [t(u) for u in Uo]
+                torch.cuda.synchronize()
                 infos = pff.batch_newton_step(b, Ud)
+                if graphs:
+                    for level in (-1, 0):
+                        style, cps, ms = pff.batch_tuning(b, level, 64)
+                        assert style in (1, 2) and cps >= 0 and ms > 0
+                precs = pff.batch_mg_precisions(b, len(xs))
+                for info, pr in zip(infos, precs):
+                    want = 64 if (mgp == 64 or info.solve.iterations > switch) else 32
+                    assert pr == want, (precs, [i.solve.iterations for i in infos])
+                if switch == 2:
+                    assert 64 in precs
                 for i, (x, info) in enumerate(zip(xs, infos)):
                     act, Rt, lv = x.oracle_system(Uo[i])
                     ga = torch.empty(x.w.n_nodes, dtype=torch.uint8, device=DEV)
+                    torch.cuda.synchronize()
                     pff.get_active_set(x.h, ga)
+                    torch.cuda.synchronize()
                     np.testing.assert_array_equal(ga.cpu().numpy().astype(bool), act)
                     assert info.n_active == int(act.sum())
                     assert info.n_changed == (int(act.sum()) if prev[i] is None else int(np.sum(act != prev[i])))
@@ -171,6 +194,7 @@ def test_batched_newton_steps_match_oracle(mgp):
                                                       rtol=1e-8, restart=30, maxit=200)
                     slack = max(1, math.floor(0.1 * its_o)) if mgp == 32 else math.floor(0.1 * its_o)
                     assert abs(info.solve.iterations - its_o) <= slack, (i, info.solve.iterations, its_o)
+                    torch.cuda.synchronize()
                     dU = Ud[i].cpu().numpy() - Uo[i]
                     assert np.linalg.norm(Rt - G @ dU) <= 1.01e-8 * np.linalg.norm(Rt)
                     prev[i] = act
@@ -188,12 +212,14 @@ def _oracle_serve(w, load_steps, max_newton=12):
     set as A_{k-1}, the request's CG seed."""
     m = fem.Mesh(w.dim, w.deg, w.n_cells, w.lo, w.hi, w.cell_mask())
     dmask = fem.dirichlet_face_mask(m, w.dirichlet_faces)
+    if w.dirichlet_mask() is not None:
+        dmask = dmask | w.dirichlet_mask()
     U, _, _ = W.initial_state(w)
     prev = None
     for n in range(1, load_steps + 1):
         ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure * n / load_steps)
         U, infos = pdas.load_step(m, ph, w.n_levels, U, None, dmask, prev, max_newton=max_newton, seed=w.seed,
-                                  maxit=200)
+                                  maxit=200, u_dirichlet=w.u_dirichlet(n / load_steps))
         prev = infos[-1].active
     return U
 
@@ -201,8 +227,7 @@ def _oracle_serve(w, load_steps, max_newton=12):
 def test_served_requests_match_oracle():
     crack = W.batch_instances(3, sizes=(16,), seed=11)[1]
     crack.pressure = 2e-2
-    lshape = W.config_3d_lshape(16, n_levels=3)
-    lshape.pressure = 2e-2
+    lshape = W.config_3d_lshape(16, n_levels=3)              # displacement ramp on the strip, p = 0
     rs = [serve.Request(0, crack, load_steps=2), serve.Request(1, lshape, load_steps=2)]
     srv = serve.Server(serve.PffBackend(), hbm_budget=8 << 30)
     srv.run(rs, realtime=False)

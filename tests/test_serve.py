@@ -32,7 +32,7 @@ class FakeBackend:
         self.live.add(id(inst))
         return inst
 
-    def start_load_step(self, inst, pressure):
+    def start_load_step(self, inst, pressure, frac=1.0):
         inst["k"] = 0
         inst["p"] = pressure
 
