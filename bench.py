@@ -151,31 +151,76 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(vals)}
 
 
-def cpu_baseline(n: int = 24, seconds: float = 3.0):
-    """Oracle Jacobian apply (assembled CSR, scipy SpMV, 1 thread) on an n^3 sample of the recipe."""
+def bench_config(n: int = 128, levels: int = 5, ws: int = 1) -> dict:
+    """The workload the JSON line is quoted on (shared by both arms)."""
+    nn = (n + 1) ** 3
+    return {"workload": f"3d_penny_q1_{n}", "n_dofs": 4 * nn, "levels": levels,
+            "step": "one active-set Newton step (FP32 V-cycle in FP64 FGMRES to 1e-8)",
+            "state": "U^3 after load steps p_n = n p / 3, n = 1..3; the step is the first of load step 4",
+            "l2": "inputs larger than L2 (one FP64 apply touches ~%.0f MB)" % (105.0 * nn / 1e6),
+            "parallelism": f"replicas{ws}"}
+
+
+def _oracle_slab(n: int = 128, layers: int = 2):
+    """The oracle's assembled Jacobian of a slab of the n^3 penny workload: the n x n x 'layers' cells
+    through the crack plane z = 0 (same cell size, eps and crack recipe as the full mesh), at the
+    workload's synthetic state.  Assembly (element by element, full Gauss quadrature) is not timed."""
     from oracle import fem
     from paper_1902_08112_gb300 import workloads as W
-    w = W.small(W.config_3d_penny(), n, 1)
+    full = W.config_3d_penny(n=n)
+    dz = (full.hi[2] - full.lo[2]) / n
+    w = W.Workload("penny_slab", 3, 1, (n, n, layers), 1, full.lo[:2] + (-dz * layers / 2,),
+                   full.hi[:2] + (dz * layers / 2,), eps=full.eps, cracks=full.cracks)
     U, po, pt = W.initial_state(w, displacement="smooth")
     m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
     ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
-    mask = fem.dirichlet_face_mask(m, 0x3F)
     t0 = time.perf_counter()
-    G = fem.assemble(m, ph, U, pt, mask)
-    t_asm = time.perf_counter() - t0
-    x = W.random_vector(m.n_dofs, 7)
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        y = G @ x
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    gdofs = m.n_dofs * reps / el / 1e9
-    return {"value": gdofs, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"3D penny recipe at {n}^3 Q1 ({m.n_dofs} DoFs): scipy CSR SpMV of the oracle's "
-                      f"assembled Jacobian, {reps} applies in {el:.2f} s; assembly {t_asm:.1f} s excluded"}, float(y[0])
+    G = fem.assemble(m, ph, U, pt, fem.dirichlet_face_mask(m, 0x3F))
+    return G, m.n_dofs, time.perf_counter() - t0
+
+
+def _spmv_rate(G, threads: int, reps: int = 5, min_s: float = 0.4):
+    """Median over 'reps' timings of the oracle's CSR product y = G x split into 'threads' row blocks run
+    on a thread pool (scipy's product releases the GIL); each timing repeats the product for >= min_s.
+    Returns DoF/s."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = G.shape[0]
+    x = np.random.default_rng(7).standard_normal(n)
+    y = np.empty(n)
+    b = np.linspace(0, n, threads + 1).astype(int)
+    parts = [(G[b[i]:b[i + 1]], b[i], b[i + 1]) for i in range(threads)]
+
+    def f(p):
+        M, a, c = p
+        y[a:c] = M @ x
+
+    rates = []
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(f, parts))
+        for _ in range(reps):
+            k, t0 = 0, time.perf_counter()
+            while True:
+                list(ex.map(f, parts))
+                k += 1
+                el = time.perf_counter() - t0
+                if el >= min_s:
+                    break
+            rates.append(n * k / el)
+    return float(np.median(rates))
+
+
+def cpu_baseline():
+    """Oracle Jacobian apply (assembled CSR product) on the host cores, on a slab of the benchmark
+    workload: 1 thread and every core, median of 5."""
+    G, nd, t_asm = _oracle_slab()
+    cores = os.cpu_count() or 1
+    r1 = _spmv_rate(G, 1)
+    rn = _spmv_rate(G, cores)
+    return {"value": rn / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "single_thread": {"value": r1 / 1e9, "unit": "GDoF/s", "cores": 1},
+            "sample": f"3d_penny_q1_128: slab of 128 x 128 x 2 cells through the crack plane ({nd} DoFs, "
+                      f"{G.nnz} nonzeros) of the oracle's assembled Jacobian (assembly {t_asm:.1f} s, not timed); "
+                      f"CSR product in {cores} row blocks on {cores} threads, median of 5"}
 
 
 def bench_batch(count: int, dev):
@@ -273,15 +318,16 @@ def bench_batch(count: int, dev):
 
 
 def bench_multi(n: int, dev):
-    """3D multi-crack configuration (n^3 Q1, 8 penny cracks, 6 levels): FP64-accurate fine apply,
-    V-cycle and time to a 1e-8 FGMRES solve of the Newton right-hand side with the FP32 and the FP64
-    V-cycle, at the initial crack state with the active set of Algorithm 1."""
+    """3D multi-crack configuration (n^3 Q1, 8 penny cracks, 6 levels) at eps = 2h and 4h: FP64-accurate
+    fine apply, V-cycle and time to a 1e-8 FGMRES solve of the Newton right-hand side with the FP32 and the
+    FP64 V-cycle, at the initial crack state with the active set of Algorithm 1.  Each solution's error
+    against the FP64 oracle: the oracle's own rows (element by element, full Gauss quadrature) of the
+    eliminated Jacobian applied to the GPU solution on 4,000 seeded rows (a third of them on cracks),
+    against the right-hand side: max |b - G x| / max |b| over the sample."""
     import torch
+    from oracle import fem
     from paper_1902_08112_gb300 import pff, workloads as W
-    w = W.config_3d_multi(n=n, n_levels=6 if n >= 128 else 4)
-    U, po, pt = W.initial_state(w, displacement="smooth")
     stream = torch.cuda.Stream(device=dev)
-    out = {"workload": f"3d_multi_q1_{n}", "n_dofs": w.n_dofs, "levels": w.n_levels}
 
     def timed(fn, reps=3):
         fn()
@@ -295,38 +341,129 @@ def bench_multi(n: int, dev):
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    for mgp in (32, 64):
-        prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
-                                 mg_precision=mgp)
-        h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm, stream)
-        try:
-            with torch.cuda.stream(stream):
-                Ud, pod, ptd = (torch.from_numpy(a).to(dev) for a in (U, po, pt))
-                x = torch.randn(w.n_dofs, dtype=torch.float64, device=dev)
-                y = torch.empty_like(x)
-                z = torch.empty_like(x)
-                R = torch.empty_like(x)
-                xs = torch.zeros_like(x)
-            stream.synchronize()
-            pff.set_state(h, Ud, pod, ptd)
-            na, _ = pff.update_active_set(h)
-            pff.setup(h)
-            if mgp == 32:
-                ms = timed(lambda: pff.apply_jacobian(h, -1, x, y), reps=5)
-                out["apply64_ms"] = ms
-                out["apply_gdofs"] = w.n_dofs / (ms * 1e-3) / 1e9
-                out["n_active"] = na
-            vc = timed(lambda: pff.vcycle(h, x, z))
-            pff.residual(h, R)
-            stream.synchronize()
-            t0 = time.perf_counter()
-            info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=300, allow_noconv=True)
-            stream.synchronize()
-            out[f"fp{mgp}_mg"] = {"vcycle_ms": vc, "solve_ms": (time.perf_counter() - t0) * 1e3,
-                                  "iterations": info.iterations, "rel_res": info.res_final / max(info.res0, 1e-300),
-                                  "converged": bool(info.converged)}
-        finally:
-            pff.destroy_hierarchy(h)
+    out = {}
+    for ef in (2.0, 4.0):
+        w = W.config_3d_multi(n=n, n_levels=6 if n >= 128 else 4, eps_factor=ef)
+        U, po, pt = W.initial_state(w, displacement="smooth")
+        m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+        rng = np.random.default_rng(17)
+        crack_nodes = np.flatnonzero(po == 0.0)
+        rows = np.concatenate([rng.choice(w.n_dofs, 2700, replace=False),
+                               rng.choice(crack_nodes, 1300, replace=False) + rng.integers(0, 4, 1300) * w.n_nodes])
+        rec = {"workload": f"3d_multi_q1_{n}_eps{int(ef)}h", "n_dofs": w.n_dofs, "levels": w.n_levels, "eps": w.eps}
+        for mgp in (32, 64):
+            prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
+                                     mg_precision=mgp)
+            h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm, stream)
+            try:
+                with torch.cuda.stream(stream):
+                    Ud, pod, ptd = (torch.from_numpy(a).to(dev) for a in (U, po, pt))
+                    x = torch.randn(w.n_dofs, dtype=torch.float64, device=dev)
+                    y = torch.empty_like(x)
+                    z = torch.empty_like(x)
+                    R = torch.empty_like(x)
+                    xs = torch.zeros_like(x)
+                    mask = torch.empty(w.n_nodes, dtype=torch.uint8, device=dev)
+                stream.synchronize()
+                pff.set_state(h, Ud, pod, ptd)
+                na, _ = pff.update_active_set(h)
+                pff.setup(h)
+                if mgp == 32:
+                    ms = timed(lambda: pff.apply_jacobian(h, -1, x, y), reps=5)
+                    rec["apply64_ms"] = ms
+                    rec["apply_gdofs"] = w.n_dofs / (ms * 1e-3) / 1e9
+                    rec["n_active"] = na
+                vc = timed(lambda: pff.vcycle(h, x, z))
+                pff.residual(h, R)
+                stream.synchronize()
+                t0 = time.perf_counter()
+                info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=300, allow_noconv=True)
+                stream.synchronize()
+                solve_ms = (time.perf_counter() - t0) * 1e3
+                pff.level_state(h, -1, None, None, mask)
+                stream.synchronize()
+                Rh, xh, mh = R.cpu().numpy(), xs.cpu().numpy(), mask.cpu().numpy()
+                Gx = fem.apply_rows(m, ph, U, pt, mh, xh, rows)
+                err = float(np.abs(Rh[rows] - Gx).max() / np.abs(Rh).max())
+                rec[f"fp{mgp}_mg"] = {"vcycle_ms": vc, "solve_ms": solve_ms, "iterations": info.iterations,
+                                      "rel_res": info.res_final / max(info.res0, 1e-300),
+                                      "converged": bool(info.converged), "oracle_rows_rel_residual": err}
+            finally:
+                pff.destroy_hierarchy(h)
+        out[f"eps_{int(ef)}h"] = rec
+    return out
+
+
+def bench_q2(dev, sizes=((64, "penny", 5), (128, "multi", 6))):
+    """Q2 on the sum-factorised fast path: the 3D penny crack on 64^3 Q2 hexahedra (8.6M DoFs) and the
+    multi-crack recipe on 128^3 Q2 (67.9M DoFs).  FP64-accurate and FP32 fine applies (GDoF/s, HBM
+    fraction of the 105 B/node algorithmic bytes), V-cycles and a 1e-8 FGMRES solve of the Newton
+    right-hand side with the FP32 and the FP64 V-cycle, at the initial crack state with the active set
+    of Algorithm 1."""
+    import torch
+    from paper_1902_08112_gb300 import pff, workloads as W
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(fn, reps=3):
+        fn()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    for n, kind, levels in sizes:
+        w = (W.config_3d_penny(n=n, deg=2, n_levels=levels) if kind == "penny"
+             else W.config_3d_multi(n=n, deg=2, n_levels=levels))
+        U, po, pt = W.initial_state(w, displacement="smooth")
+        rec = {"workload": f"3d_{kind}_q2_{n}", "n_dofs": w.n_dofs, "levels": levels}
+        for mgp in (32, 64):
+            prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
+                                     mg_precision=mgp)
+            h = pff.create_hierarchy(pff.make_mesh(3, 2, w.n_cells, levels, w.lo, w.hi), prm, stream)
+            try:
+                with torch.cuda.stream(stream):
+                    Ud, pod, ptd = (torch.from_numpy(a).to(dev) for a in (U, po, pt))
+                    x = torch.randn(w.n_dofs, dtype=torch.float64, device=dev)
+                    y = torch.empty_like(x)
+                    z = torch.empty_like(x)
+                    R = torch.empty_like(x)
+                    xs = torch.zeros_like(x)
+                    x32 = x.float()
+                    y32 = torch.empty_like(x32)
+                stream.synchronize()
+                pff.set_state(h, Ud, pod, ptd)
+                pff.update_active_set(h)
+                pff.setup(h)
+                if mgp == 32:
+                    ms = timed(lambda: pff.apply_jacobian(h, -1, x, y), reps=5)
+                    ms32 = timed(lambda: pff.apply_jacobian_f32(h, -1, x32, y32), reps=5)
+                    nn = w.n_nodes
+                    rec["apply64_ms"] = ms
+                    rec["apply64_gdofs"] = w.n_dofs / (ms * 1e-3) / 1e9
+                    rec["apply64_hbm_frac"] = 105.0 * nn / (ms * 1e-3) / 1e9 / hbm
+                    rec["apply32_ms"] = ms32
+                    rec["apply32_gdofs"] = w.n_dofs / (ms32 * 1e-3) / 1e9
+                    rec["apply32_hbm_frac"] = 53.0 * nn / (ms32 * 1e-3) / 1e9 / hbm
+                vc = timed(lambda: pff.vcycle(h, x, z))
+                pff.residual(h, R)
+                stream.synchronize()
+                t0 = time.perf_counter()
+                info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=300, allow_noconv=True)
+                stream.synchronize()
+                rec[f"fp{mgp}_mg"] = {"vcycle_ms": vc, "solve_ms": (time.perf_counter() - t0) * 1e3,
+                                      "iterations": info.iterations, "converged": bool(info.converged),
+                                      "rel_res": info.res_final / max(info.res0, 1e-300)}
+            finally:
+                pff.destroy_hierarchy(h)
+        out[rec["workload"]] = rec
     return out
 
 
@@ -415,30 +552,37 @@ def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return 0
-    from oracle import fem
-    from paper_1902_08112_gb300 import workloads as W
-    n = 24
-    w = W.small(W.config_3d_penny(), n, 1)
-    U, po, pt = W.initial_state(w, displacement="smooth")
-    m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
-    ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
-    G = fem.assemble(m, ph, U, pt, fem.dirichlet_face_mask(m, 0x3F))
-    x = W.random_vector(m.n_dofs, 7)
-    for _ in range(args.warmup):
-        G @ x
+    G, nd, t_asm = _oracle_slab()
+    cores = os.cpu_count() or 1
+    from concurrent.futures import ThreadPoolExecutor
+    n = G.shape[0]
+    x = np.random.default_rng(7).standard_normal(n)
+    y = np.empty(n)
+    b = np.linspace(0, n, cores + 1).astype(int)
+    parts = [(G[b[i]:b[i + 1]], b[i], b[i + 1]) for i in range(cores)]
+
+    def f(p):
+        M, a, c = p
+        y[a:c] = M @ x
+
     reps_per_step = 20
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for _ in range(reps_per_step):
-            G @ x
-    el = time.perf_counter() - t0
-    val = m.n_dofs * reps_per_step * args.steps / el / 1e9
-    sample = f"3D penny recipe at {n}^3 Q1 ({m.n_dofs} DoFs): oracle CSR SpMV, {reps_per_step} applies per step"
+    with ThreadPoolExecutor(cores) as ex:
+        for _ in range(args.warmup):
+            list(ex.map(f, parts))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for _ in range(reps_per_step):
+                list(ex.map(f, parts))
+        el = time.perf_counter() - t0
+    val = nd * reps_per_step * args.steps / el / 1e9
+    sample = (f"3d_penny_q1_128: slab of 128 x 128 x 2 cells through the crack plane ({nd} DoFs) of the oracle's "
+              f"assembled Jacobian (assembly {t_asm:.1f} s, not timed); {reps_per_step} CSR products per step on "
+              f"{cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GDoF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "3d_penny_q1_128 (oracle sample 24^3)"},
-            "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": bench_config(128, 5, args.gpus),
+            "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -457,6 +601,7 @@ def main():
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving measurement (0: skip)")
     ap.add_argument("--multi", type=int, default=256, help="cells per edge of the multi-crack measurement (0: skip)")
     ap.add_argument("--variants", type=int, default=64, help="cells per edge of the variant measurements (0: skip)")
+    ap.add_argument("--q2", type=int, default=1, help="Q2 measurements (64^3 penny, 128^3 multi-crack; 0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -652,11 +797,7 @@ def main():
         "vs_baseline": None, "dtype": "df64", "data": "synthetic",
         "dtype_note": "double-float (pairs of FP32) arithmetic, FP64 vectors in memory; matches the FP64 "
                       "oracle's assembled product to 1e-12 relative",
-        "config": {"workload": f"3d_penny_q1_{args.n}", "n_dofs": nd, "levels": w.n_levels,
-                   "step": "one active-set Newton step (FP32 V-cycle in FP64 FGMRES to 1e-8)",
-                   "state": "U^3 after load steps p_n = n p / 3, n = 1..3; the step is the first of load step 4",
-                   "l2": "inputs larger than L2 (one FP64 apply touches ~%.0f MB)" % (105.0 * nn / 1e6),
-                   "parallelism": f"replicas{ws}"},
+        "config": bench_config(args.n, w.n_levels, ws),
         "clocks": clk.summary(),
         "e2e": {"value": job_gdofs(ws, nd, e2e_ms), "unit": "GDoF/s", "h2d_bytes_per_step": nd * 8,
                 "d2h_bytes_per_step": nd * 8},
@@ -677,9 +818,10 @@ def main():
         line["multi_crack"] = bench_multi(args.multi, dev)
     if args.variants > 0:
         line["variants"] = bench_variants(args.variants, dev)
+    if args.q2 > 0:
+        line["q2"] = bench_q2(dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb, _ = cpu_baseline()
-        line["cpu_baseline"] = cb
+        line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -103,6 +103,13 @@ typedef struct {
  *                 tangent of g sigma^+ + sigma^- (28 coefficients per Gauss point in 3D, allocated
  *                 on first use, not counted by pff_hierarchy_bytes); residuals, diagonals and Q2 use
  *                 the generic kernels; batches require 0.
+ *  tie_scale      scale of the tie band of the active-set test (the paper's test is a strict
+ *                 inequality; values within tol_as of zero are rounding noise and count as inactive):
+ *                 0 (default): lambda_i + c (phi_i - phi_old_i) > tol_as, lambda = M^-1 R;
+ *                 1: M_ii (lambda_i + c (phi_i - phi_old_i)) > tol_as, i.e. the band on the scale of the
+ *                 residual entry R_i, whose rounding noise does not shrink with the lumped mass
+ *                 (M_ii ~ h^d) when the mesh is refined.
+ *  newton_rtol    relative tolerance of the linear solve of each pff_newton_step (1e-8).
  *  preconditioner 0: P_full = MG(G~), the monolithic V-cycle (Sec. 3.3, default);
  *                 1: P_diag = blockdiag(MG(U~), MG(P~)) (Sec. 3.3): the coupling G_phiu is
  *                 left out of every V-cycle residual and of the coarse solve.  Batches
@@ -121,6 +128,8 @@ typedef struct {
     uint64_t seed;
     int preconditioner;
     int split;
+    int tie_scale;
+    double newton_rtol;
 } pff_params;
 
 typedef struct {
@@ -140,7 +149,7 @@ typedef struct {
 
 /* Fill *p with the defaults quoted above (E=1, nu=0.2, Gc=1, kappa=1e-10, eps=1, p=1e-3,
  * c=100, eps_as=1e-10, f=1, FP32 V-cycle, degree 4, 10 CG steps, 1.2, 0.2, 1e-6, 200, 12345,
- * P_full, no split). */
+ * P_full, no split, tie band on lambda, Newton linear tolerance 1e-8). */
 void pff_default_params(pff_params* p);
 
 /* Create the level hierarchy (Sec. 3.2 and 4.2) on the current CUDA device.  cuda_stream is a
@@ -183,8 +192,10 @@ pff_status pff_set_modulus(pff_hierarchy* h, const double* escale);
  * with a shared-memory gather in both precisions, 3 = one thread per cell in both precisions,
  * 4 = as 0 but the FP64-accurate operator gathers through shared memory, 5 = one thread per Gauss
  * point with global atomics in both precisions, 6 / 7 = as 0 with the per-cell FP64-accurate /
- * FP32 form with shared-memory derivatives on every 3D level.  Q2 meshes always use the generic
- * kernels.  Errors: PFF_EINVAL outside 0 .. 7. */
+ * FP32 form with shared-memory derivatives on every 3D level.  3D Q2 levels run, in every variant but
+ * 1, the sum-factorised Q2 applies (one warp per cell, a lane per node and Gauss point, 1D stages
+ * exchanged by warp shuffles, Gauss-point linearisation data precomputed per state, double-float /
+ * FP32); 2D Q2 uses the generic kernels.  Errors: PFF_EINVAL outside 0 .. 7. */
 pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant);
 
 /* Set the linearisation point.  U: FP64 [u | phi] (n_dofs), phi_old: FP64 (n_nodes) = the
@@ -217,7 +228,8 @@ pff_status pff_set_active_set(pff_hierarchy* h, const uint8_t* active);
 pff_status pff_get_active_set(const pff_hierarchy* h, uint8_t* active);
 
 /* Steps 1 and 3 of Algorithm 1 at the current state: R = -A(U), lambda = M^-1 R on the phi
- * DoFs with the lumped Gauss-Lobatto mass, active iff lambda + c (phi - phi_old) > tol_as.
+ * DoFs with the lumped Gauss-Lobatto mass, active iff lambda + c (phi - phi_old) > tol_as (tie_scale 1:
+ * M (lambda + c (phi - phi_old)) > tol_as).
  * Installs the new active set on all levels.  Host outputs (may be NULL): the set size and
  * the number of nodes that changed.  Synchronises. */
 pff_status pff_update_active_set(pff_hierarchy* h, int* n_active, int* n_changed);
@@ -306,7 +318,7 @@ pff_status pff_gmres_solve(pff_hierarchy* h, const double* b, double* x, double 
 
 /* One primal-dual active-set step (Algorithm 1) at state U (device FP64 in/out, n_dofs) with
  * the phi_old and phi_tilde of the last pff_set_state: residual, active set, elimination
- * (active rows carry phi_old - phi), FGMRES + V-cycle solve to rtol 1e-8 (restart 30,
+ * (active rows carry phi_old - phi), FGMRES + V-cycle solve to rtol params.newton_rtol (restart 30,
  * maxit 200), U += dU.  The new U becomes the hierarchy's state. */
 pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_info* info);
 
@@ -353,7 +365,8 @@ pff_status pff_batch_vcycle(pff_batch* b, const double* const* r, double* const*
 pff_status pff_batch_gmres_solve(pff_batch* b, const double* const* rhs, double* const* x, double rtol,
                                  int maxit, pff_solve_info* info);
 /* One active-set step (Algorithm 1) of every instance at U_i (host array of n device pointers,
- * updated in place), the linear solves batched.  infos: host array of n entries or NULL. */
+ * updated in place), the linear solves batched (to the first instance's newton_rtol).  infos: host
+ * array of n entries or NULL. */
 pff_status pff_batch_newton_step(pff_batch* b, double* const* U, pff_newton_info* infos);
 /* y_i = G~_i x_i on one level of every instance (Sec. 4.1), batched: level -1 = each instance's finest
  * level, level l >= 0 = the instance's level l (0 = coarsest; instances with fewer levels are
@@ -411,7 +424,7 @@ pff_status pff_profile_read(pff_hierarchy* h, int cls, int* count, double* total
  * phi is prescribed -- PFF_MASK_PHI_DIR set, or on no cell of the domain -- are never active) on
  * caller buffers, without a hierarchy and without any device allocation.
  *   mesh     the fine mesh (dim, degree, n_cells, lo, hi are used; n_levels is ignored).
- *   params   c_as and tol_as are used.
+ *   params   c_as, tol_as and tie_scale are used.
  *   cell_mask  device uint8, n_cells, nonzero = in the domain, or NULL for the whole box.  The
  *            lumped mass of a node sums over its domain cells only, as the hierarchy's does.
  *            mesh->cell_mask is a HOST array this call cannot read: a mesh that has one needs

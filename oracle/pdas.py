@@ -42,13 +42,16 @@ class StepInfo:
 
 
 def active_set(mesh: fem.Mesh, R: np.ndarray, M: np.ndarray, U: np.ndarray, phi_old: np.ndarray,
-               c: float, threshold: float = 1e-10, fixed: np.ndarray | None = None) -> np.ndarray:
-    """fixed: bool per node whose phi is prescribed (phi Dirichlet, outside the domain): never active."""
+               c: float, threshold: float = 1e-10, fixed: np.ndarray | None = None, tie_scale: int = 0) -> np.ndarray:
+    """fixed: bool per node whose phi is prescribed (phi Dirichlet, outside the domain): never active.
+    tie_scale 0: the tie band |lambda + c (phi - phi_old)| <= threshold; 1: the band on the scale of the
+    residual entry, |M (lambda + c (phi - phi_old))| <= threshold."""
     nn = mesh.n_nodes
     phi = U[mesh.dim * nn:]
     free = M > 0 if fixed is None else (M > 0) & ~fixed
     lam = np.divide(R[mesh.dim * nn:], M, out=np.zeros(nn), where=free)
-    return free & (lam + c * (phi - phi_old) > threshold)
+    v = lam + c * (phi - phi_old)
+    return free & ((v * M if tie_scale else v) > threshold)
 
 
 def eliminated_rhs(mesh, phys, U, ptil, phi_old, dir_mask, active, R):
@@ -80,7 +83,7 @@ def lift_dirichlet(mesh, U, dir_mask, u_dirichlet):
 
 def newton_step(mesh, phys, n_levels, U, phi_old, ptil, dir_mask, prev_active, c_as=100.0,
                 tol_as=1e-10, rtol=1e-8, restart=30, maxit=500, seed=12345, cg_steps=10,
-                prm: multigrid.MGParams | None = None, u_dirichlet=None):
+                prm: multigrid.MGParams | None = None, u_dirichlet=None, tie_scale: int = 0):
     """u_dirichlet: prescribed displacement values (displacement-driven loading, Sec. 5.2/5.3).  The
     iterate takes them on the Dirichlet DoFs before step 1, so R, G and the active set are evaluated at
     a state that satisfies the boundary condition and the increment of step 5 vanishes there (those rows
@@ -91,7 +94,8 @@ def newton_step(mesh, phys, n_levels, U, phi_old, ptil, dir_mask, prev_active, c
         U = lift_dirichlet(mesh, U, dir_mask, u_dirichlet)
     R = -fem.residual_A(mesh, phys, U, ptil)
     M = fem.lumped_mass(mesh)
-    act = active_set(mesh, R, M, U, phi_old, c_as, tol_as, fixed=(dir_mask & fem.BIT_PHI_DIR) != 0)
+    act = active_set(mesh, R, M, U, phi_old, c_as, tol_as, fixed=(dir_mask & fem.BIT_PHI_DIR) != 0,
+                     tie_scale=tie_scale)
     Rt, mask = eliminated_rhs(mesh, phys, U, ptil, phi_old, dir_mask, act, R)
     levels = multigrid.build_levels(mesh, n_levels, phys, U, ptil, mask)
     multigrid.estimate_levels(levels, seed, cg_steps)

@@ -47,6 +47,8 @@ extern "C" void pff_default_params(pff_params* p) {
     p->seed = 12345;
     p->preconditioner = 0;
     p->split = 0;
+    p->tie_scale = 0;
+    p->newton_rtol = 1e-8;
 }
 
 // Gauss-Legendre rule with deg+1 points mapped to [0,1] and the Lagrange basis on the
@@ -111,6 +113,8 @@ static const char* check_params(const pff_params* p) {
     if (!(p->coarse_rtol > 0 && p->coarse_rtol < 1) || p->coarse_maxit < 1) return "need 0 < coarse_rtol < 1, coarse_maxit >= 1";
     if (p->preconditioner != 0 && p->preconditioner != 1) return "preconditioner must be 0 (P_full) or 1 (P_diag)";
     if (p->split != 0 && p->split != 1) return "split must be 0 (none) or 1 (Miehe)";
+    if (p->tie_scale != 0 && p->tie_scale != 1) return "tie_scale must be 0 (lambda) or 1 (residual)";
+    if (!(p->newton_rtol > 0 && p->newton_rtol < 1)) return "need 0 < newton_rtol < 1";
     return nullptr;
 }
 
@@ -214,8 +218,10 @@ extern "C" pff_status pff_create_hierarchy(const pff_mesh* mesh, const pff_param
         if (e == cudaSuccess) e = dalloc(h, &L.pt32, nn);
         if (e == cudaSuccess) e = dalloc(h, &L.dinv64, nd);
         if (e == cudaSuccess) e = dalloc(h, &L.dinv32, nd);
-        if (e == cudaSuccess && g.deg == 1) {
-            const size_t nq = (size_t)q1_nk(g.dim) * (size_t)(1 << g.dim) * (size_t)g.n_cells;
+        if (e == cudaSuccess && (g.deg == 1 || g.dim == 3)) {
+            // Gauss-point linearisation data of the fast paths (Q1; Q2 in 3D)
+            const size_t nq = g.deg == 1 ? (size_t)q1_nk(g.dim) * (size_t)(1 << g.dim) * (size_t)g.n_cells
+                                         : q2_data_size(g);
             e = dalloc(h, &L.qpd32, nq);
             if (e == cudaSuccess) e = dalloc(h, &L.qpd64, nq);
         }
@@ -330,8 +336,9 @@ extern "C" int64_t pff_hierarchy_bytes(const pff_mesh* mesh, int restart) {
         const int64_t nd = (mesh->dim + 1) * nn;
         total += (nn + pad) + (nd * 8 + pad) + (nn * 8 + pad) + (nd * 4 + pad) + (nn * 4 + pad) + (nd * 8 + pad) +
                  (nd * 4 + pad) + 6 * ((nd * 4 + pad) + (nd * 8 + pad));
-        if (mesh->degree == 1) {
-            const int64_t nq = (int64_t)(mesh->dim == 3 ? 8 : 5) * (1 << mesh->dim) * nc;
+        if (mesh->degree == 1 || mesh->dim == 3) {
+            const int64_t nq = mesh->degree == 1 ? (int64_t)(mesh->dim == 3 ? 8 : 5) * (1 << mesh->dim) * nc
+                                                 : (int64_t)8 * 27 * nc;
             total += (nq * 4 + pad) + (nq * 8 + pad);
         }
         if (mesh->cell_mask) total += nc + pad;
@@ -480,8 +487,8 @@ static pff_status update_active(pff_hierarchy* h, int* n_active, int* n_changed)
     Level& F = h->lv[h->L - 1];
     CUDA_OR_FAIL(h, residual_fine(h, h->R));
     CUDA_OR_FAIL(h, cudaMemsetAsync(h->d_counts, 0, 2 * sizeof(int), h->stream));
-    CUDA_OR_FAIL(h, launch_active_set(F.g, h->R, h->lumped, F.U64, h->phi_old, h->prm.c_as, h->prm.tol_as, F.mask,
-                                      h->d_counts, h->stream));
+    CUDA_OR_FAIL(h, launch_active_set(F.g, h->R, h->lumped, F.U64, h->phi_old, h->prm.c_as, h->prm.tol_as,
+                                      h->prm.tie_scale, F.mask, h->d_counts, h->stream));
     int cnt[2] = {0, 0};
     CUDA_OR_FAIL(h, cudaMemcpyAsync(cnt, h->d_counts, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
     CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
@@ -851,7 +858,7 @@ extern "C" pff_status pff_newton_step(pff_hierarchy* h, double* U, pff_newton_in
     pff_solve_info si;
     memset(&si, 0, sizeof(si));
     std::string err;
-    st = fgmres(h, h->tmp64[1], dU, 1e-8, 30, 200, &si, err);
+    st = fgmres(h, h->tmp64[1], dU, h->prm.newton_rtol, 30, 200, &si, err);
     if (st != PFF_OK && st != PFF_ENOCONV) {
         h->err = err;
         return st;

@@ -1153,7 +1153,7 @@ extern "C" pff_status pff_batch_newton_step(pff_batch* b, double* const* U, pff_
         BCUDA_OR_FAIL(b, cudaMemsetAsync(h->tmp64[2], 0, nd * sizeof(double), b->stream));
     }
     std::vector<pff_solve_info> si(n);
-    st = b_fgmres(b, 1e-8, 200, si.data());
+    st = b_fgmres(b, b->hs[0]->prm.newton_rtol, 200, si.data());
     if (st != PFF_OK && st != PFF_ENOCONV) return st;
     for (int i = 0; i < n; ++i) {
         pff_status s2 = pff_internal_newton_finish(b->hs[i], U[i]);

@@ -71,6 +71,15 @@ __device__ __forceinline__ df64 df_from_double(double d) {
     if (se > 0 && rem) lo = __fmul_rn(__fmul_rn(__uint2float_rn(rem), 0x1.0p-29f), __uint_as_float((unsigned)se << 23));
     return df_make(hi, sign ? -lo : lo);
 }
+// double -> df64 with the conversion instructions (which issue on the FP64 pipe): hi = the nearest
+// float, lo = the nearest float to the remainder.  Used where few values are converted per thread, so
+// that the FP64 pipe (otherwise idle in the df64 kernels) takes the work off the FP32/integer pipes.
+__device__ __forceinline__ df64 df_from_double_cvt(double d) {
+    const float hi = __double2float_rn(d);
+    return df_make(hi, __double2float_rn(d - (double)hi));
+}
+template <typename S>
+__device__ __forceinline__ S load_cvt(double d);
 // exact float -> double by field arithmetic (subnormal floats become 0)
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
     const unsigned u = __float_as_uint(f);
@@ -96,6 +105,9 @@ struct Scalar<float> {
     __device__ static __forceinline__ float store(float v) { return v; }
     __device__ static __forceinline__ float zero() { return 0.f; }
 };
+
+template <> __device__ __forceinline__ float load_cvt<float>(double d) { return (float)d; }
+template <> __device__ __forceinline__ df64 load_cvt<df64>(double d) { return df_from_double_cvt(d); }
 
 template <>
 struct Scalar<df64> {

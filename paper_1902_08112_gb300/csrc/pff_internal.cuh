@@ -161,7 +161,7 @@ cudaError_t launch_cg_update_p(const Geom& g, T* p, const T* z, const double* be
 // lumped Gauss-Lobatto mass and active set (Algorithm 1 step 3)
 cudaError_t launch_lumped_mass(const Geom& g, double* M, cudaStream_t s);
 cudaError_t launch_active_set(const Geom& g, const double* R, const double* M, const double* U,
-                              const double* phi_old, double c, double threshold, uint8_t* mask,
+                              const double* phi_old, double c, double threshold, int tie_scale, uint8_t* mask,
                               int* counts, cudaStream_t s);
 cudaError_t launch_newton_rhs(const Geom& g, const double* R, const double* t, const double* U,
                               const double* phi_old, const uint8_t* mask, double* Rt, cudaStream_t s);

@@ -59,7 +59,7 @@ __device__ __forceinline__ double lumped_mass_node(const pff::Geom& g, const uin
 
 __global__ void k_active_set_noalloc(pff::Geom g, const uint8_t* __restrict__ cm, const double* __restrict__ R,
                                      const double* __restrict__ U, const double* __restrict__ phi_old, double c,
-                                     double thr, uint8_t* __restrict__ mask, int* __restrict__ counts) {
+                                     double thr, int tie_scale, uint8_t* __restrict__ mask, int* __restrict__ counts) {
     const int64_t nn = g.n_nodes;
     const int64_t base = (int64_t)blockIdx.x * kNoAllocNodesPerCta;
     int na = 0, nch = 0;
@@ -71,7 +71,8 @@ __global__ void k_active_set_noalloc(pff::Geom g, const uint8_t* __restrict__ cm
         const double M = lumped_mass_node(g, cm, n);
         const bool fixed = (m & PFF_MASK_PHI_DIR) != 0 || !(M > 0.0);
         const double lam = fixed ? 0.0 : R[g.dim * nn + n] / M;
-        const bool act = !fixed && lam + c * (U[g.dim * nn + n] - phi_old[n]) > thr;
+        const double v = lam + c * (U[g.dim * nn + n] - phi_old[n]);
+        const bool act = !fixed && (tie_scale ? v * M : v) > thr;
         const bool was = (m & PFF_MASK_ACTIVE) != 0;
         mask[n] = (uint8_t)((m & ~PFF_MASK_ACTIVE) | (act ? PFF_MASK_ACTIVE : 0));
         na += act;
@@ -158,7 +159,7 @@ extern "C" pff_status pff_active_set_noalloc(const pff_mesh* mesh, const pff_par
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     k_active_set_noalloc<<<(unsigned)nctas, kNoAllocThreads, 0, s>>>(g, cell_mask, R, U, phi_old, params->c_as,
-                                                                      params->tol_as, mask, counts);
+                                                                      params->tol_as, params->tie_scale, mask, counts);
     if (cudaGetLastError() != cudaSuccess) return PFF_ECUDA;
     k_sum_counts_noalloc<<<1, kNoAllocThreads, 0, s>>>(counts, (int)nctas);
     if (cudaGetLastError() != cudaSuccess) return PFF_ECUDA;

@@ -1053,7 +1053,7 @@ __device__ __forceinline__ void q1_cell_tile(const Q1ApplyArgs<typename Scalar<S
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const bool el = c < 3 ? ((m >> c) & 1) != 0 : (m & a.phi_bits) != 0;
-            sx[c * NT + t] = (in && !el) ? Scalar<S>::load(a.x[c * nn + gn]) : Scalar<S>::zero();
+            sx[c * NT + t] = (in && !el) ? load_cvt<S>(a.x[c * nn + gn]) : Scalar<S>::zero();
         }
     }
     __syncthreads();

@@ -75,4 +75,15 @@ cudaError_t launch_q1_apply_split32(const Geom& g, const Phys& ph, const float* 
                                     const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
 inline int q1_nks(int dim) { return dim == 3 ? 28 : 10; }
 
+// Q2 fast path on 3D levels (pff_q2.cu): Gauss-point linearisation data (8 coefficients x 27 points per
+// cell, [(cell * 8 + k) * 27 + q]) and the warp-per-cell sum-factorised applies (eliminated rows of y
+// preset by the caller).  Miehe split and 2D Q2 use the generic kernels.
+inline size_t q2_data_size(const Geom& g) { return (size_t)8 * 27 * (size_t)g.n_cells; }
+cudaError_t launch_q2_linearize(const Geom& g, const Phys& ph, const double* U, const double* pt, float* q32,
+                                float2* q64, cudaStream_t s);
+cudaError_t launch_q2_apply64(const Geom& g, const Phys& ph, const float2* qd, const double* x, double* y,
+                              const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
+cudaError_t launch_q2_apply32(const Geom& g, const Phys& ph, const float* qd, const float* x, float* y,
+                              const uint8_t* mask, int phi_bits, bool blockdiag, cudaStream_t s);
+
 }  // namespace pff

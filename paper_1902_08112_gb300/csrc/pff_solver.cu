@@ -78,6 +78,13 @@ cudaError_t apply_level(pff_hierarchy* h, int l, int op, const T* x, T* y, int p
                                  (h->q1_style & 2) != 0, h->stream, (h->q1_style & 8) != 0,
                                  (h->q1_style & 128) != 0 ||
                                      ((h->q1_style & 32) != 0 && L.g.n_cells >= kCellMinCells)));
+    } else if (h->fast_q1 && L.g.deg == 2 && L.g.dim == 3 && !h->ph.split && L.qpd64 &&
+               (op == OP_APPLY || op == OP_APPLY_BLOCKDIAG)) {
+        const bool bd = op == OP_APPLY_BLOCKDIAG;
+        if constexpr (sizeof(T) == 8)
+            CK(launch_q2_apply64(L.g, h->ph, L.qpd64, (const double*)x, (double*)y, L.mask, phi_bits, bd, h->stream));
+        else
+            CK(launch_q2_apply32(L.g, h->ph, L.qpd32, (const float*)x, (float*)y, L.mask, phi_bits, bd, h->stream));
     } else {
         CellArgs<T> a;
         a.g = L.g;
@@ -161,7 +168,10 @@ cudaError_t propagate_state(pff_hierarchy* h, bool values) {
         if (!values) break;     // only the masks changed: FP32 copies and Gauss-point data stay valid
         CK(launch_cast_f64_f32(L.U64, L.U32, n_dofs(L.g), h->stream));
         CK(launch_cast_f64_f32(L.pt64, L.pt32, L.g.n_nodes, h->stream));
-        if (L.qpd64 && !h->ph.split) CK(launch_q1_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
+        if (L.qpd64 && !h->ph.split) {
+            if (L.g.deg == 1) CK(launch_q1_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
+            else CK(launch_q2_linearize(L.g, h->ph, L.U64, L.pt64, L.qpd32, L.qpd64, h->stream));
+        }
         if (L.qps64 && h->ph.split)
             CK(launch_q1_linearize_split(L.g, h->ph, L.U64, L.pt64, L.qps32, L.qps64, h->stream));
     }

@@ -582,7 +582,7 @@ cudaError_t launch_lumped_mass(const Geom& g, double* M, cudaStream_t s) {
 // counts[1] = nodes whose membership changed.
 __global__ void k_active_set(Geom g, const double* __restrict__ R, const double* __restrict__ M,
                              const double* __restrict__ U, const double* __restrict__ phi_old, double c,
-                             double thr, uint8_t* __restrict__ mask, int* __restrict__ counts) {
+                             double thr, int tie_scale, uint8_t* __restrict__ mask, int* __restrict__ counts) {
     const int64_t nn = g.n_nodes;
     int na = 0, nch = 0;
     GRID_STRIDE(n, nn) {
@@ -590,7 +590,8 @@ __global__ void k_active_set(Geom g, const double* __restrict__ R, const double*
         // prescribed phi (phi Dirichlet, nodes outside the domain) never enters the active set
         const bool fixed = (m & PFF_MASK_PHI_DIR) != 0 || !(M[n] > 0.0);
         const double lam = fixed ? 0.0 : R[g.dim * nn + n] / M[n];
-        const bool act = !fixed && lam + c * (U[g.dim * nn + n] - phi_old[n]) > thr;
+        const double v = lam + c * (U[g.dim * nn + n] - phi_old[n]);
+        const bool act = !fixed && (tie_scale ? v * M[n] : v) > thr;
         const bool was = (m & PFF_MASK_ACTIVE) != 0;
         mask[n] = (uint8_t)((m & ~PFF_MASK_ACTIVE) | (act ? PFF_MASK_ACTIVE : 0));
         na += act;
@@ -606,9 +607,9 @@ __global__ void k_active_set(Geom g, const double* __restrict__ R, const double*
     }
 }
 cudaError_t launch_active_set(const Geom& g, const double* R, const double* M, const double* U,
-                              const double* phi_old, double c, double threshold, uint8_t* mask, int* counts,
-                              cudaStream_t s) {
-    k_active_set<<<grid_for(g.n_nodes), kThreads, 0, s>>>(g, R, M, U, phi_old, c, threshold, mask, counts);
+                              const double* phi_old, double c, double threshold, int tie_scale, uint8_t* mask,
+                              int* counts, cudaStream_t s) {
+    k_active_set<<<grid_for(g.n_nodes), kThreads, 0, s>>>(g, R, M, U, phi_old, c, threshold, tie_scale, mask, counts);
     return count_launch(cudaGetLastError());
 }
 

@@ -123,6 +123,10 @@ CASES = {
     "2d_q1_lshape": (lambda: W.small(W.config_2d_lshape(), 24, 3), 0),
     "3d_q1_lshape_lanes": (lambda: W.small(W.config_3d_lshape(), (16, 16, 4), 2), 2),
     "2d_q2_lshape": (lambda: W.small(W.config_2d_lshape(deg=2), 12, 2), 1),
+    # 3D Q2 fast path (warp per cell, sum-factorised stages by shuffles, stored Gauss-point data)
+    "3d_q2_fast": (lambda: W.small(W.config_3d_penny(deg=2), 12, 3), 0),
+    "3d_q2_fast_modulus": (lambda: W.small(W.config_3d_penny(deg=2), 8, 2), 0, True),
+    "3d_q2_fast_lshape": (lambda: W.small(W.config_3d_lshape(deg=2), (8, 8, 4), 2), 0),
 }
 
 

@@ -46,6 +46,7 @@ SOLVE_CASES = {
     "2d_q1_64": lambda: W.config_2d_single_crack(),            # the 2D config itself (3 levels)
     "3d_q1_16": lambda: W.small(W.config_3d_penny(), 16, 3),
     "3d_q2_8": lambda: W.small(W.config_3d_penny(deg=2), 8, 2),
+    "3d_q2_12": lambda: W.small(W.config_3d_penny(deg=2), 12, 3),
     "3d_lshape_32": lambda: W.config_3d_lshape(32, 3),
 }
 
@@ -104,6 +105,41 @@ def test_newton_step_matches_oracle(mgp):
             Ud = t(Uo)     # continue both from the oracle's iterate
             if oi.converged:
                 break
+    finally:
+        pff.destroy_hierarchy(h)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_full_size_q2_apply_sampled_rows(prec):
+    """The 3D penny workload on 64^3 Q2 hexahedra (8.6M DoFs, the Q2 size of the benchmark workload),
+    sum-factorised Q2 apply, 4,000 sampled rows (with crack and boundary rows) against the oracle's
+    row-by-row element computation: FP64-accurate to 1e-12 of the largest entry, FP32 to 1e-5."""
+    w = W.config_3d_penny(n=64, deg=2, n_levels=5)
+    h, U, po, pt = make(w, 32)
+    try:
+        pff.update_active_set(h)
+        active = torch.empty(w.n_nodes, dtype=torch.uint8, device=DEV)
+        pff.get_active_set(h, active)
+        act = active.cpu().numpy()
+        m = fem.Mesh(3, 2, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+        mask = fem.dirichlet_face_mask(m, 0x3F) | (act * fem.BIT_ACTIVE).astype(np.uint8)
+        x = W.random_vector(w.n_dofs, 12)
+        if prec == 64:
+            y = torch.empty(w.n_dofs, dtype=torch.float64, device=DEV)
+            pff.apply_jacobian(h, -1, t(x), y)
+        else:
+            x = x.astype(np.float32).astype(np.float64)
+            y = torch.empty(w.n_dofs, dtype=torch.float32, device=DEV)
+            pff.apply_jacobian_f32(h, -1, t(x.astype(np.float32)), y)
+        rng = np.random.default_rng(6)
+        rows = rng.choice(w.n_dofs, 4000, replace=False)
+        crack_nodes = np.flatnonzero(po == 0.0)
+        rows = np.concatenate([rows, crack_nodes[:200] + 3 * w.n_nodes, crack_nodes[:200] + w.n_nodes, np.arange(50)])
+        ref = fem.apply_rows(m, ph, U, pt, mask, x, rows)
+        got = y.double().cpu().numpy()[rows]
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= (1e-12 if prec == 64 else 1e-5) * scale
     finally:
         pff.destroy_hierarchy(h)
 

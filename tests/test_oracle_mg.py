@@ -224,9 +224,11 @@ def test_sneddon_crack_volume_2d():
     assert vol_pf > 0
 
 
-def test_active_set_complementarity_at_convergence():
+@pytest.mark.parametrize("tie_scale", [0, 1])
+def test_active_set_complementarity_at_convergence(tie_scale):
     """At PDAS convergence: phi <= phi_old, phi = phi_old on the active set, the multiplier
-    lambda = M^-1 R is >= 0 on the active set and ~0 on the inactive set (Algorithm 1)."""
+    lambda = M^-1 R is >= 0 on the active set and ~0 on the inactive set (Algorithm 1); with either
+    scale of the tie band (lambda, or the residual entry M lambda)."""
     w = W.small(W.config_2d_single_crack(), 16, 2)
     m = fem.Mesh(2, 1, w.n_cells, w.lo, w.hi)
     ph = fem.Phys(eps=w.eps, p=w.pressure * 50, kappa=w.kappa)
@@ -234,7 +236,7 @@ def test_active_set_complementarity_at_convergence():
     dmask = fem.dirichlet_face_mask(m, 0x3F)
     prev = None
     for k in range(12):
-        U, info = pdas.newton_step(m, ph, 2, U, po, pt, dmask, prev, rtol=1e-12)
+        U, info = pdas.newton_step(m, ph, 2, U, po, pt, dmask, prev, rtol=1e-12, tie_scale=tie_scale)
         if info.converged:
             break
         prev = info.active
