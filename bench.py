@@ -445,6 +445,12 @@ def bench_q2(dev, sizes=((64, "penny", 5), (128, "multi", 6))):
                 if mgp == 32:
                     ms = timed(lambda: pff.apply_jacobian(h, -1, x, y), reps=5)
                     ms32 = timed(lambda: pff.apply_jacobian_f32(h, -1, x32, y32), reps=5)
+                    if kind == "penny":
+                        # the generic direct-evaluation kernels (native FP64) for comparison
+                        pff.set_kernel_variant(h, 1)
+                        rec["generic_apply64_ms"] = timed(lambda: pff.apply_jacobian(h, -1, x, y), reps=2)
+                        pff.set_kernel_variant(h, 0)
+                        pff.setup(h)
                     nn = w.n_nodes
                     rec["apply64_ms"] = ms
                     rec["apply64_gdofs"] = w.n_dofs / (ms * 1e-3) / 1e9
@@ -456,7 +462,7 @@ def bench_q2(dev, sizes=((64, "penny", 5), (128, "multi", 6))):
                 pff.residual(h, R)
                 stream.synchronize()
                 t0 = time.perf_counter()
-                info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=300, allow_noconv=True)
+                info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=100, allow_noconv=True)
                 stream.synchronize()
                 rec[f"fp{mgp}_mg"] = {"vcycle_ms": vc, "solve_ms": (time.perf_counter() - t0) * 1e3,
                                       "iterations": info.iterations, "converged": bool(info.converged),
@@ -602,6 +608,8 @@ def main():
     ap.add_argument("--multi", type=int, default=256, help="cells per edge of the multi-crack measurement (0: skip)")
     ap.add_argument("--variants", type=int, default=64, help="cells per edge of the variant measurements (0: skip)")
     ap.add_argument("--q2", type=int, default=1, help="Q2 measurements (64^3 penny, 128^3 multi-crack; 0: skip)")
+    ap.add_argument("--q2-case", type=int, default=0,
+                    help="run the Q2 section on an n^3 Q2 penny crack (3 levels) only (a small profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -818,7 +826,9 @@ def main():
         line["multi_crack"] = bench_multi(args.multi, dev)
     if args.variants > 0:
         line["variants"] = bench_variants(args.variants, dev)
-    if args.q2 > 0:
+    if args.q2_case > 0:
+        line["q2"] = bench_q2(dev, sizes=((args.q2_case, "penny", 3),))
+    elif args.q2 > 0:
         line["q2"] = bench_q2(dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
