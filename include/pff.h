@@ -354,6 +354,21 @@ pff_status pff_load_step(pff_hierarchy* h, double* U, const double* phi_prev, do
 typedef struct pff_batch pff_batch;
 pff_status pff_batch_create(int n, pff_hierarchy* const* hierarchies, int restart, pff_batch** out);
 pff_status pff_batch_destroy(pff_batch* b);
+/* Continuous batching: instances join and leave a live batch between calls.  n may be 0 at creation
+ * (an empty batch takes its dimension, stream and options from the first submitted instance).
+ * pff_batch_submit appends a compatible hierarchy (same dimension, stream, mg_precision and
+ * cheb_degree; Q1, P_full, no split) at index pff_batch_size() - 1 and gives it a Krylov workspace of
+ * the batch's restart length; pff_batch_retire removes the instance at 'index' (later indices move
+ * down by one; the hierarchy itself is not destroyed).  The device tables, FGMRES state and captured
+ * graphs are rebuilt at the next batched call (the autotuner's choices come from its process-wide
+ * cache when the make-up is similar).  The per-instance arrays of the batched calls (U, rhs, x, infos)
+ * follow the current order.  pff_batch_poll returns the instance's info of the last
+ * pff_batch_newton_step (zeros before one).  Calls on an empty batch return PFF_ESTATE.
+ * Errors: PFF_EINVAL (NULL, incompatible or duplicate instance, index out of range), PFF_ENOMEM. */
+pff_status pff_batch_submit(pff_batch* b, pff_hierarchy* h, int* index);
+pff_status pff_batch_retire(pff_batch* b, int index);
+int pff_batch_size(const pff_batch* b);
+pff_status pff_batch_poll(const pff_batch* b, int index, pff_newton_info* info);
 /* Diagonals and eigenvalue bounds of every instance (batched CG estimates, Sec. 3.2.1). */
 pff_status pff_batch_setup(pff_batch* b);
 /* z_i ~ G~_i^-1 r_i for every instance: one V-cycle (FP32 or FP64 levels, FP64 coarse solve) run

@@ -77,6 +77,8 @@ struct pff_batch {
     bool mg64 = false;                       // FP64 V-cycle (mg_precision 64 in every instance)
     int style = 0;                           // level-operator kernels: 0 by level size, 1 small-level, 2 per-cell
     bool stale = true;
+    bool dirty = false;                      // instances changed: device state rebuilt before the next call
+    std::vector<pff_newton_info> last;       // per instance: the last batched Newton step (pff_batch_poll)
     std::vector<void*> allocs;
     std::string err;
 };
@@ -965,13 +967,81 @@ pff_status b_fgmres(pff_batch* b, double rtol, int maxit, pff_solve_info* info) 
     return st;
 }
 
-void free_batch(pff_batch* b) {
+// The device-side state of a batch (descriptor tables, reduction scratch, FGMRES state, captured
+// graphs, tuning): released and rebuilt from the current instance list when it changes.
+void release_state(pff_batch* b) {
     drop_step_graph(b);
-    for (cudaEvent_t& e : b->ev_step)
+    for (cudaEvent_t& e : b->ev_step) {
         if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
     if (b->h_status) cudaFreeHost(b->h_status);
+    b->h_status = nullptr;
     for (void* p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+    b->d_lv = b->d_fine = nullptr;
+    b->d_tiles = nullptr;
+    b->d_part = b->d_vals = b->d_coef = b->d_fg = nullptr;
+    b->coef_cap = 0;
+    b->d_seeds = nullptr;
+    b->d_on = b->d_cyc = b->d_col = b->d_its = b->d_k = b->d_flags = b->d_count = b->d_prec = b->d_save = nullptr;
+    b->tuned = false;
+    b->stale = true;
+    b->use_graphs = true;
+}
+
+void free_batch(pff_batch* b) {
+    release_state(b);
     delete b;
+}
+
+cudaError_t build_state(pff_batch* b) {
+    const int n = b->n, restart = b->m;
+    b->Lmax = 0;
+    for (auto* h : b->hs) b->Lmax = std::max(b->Lmax, h->L);
+    b->valid.assign(n, 1);
+    b->h_lv.assign(b->Lmax, std::vector<BLevel>(n));
+    b->h_fine.assign(n, BLevel());
+    cudaError_t e = balloc(b, &b->d_lv, (size_t)b->Lmax * n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_fine, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_tiles, (size_t)(b->Lmax + 1) * 2 * (n + 1));
+    if (e == cudaSuccess) e = balloc(b, &b->d_part, (size_t)n * (restart + 2) * kBPartials * 2);
+    if (e == cudaSuccess) e = balloc(b, &b->d_vals, (size_t)n * (12 + 4 * kMaxCG + 4 * b->Lmax + 4 * (restart + 2)));
+    if (e == cudaSuccess) e = balloc(b, &b->d_seeds, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_on, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_cyc, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_col, (size_t)4);
+    if (e == cudaSuccess) e = balloc(b, &b->d_its, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_k, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_flags, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_count, (size_t)4);
+    if (e == cudaSuccess) e = balloc(b, &b->d_fg, (size_t)n * fg_stride(restart));
+    if (e == cudaSuccess) e = balloc(b, &b->d_prec, (size_t)n);
+    if (e == cudaSuccess) e = balloc(b, &b->d_save, (size_t)n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * (size_t)(n + 5));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev_step[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = q1_batched_prepare();
+    if (e == cudaSuccess) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (e == cudaSuccess) {
+        std::vector<uint64_t> seeds(n);
+        for (int i = 0; i < n; ++i) seeds[i] = b->hs[i]->prm.seed;
+        e = cudaMemcpyAsync(b->d_seeds, seeds.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, b->stream);
+    }
+    if (e == cudaSuccess) e = upload(b);   // synchronises: the seeds' host vector may go
+    if (e == cudaSuccess) b->dirty = false;
+    return e;
+}
+
+// an instance a batch can hold: Q1, same dimension, stream, V-cycle precision and Chebyshev degree as
+// the batch's first instance, P_full, no split, the Q1 fast path
+bool batch_compatible(const pff_hierarchy* h, const pff_hierarchy* ref) {
+    return h && h->mesh.degree == 1 && h->mesh.dim == ref->mesh.dim && h->stream == ref->stream &&
+           h->prm.mg_precision == ref->prm.mg_precision && h->prm.preconditioner == 0 && h->prm.split == 0 &&
+           h->prm.cheb_degree == ref->prm.cheb_degree && h->fast_q1;
 }
 
 pff_status b_fail(pff_batch* b, pff_status st, const std::string& msg) {
@@ -993,72 +1063,96 @@ extern pff_status pff_internal_ensure_krylov(pff_hierarchy* h, int m);
 extern "C" pff_status pff_batch_create(int n, pff_hierarchy* const* hs, int restart, pff_batch** out) {
     if (!out) return PFF_EINVAL;
     *out = nullptr;
-    if (n < 1 || !hs || restart < 1 || restart > 200) return PFF_EINVAL;
-    for (int i = 0; i < n; ++i) {
-        if (!hs[i]) return PFF_EINVAL;
-        if (hs[i]->mesh.degree != 1 || hs[i]->mesh.dim != hs[0]->mesh.dim) return PFF_EINVAL;
-        if (hs[i]->stream != hs[0]->stream) return PFF_EINVAL;
-        if (hs[i]->prm.mg_precision != hs[0]->prm.mg_precision || hs[i]->prm.preconditioner != 0 || hs[i]->prm.split != 0 || hs[i]->prm.cheb_degree != hs[0]->prm.cheb_degree) return PFF_EINVAL;
-        if (!hs[i]->fast_q1) return PFF_EINVAL;
-    }
+    if (n < 0 || (n > 0 && !hs) || restart < 1 || restart > 200) return PFF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!batch_compatible(hs[i], hs[0])) return PFF_EINVAL;
     pff_batch* b = new (std::nothrow) pff_batch();
     if (!b) return PFF_ENOMEM;
-    b->n = n;
-    b->dim = hs[0]->mesh.dim;
     b->m = restart;
-    b->mg64 = hs[0]->prm.mg_precision == 64;
     b->hs.assign(hs, hs + n);
-    b->stream = hs[0]->stream;
-    b->cheb_k = hs[0]->prm.cheb_degree;
-    for (auto* h : b->hs) b->Lmax = std::max(b->Lmax, h->L);
-    b->valid.assign(n, 1);
-    b->h_lv.assign(b->Lmax, std::vector<BLevel>(n));
-    b->h_fine.resize(n);
-    pff_status st = PFF_OK;
-    for (auto* h : b->hs) {
-        st = pff_internal_ensure_krylov(h, restart);
-        if (st != PFF_OK) break;
-    }
-    cudaError_t e = cudaSuccess;
-    if (st == PFF_OK) {
-        e = balloc(b, &b->d_lv, (size_t)b->Lmax * n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_fine, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_tiles, (size_t)(b->Lmax + 1) * 2 * (n + 1));
-        if (e == cudaSuccess) e = balloc(b, &b->d_part, (size_t)n * (restart + 2) * kBPartials * 2);
-        if (e == cudaSuccess) e = balloc(b, &b->d_vals, (size_t)n * (12 + 4 * kMaxCG + 4 * b->Lmax + 4 * (restart + 2)));
-        if (e == cudaSuccess) e = balloc(b, &b->d_seeds, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_on, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_cyc, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_col, (size_t)4);
-        if (e == cudaSuccess) e = balloc(b, &b->d_its, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_k, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_flags, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_count, (size_t)4);
-        if (e == cudaSuccess) e = balloc(b, &b->d_fg, (size_t)n * fg_stride(restart));
-        if (e == cudaSuccess) e = balloc(b, &b->d_prec, (size_t)n);
-        if (e == cudaSuccess) e = balloc(b, &b->d_save, (size_t)n);
-        if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * (size_t)(n + 5));
-        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev_step[k], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = q1_batched_prepare();
-        if (e == cudaSuccess) {
-            int dev = 0;
-            e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    b->n = n;
+    b->last.assign(n, pff_newton_info());
+    b->dirty = true;
+    if (n > 0) {
+        b->dim = hs[0]->mesh.dim;
+        b->mg64 = hs[0]->prm.mg_precision == 64;
+        b->stream = hs[0]->stream;
+        b->cheb_k = hs[0]->prm.cheb_degree;
+        pff_status st = PFF_OK;
+        for (auto* h : b->hs) {
+            st = pff_internal_ensure_krylov(h, restart);
+            if (st != PFF_OK) break;
         }
-        if (e == cudaSuccess) {
-            std::vector<uint64_t> seeds(n);
-            for (int i = 0; i < n; ++i) seeds[i] = b->hs[i]->prm.seed;
-            e = cudaMemcpyAsync(b->d_seeds, seeds.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, b->stream);
+        if (st == PFF_OK) {
+            cudaError_t e = build_state(b);
+            if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? PFF_ENOMEM : PFF_ECUDA;
         }
-        if (e == cudaSuccess) e = upload(b);
-        if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? PFF_ENOMEM : PFF_ECUDA;
-    }
-    if (st != PFF_OK) {
-        cudaGetLastError();
-        free_batch(b);
-        return st;
+        if (st != PFF_OK) {
+            cudaGetLastError();
+            free_batch(b);
+            return st;
+        }
     }
     *out = b;
+    return PFF_OK;
+}
+
+// rebuild the device state after submit/retire; an empty batch has nothing to run
+static pff_status ensure_built(pff_batch* b) {
+    if (b->n == 0) return b_fail(b, PFF_ESTATE, "the batch holds no instance");
+    if (!b->dirty) return PFF_OK;
+    BCUDA_OR_FAIL(b, cudaStreamSynchronize(b->stream));
+    release_state(b);
+    cudaError_t e = build_state(b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release_state(b);
+        b->dirty = true;
+        return b_fail(b, e == cudaErrorMemoryAllocation ? PFF_ENOMEM : PFF_ECUDA,
+                      std::string("batch rebuild: ") + cudaGetErrorString(e));
+    }
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_batch_submit(pff_batch* b, pff_hierarchy* h, int* index) {
+    if (!b || !h) return PFF_EINVAL;
+    if (b->n > 0 && !batch_compatible(h, b->hs[0]))
+        return b_fail(b, PFF_EINVAL, "instance incompatible with the batch (dimension, stream, precision, options)");
+    if (b->n == 0 && !batch_compatible(h, h)) return b_fail(b, PFF_EINVAL, "instance cannot be batched (Q1, P_full, no split)");
+    for (auto* g : b->hs)
+        if (g == h) return b_fail(b, PFF_EINVAL, "instance already in the batch");
+    pff_status st = pff_internal_ensure_krylov(h, b->m);
+    if (st != PFF_OK) return b_fail(b, st, "Krylov workspace of the submitted instance");
+    if (b->n == 0) {
+        b->dim = h->mesh.dim;
+        b->mg64 = h->prm.mg_precision == 64;
+        b->stream = h->stream;
+        b->cheb_k = h->prm.cheb_degree;
+    }
+    b->hs.push_back(h);
+    b->last.push_back(pff_newton_info());
+    b->n = (int)b->hs.size();
+    b->dirty = true;
+    if (index) *index = b->n - 1;
+    return PFF_OK;
+}
+
+extern "C" pff_status pff_batch_retire(pff_batch* b, int index) {
+    if (!b) return PFF_EINVAL;
+    if (index < 0 || index >= b->n) return b_fail(b, PFF_EINVAL, "index out of range");
+    if (b->stream) BCUDA_OR_FAIL(b, cudaStreamSynchronize(b->stream));
+    b->hs.erase(b->hs.begin() + index);
+    b->last.erase(b->last.begin() + index);
+    b->n = (int)b->hs.size();
+    b->dirty = true;
+    return PFF_OK;
+}
+
+extern "C" int pff_batch_size(const pff_batch* b) { return b ? b->n : -1; }
+
+extern "C" pff_status pff_batch_poll(const pff_batch* b, int index, pff_newton_info* info) {
+    if (!b || !info || index < 0 || index >= b->n) return PFF_EINVAL;
+    *info = b->last[index];
     return PFF_OK;
 }
 
@@ -1071,6 +1165,10 @@ extern "C" pff_status pff_batch_destroy(pff_batch* b) {
 
 extern "C" pff_status pff_batch_setup(pff_batch* b) {
     if (!b) return PFF_EINVAL;
+    {
+        const pff_status sb = ensure_built(b);
+        if (sb != PFF_OK) return sb;
+    }
     for (auto* h : b->hs)
         if (!h->has_state) return b_fail(b, PFF_ESTATE, "batch setup before pff_set_state of every instance");
     for (auto* h : b->hs) BCUDA_OR_FAIL(b, refresh_state(h));
@@ -1089,6 +1187,10 @@ static pff_status ensure_batch_setup(pff_batch* b) {
 
 extern "C" pff_status pff_batch_vcycle(pff_batch* b, const double* const* r, double* const* z) {
     if (!b || !r || !z) return PFF_EINVAL;
+    {
+        const pff_status sb = ensure_built(b);
+        if (sb != PFF_OK) return sb;
+    }
     pff_status st = ensure_batch_setup(b);
     if (st != PFF_OK) return st;
     for (int i = 0; i < b->n; ++i) {
@@ -1110,6 +1212,10 @@ extern "C" pff_status pff_batch_vcycle(pff_batch* b, const double* const* r, dou
 extern "C" pff_status pff_batch_gmres_solve(pff_batch* b, const double* const* rhs, double* const* x, double rtol,
                                             int maxit, pff_solve_info* info) {
     if (!b || !rhs || !x) return PFF_EINVAL;
+    {
+        const pff_status sb = ensure_built(b);
+        if (sb != PFF_OK) return sb;
+    }
     if (!(rtol > 0 && rtol < 1) || maxit < 1) return b_fail(b, PFF_EINVAL, "need 0 < rtol < 1 and maxit >= 1");
     pff_status st = ensure_batch_setup(b);
     if (st != PFF_OK) return st;
@@ -1136,6 +1242,10 @@ extern pff_status pff_internal_newton_finish(pff_hierarchy* h, double* U);
 
 extern "C" pff_status pff_batch_newton_step(pff_batch* b, double* const* U, pff_newton_info* infos) {
     if (!b || !U) return PFF_EINVAL;
+    {
+        const pff_status sb = ensure_built(b);
+        if (sb != PFF_OK) return sb;
+    }
     const int n = b->n;
     std::vector<int> na(n), nc(n);
     std::vector<double> res(n);
@@ -1158,13 +1268,13 @@ extern "C" pff_status pff_batch_newton_step(pff_batch* b, double* const* U, pff_
     for (int i = 0; i < n; ++i) {
         pff_status s2 = pff_internal_newton_finish(b->hs[i], U[i]);
         if (s2 != PFF_OK) return b_fail(b, s2, "instance " + std::to_string(i) + ": " + b->hs[i]->err);
-        if (infos) {
-            infos[i].n_active = na[i];
-            infos[i].n_changed = nc[i];
-            infos[i].res_norm = res[i];
-            infos[i].solve = si[i];
-            infos[i].converged = (nc[i] == 0 && res[i] <= b->hs[i]->prm.tol_as) ? 1 : 0;
-        }
+        pff_newton_info& li = b->last[i];
+        li.n_active = na[i];
+        li.n_changed = nc[i];
+        li.res_norm = res[i];
+        li.solve = si[i];
+        li.converged = (nc[i] == 0 && res[i] <= b->hs[i]->prm.tol_as) ? 1 : 0;
+        if (infos) infos[i] = li;
     }
     BCUDA_OR_FAIL(b, cudaStreamSynchronize(b->stream));
     return st;
@@ -1186,6 +1296,10 @@ extern "C" pff_status pff_batch_set_precision_switch(pff_batch* b, int iteration
 
 extern "C" pff_status pff_batch_mg_precisions(pff_batch* b, int* precisions) {
     if (!b || !precisions) return PFF_EINVAL;
+    {
+        const pff_status sb = ensure_built(b);
+        if (sb != PFF_OK) return sb;
+    }
     BCUDA_OR_FAIL(b, cudaMemcpyAsync(precisions, b->d_prec, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream));
     BCUDA_OR_FAIL(b, cudaStreamSynchronize(b->stream));
     for (int i = 0; i < b->n; ++i)
@@ -1198,7 +1312,7 @@ extern "C" pff_status pff_batch_tuning(pff_batch* b, int level, int precision, i
     if (!b) return PFF_EINVAL;
     if (precision != 32 && precision != 64) return b_fail(b, PFF_EINVAL, "precision must be 32 or 64");
     if (level < -1 || level >= b->Lmax) return b_fail(b, PFF_EINVAL, "level out of range");
-    if (!b->tuned) return b_fail(b, PFF_ESTATE, "the batch has not been tuned (pff_batch_setup with style 0)");
+    if (!b->tuned || b->dirty) return b_fail(b, PFF_ESTATE, "the batch has not been tuned (pff_batch_setup with style 0)");
     const pff_batch::Tune& t = b->tune[(size_t)(level < 0 ? b->Lmax : level) * 2 + (precision == 64 ? 1 : 0)];
     if (style) *style = t.style;
     if (ctas_per_sm) *ctas_per_sm = t.cps;
@@ -1209,6 +1323,10 @@ extern "C" pff_status pff_batch_tuning(pff_batch* b, int level, int precision, i
 extern "C" pff_status pff_batch_apply_jacobian(pff_batch* b, int level, int precision, const void* const* x,
                                                void* const* y) {
     if (!b || !x || !y) return PFF_EINVAL;
+    {
+        const pff_status sb = ensure_built(b);
+        if (sb != PFF_OK) return sb;
+    }
     if (precision != 32 && precision != 64) return b_fail(b, PFF_EINVAL, "precision must be 32 or 64");
     if (level < -1 || level >= b->Lmax) return b_fail(b, PFF_EINVAL, "level out of range");
     for (auto* h : b->hs)

@@ -93,6 +93,10 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _VP]),
     "pff_batch_create": (_I, [_I, ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)]),
     "pff_batch_destroy": (_I, [_VP]),
+    "pff_batch_submit": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_int)]),
+    "pff_batch_retire": (_I, [_VP, _I]),
+    "pff_batch_size": (_I, [_VP]),
+    "pff_batch_poll": (_I, [_VP, _I, ctypes.POINTER(NewtonInfo)]),
     "pff_batch_setup": (_I, [_VP]),
     "pff_batch_vcycle": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "pff_batch_gmres_solve": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _I, ctypes.POINTER(SolveInfo)]),
@@ -378,12 +382,33 @@ def _bcheck(b, st, where, allow=()):
     return st
 
 
-def batch_create(hierarchies, restart=30):
-    arr = (ctypes.c_void_p * len(hierarchies))(*[h.value for h in hierarchies])
+def batch_create(hierarchies=(), restart=30):
+    arr = (ctypes.c_void_p * max(1, len(hierarchies)))(*[h.value for h in hierarchies])
     b = ctypes.c_void_p()
-    st = load().pff_batch_create(len(hierarchies), arr, restart, ctypes.byref(b))
+    st = load().pff_batch_create(len(hierarchies), arr if hierarchies else None, restart, ctypes.byref(b))
     _check(None, st, "pff_batch_create")
     return b
+
+
+def batch_submit(b, h) -> int:
+    """Append a hierarchy to a live batch; returns its index."""
+    idx = ctypes.c_int()
+    _bcheck(b, load().pff_batch_submit(b, h, ctypes.byref(idx)), "pff_batch_submit")
+    return idx.value
+
+
+def batch_retire(b, index: int):
+    return _bcheck(b, load().pff_batch_retire(b, int(index)), "pff_batch_retire")
+
+
+def batch_size(b) -> int:
+    return int(load().pff_batch_size(b))
+
+
+def batch_poll(b, index: int) -> NewtonInfo:
+    info = NewtonInfo()
+    _bcheck(b, load().pff_batch_poll(b, int(index), ctypes.byref(info)), "pff_batch_poll")
+    return info
 
 
 def batch_destroy(b):

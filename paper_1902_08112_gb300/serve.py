@@ -59,8 +59,8 @@ class PffBackend:
         self.dev = torch.device(device)
         self.stream = torch.cuda.Stream(device=self.dev)
         self.restart = restart
-        self._batch, self._batch_key = None, None
-        self.batches_built = 0
+        self._batch, self._members = None, []
+        self.batches_built = 0          # ticks whose batch membership changed (device state rebuilt)
 
     def mesh(self, w):
         return self.pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi,
@@ -97,27 +97,48 @@ class PffBackend:
 
     def newton(self, insts):
         """One batched Newton step.  The batch (descriptor tables, device FGMRES state, captured Arnoldi
-        graph, tuned kernels) is kept across ticks and rebuilt only when the set of instances changes."""
-        key = tuple(i["h"].value for i in insts)
-        if self._batch is None or self._batch_key != key:
-            self.release()
-            self._batch = self.pff.batch_create([i["h"] for i in insts], self.restart)
-            self._batch_key = key
-            self.batches_built += 1
-        return self.pff.batch_newton_step(self._batch, [i["U"] for i in insts], allow_noconv=True)
+        graph, tuned kernels) lives across ticks: instances that joined are submitted to it and those
+        that left are retired (pff_batch_submit / pff_batch_retire), and the library rebuilds its device
+        state only when the membership changed."""
+        if self._batch is None:
+            self._batch = self.pff.batch_create([], self.restart)
+            self._members = []
+        want = {i["h"].value for i in insts}
+        changed = False
+        for idx in reversed(range(len(self._members))):
+            if self._members[idx] not in want:
+                self.pff.batch_retire(self._batch, idx)
+                self._members.pop(idx)
+                changed = True
+        for i in insts:
+            if i["h"].value not in self._members:
+                self.pff.batch_submit(self._batch, i["h"])
+                self._members.append(i["h"].value)
+                changed = True
+        self.batches_built += changed
+        order = {hv: k for k, hv in enumerate(self._members)}
+        Us = [None] * len(self._members)
+        for i in insts:
+            Us[order[i["h"].value]] = i["U"]
+        infos = self.pff.batch_newton_step(self._batch, Us, allow_noconv=True)
+        return [infos[order[i["h"].value]] for i in insts]
 
     def release(self):
+        """Destroy the batch (not its instances)."""
         if self._batch is not None:
             self.pff.batch_destroy(self._batch)
-        self._batch, self._batch_key = None, None
+        self._batch, self._members = None, []
 
     def fetch(self, inst):
         self.stream.synchronize()
         return inst["U"].cpu().numpy()
 
     def destroy(self, inst):
-        if self._batch_key is not None and inst["h"].value in self._batch_key:
-            self.release()        # the batch is a view over its hierarchies: drop it first
+        hv = inst["h"].value
+        if self._batch is not None and hv in self._members:   # the batch holds the hierarchy: retire it first
+            idx = self._members.index(hv)
+            self.pff.batch_retire(self._batch, idx)
+            self._members.pop(idx)
         self.pff.destroy_hierarchy(inst["h"])
 
 
@@ -235,6 +256,8 @@ class Server:
                     time.sleep(max(0.0, min(idle_sleep, pending[0].arrival - self.now())))
                 continue
             self.tick()
+        if hasattr(self.backend, "release"):
+            self.backend.release()
         return self.results
 
 

@@ -175,3 +175,57 @@ def test_batch_fp64_vcycle_and_solve_match_single():
     finally:
         for x in xs:
             pff.destroy_hierarchy(x["h"])
+
+
+def test_batch_submit_retire_poll():
+    """Continuous batching through the ABI: an empty batch, instances submitted and retired between
+    Newton steps; each instance's step equals the single-instance step (active set exact, same
+    iterations +-1, 1e-6), poll returns the last infos, and misuse is rejected."""
+    xs = make_instances(SIZES[:4], seed=3)
+    ref = make_instances(SIZES[:4], seed=3)
+    try:
+        b = pff.batch_create([])
+        try:
+            with pytest.raises(pff.PffError) as e:
+                pff.batch_newton_step(b, [])
+            assert e.value.status == pff.ESTATE
+            for x in xs[:3]:
+                pff.batch_submit(b, x["h"])
+            assert pff.batch_size(b) == 3
+            with pytest.raises(pff.PffError) as e:
+                pff.batch_submit(b, xs[0]["h"])            # already in the batch
+            assert e.value.status == pff.EINVAL
+            pff.batch_retire(b, 1)                         # xs[1] leaves before any step
+            pff.batch_submit(b, xs[3]["h"])                # xs[3] joins: order is xs[0], xs[2], xs[3]
+            members = [0, 2, 3]
+            Us = [xs[k]["U"].clone() for k in members]
+            infos = pff.batch_newton_step(b, Us)
+            for j, k in enumerate(members):
+                Ur = ref[k]["U"].clone()
+                ir = pff.newton_step(ref[k]["h"], Ur)
+                assert infos[j].n_active == ir.n_active and abs(infos[j].solve.iterations - ir.solve.iterations) <= 1
+                assert rel(Us[j], Ur) <= 1e-6
+                p = pff.batch_poll(b, j)
+                assert p.n_active == infos[j].n_active and p.solve.iterations == infos[j].solve.iterations
+            pff.batch_retire(b, 0)
+            assert pff.batch_size(b) == 2
+            with pytest.raises(pff.PffError) as e:
+                pff.batch_retire(b, 5)
+            assert e.value.status == pff.EINVAL
+            infos2 = pff.batch_newton_step(b, [Us[1], Us[2]])
+            assert all(i.solve.converged for i in infos2)
+        finally:
+            pff.batch_destroy(b)
+        w = W.small(W.config_3d_penny(), 8, 2)
+        h64 = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, 2, w.lo, w.hi), pff.default_params(mg_precision=64))
+        b = pff.batch_create([xs[0]["h"]])
+        try:
+            with pytest.raises(pff.PffError) as e:
+                pff.batch_submit(b, h64)                   # another V-cycle precision
+            assert e.value.status == pff.EINVAL
+        finally:
+            pff.batch_destroy(b)
+            pff.destroy_hierarchy(h64)
+    finally:
+        for x in xs + ref:
+            pff.destroy_hierarchy(x["h"])
