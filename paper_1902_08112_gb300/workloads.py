@@ -12,6 +12,8 @@ Recipes (seed 12345 unless stated):
   * 3D multi-crack: 8 penny cracks, centres U[-6,6]^3, normals N(0,I) normalised, radii U[1,2].
   * batch instances: N^3 Q1 with N in {16,24,32,48,64}, 1-6 cracks of radius U[0.5,2],
     p ~ U[5e-4, 2e-3].
+  * 3D penny crack in SI units: a 1 cm box [-5e-3,5e-3]^3 m, E=2.1e11 Pa, nu=0.3, Gc=2.7e3 J/m^2,
+    p=1e7 Pa, crack disk of radius 1 mm; kappa=1e-10, eps=2h.
 h is the cell diameter (sqrt(dim) times the edge length); the paper calls h the element
 diameter in its first example.
 """
@@ -172,6 +174,15 @@ def config_2d_lshape(n: int = 32, n_levels: int = 4, deg: int = 1, loading: str 
 def config_3d_penny(n: int = 128, deg: int = 1, n_levels: int = 5) -> Workload:
     w = Workload("3d_penny", 3, deg, (n, n, n), n_levels, (-10.0,) * 3, (10.0,) * 3)
     w.cracks = [Crack((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), 1.0)]
+    return w.finalize()
+
+
+def config_3d_penny_si(n: int = 16, deg: int = 1, n_levels: int = 3, pressure: float = 1e7) -> Workload:
+    """The penny-crack geometry in SI units (steel-like material in a 1 cm box): coefficients spanning
+    about 30 decades, residual entries of order 1e-4 N beside rounding noise of order 1e-20."""
+    w = Workload("3d_penny_si", 3, deg, (n, n, n), n_levels, (-5e-3,) * 3, (5e-3,) * 3, E=2.1e11, nu=0.3,
+                 Gc=2.7e3, pressure=pressure)
+    w.cracks = [Crack((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), 1e-3)]
     return w.finalize()
 
 

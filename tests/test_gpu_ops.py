@@ -127,6 +127,12 @@ CASES = {
     "3d_q2_fast": (lambda: W.small(W.config_3d_penny(deg=2), 12, 3), 0),
     "3d_q2_fast_modulus": (lambda: W.small(W.config_3d_penny(deg=2), 8, 2), 0, True),
     "3d_q2_fast_lshape": (lambda: W.small(W.config_3d_lshape(deg=2), (8, 8, 4), 2), 0),
+    # SI units (steel in a 1 cm box): coefficients over ~30 decades, inside the float exponent range
+    # that the double-float operators inherit
+    "3d_q1_si_units": (lambda: W.config_3d_penny_si(12, 1, 2), 0),
+    "3d_q1_cell64_si_units": (lambda: W.config_3d_penny_si(12, 1, 2), 6),
+    "3d_q1_generic_si_units": (lambda: W.config_3d_penny_si(8, 1, 2), 1),
+    "3d_q2_si_units": (lambda: W.config_3d_penny_si(6, 2, 2), 0),
 }
 
 

@@ -109,6 +109,48 @@ def test_newton_step_matches_oracle(mgp):
         pff.destroy_hierarchy(h)
 
 
+@pytest.mark.parametrize("mgp", [64, 32])
+def test_newton_steps_in_si_units(mgp):
+    """Algorithm 1 on the penny crack in SI units (steel in a 1 cm box, p = 1e9 Pa so that the active set
+    moves over five steps) with the tie band on the residual scale (tie_scale 1): where the exact value is
+    0 the residual entries are ~1e-20 J and the genuine ones ~1e-4 J.  eps_as = 1e-9: the double-float
+    residual's rounding floor at the converged iterate is ~1e-10 here (FP64's ~5e-12), so the paper's
+    absolute 1e-10 (nondimensional units) sits at the floor; 1e-9 still splits noise and genuine tie-band
+    values by many decades.  Every step matches the oracle: active set size and changes, residual norm
+    (to 1e-12 of the first step's, the floor), FGMRES iterations, the iterate; both converge together."""
+    tol = 1e-9
+    w = W.config_3d_penny_si(16, 1, 3, pressure=1e9)
+    U, po, pt = W.initial_state(w)
+    prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu, Gc=w.Gc,
+                             mg_precision=mgp, tie_scale=1, tol_as=tol)
+    h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm)
+    try:
+        pff.set_state(h, t(U), t(po), t(pt))
+        m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+        dmask = fem.dirichlet_face_mask(m, 0x3F)
+        Ud, Uo, prev, res0 = t(U), U.copy(), None, None
+        for k in range(8):
+            info = pff.newton_step(h, Ud, allow_noconv=True)
+            Uo_new, oi = pdas.newton_step(m, ph, 3, Uo, po, pt, dmask, prev, tol_as=tol, tie_scale=1)
+            res0 = oi.res_norm if res0 is None else res0
+            assert info.n_active == int(oi.active.sum()), k
+            assert info.n_changed == oi.n_changed, k
+            assert info.res_norm == pytest.approx(oi.res_norm, rel=1e-6, abs=1e-12 * res0), k
+            assert bool(info.converged) == oi.converged, k
+            slack = 1 if mgp == 32 else 0
+            assert abs(info.solve.iterations - oi.gmres_its) <= max(slack, math.floor(0.1 * oi.gmres_its)), k
+            Ug = Ud.cpu().numpy()
+            assert np.linalg.norm(Ug - Uo_new) <= 1e-6 * np.linalg.norm(Uo_new), k
+            Uo, prev = Uo_new, oi.active
+            Ud = t(Uo)
+            if oi.converged:
+                break
+        assert oi.converged and k >= 2
+    finally:
+        pff.destroy_hierarchy(h)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_full_size_q2_apply_sampled_rows(prec):
     """The 3D penny workload on 64^3 Q2 hexahedra (8.6M DoFs, the Q2 size of the benchmark workload),
