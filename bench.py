@@ -223,6 +223,93 @@ def cpu_baseline():
                       f"CSR product in {cores} row blocks on {cores} threads, median of 5"}
 
 
+SMALL_SOLVE = (32, 3)     # 3D penny recipe on 32^3 Q1 with 3 levels: the solve both the GPU and the oracle time
+
+
+def bench_small_solve(dev, pending: list):
+    """The GPU side of the solve comparison with the oracle: V-cycle and 1e-8 FGMRES solve (FP32-MG and
+    FP64-MG) of the system G~ x = -A(U) on the penny recipe at 32^3 Q1 (3 levels, smooth displacement
+    state, the active set of Algorithm 1).  The oracle's times for the same system are added by the CPU
+    leg (oracle_solve_times)."""
+    import torch
+    from paper_1902_08112_gb300 import pff, workloads as W
+    n, levels = SMALL_SOLVE
+    w = W.small(W.config_3d_penny(), n, levels)
+    U, po, pt = W.initial_state(w, displacement="smooth")
+    stream = torch.cuda.Stream(device=dev)
+    rec = {"workload": f"3d_penny_q1_{n} ({levels} levels, {w.n_dofs} DoFs)", "rtol": 1e-8}
+    for mgp in (32, 64):
+        prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
+                                 mg_precision=mgp)
+        h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, levels, w.lo, w.hi), prm, stream)
+        try:
+            with torch.cuda.stream(stream):
+                Ud, pod, ptd = (torch.from_numpy(a).to(dev) for a in (U, po, pt))
+                R = torch.empty(w.n_dofs, dtype=torch.float64, device=dev)
+                z = torch.empty_like(R)
+                xs = torch.zeros_like(R)
+            stream.synchronize()
+            pff.set_state(h, Ud, pod, ptd)
+            na, _ = pff.update_active_set(h)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            pff.setup(h)
+            stream.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            pff.residual(h, R)
+            pff.vcycle(h, R, z)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(10):
+                pff.vcycle(h, R, z)
+            stream.synchronize()
+            vc_ms = (time.perf_counter() - t0) * 1e3 / 10
+            t0 = time.perf_counter()
+            info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=200, allow_noconv=True)
+            stream.synchronize()
+            rec[f"gpu_fp{mgp}_mg"] = {"setup_ms": setup_ms, "vcycle_ms": vc_ms,
+                                      "solve_ms": (time.perf_counter() - t0) * 1e3, "iterations": info.iterations,
+                                      "rel_res": info.res_final / max(info.res0, 1e-300), "n_active": na}
+        finally:
+            pff.destroy_hierarchy(h)
+    pending.append({"solve": rec, "w": w, "U": U, "po": po, "pt": pt})
+    return rec
+
+
+def oracle_solve_times(pending: list):
+    """The oracle's side of the solve comparison (CPU leg): the same system, assembled element by element
+    with the active set of Algorithm 1, its V-cycle (FP64, Chebyshev-Jacobi) and FGMRES to 1e-8, timed on
+    the host; setup = assembly of every level plus the eigenvalue estimates."""
+    from oracle import fem, krylov, multigrid as mg, pdas
+    for p in pending:
+        if "solve" not in p:
+            continue
+        w, U, po, pt = p["w"], p["U"], p["po"], p["pt"]
+        m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+        t0 = time.perf_counter()
+        R = -fem.residual_A(m, ph, U, pt)
+        dmask = fem.dirichlet_face_mask(m, w.dirichlet_faces)
+        act = pdas.active_set(m, R, fem.lumped_mass(m), U, po, 100.0, 1e-10, fixed=(dmask & fem.BIT_PHI_DIR) != 0)
+        mask = dmask | (act * fem.BIT_ACTIVE).astype(np.uint8)
+        lv = mg.build_levels(m, w.n_levels, ph, U, pt, mask)
+        mg.estimate_levels(lv, 12345, 10)
+        setup_s = time.perf_counter() - t0
+        prm = mg.MGParams()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            mg.precondition(lv, R, prm)
+        vc_s = (time.perf_counter() - t0) / 3
+        G = lv[-1].G
+        t0 = time.perf_counter()
+        _, its, res, res0, _ = krylov.fgmres(lambda v: G @ v, R, lambda v: mg.precondition(lv, v, prm),
+                                             rtol=1e-8, restart=30, maxit=200)
+        p["solve"]["oracle_fp64_mg"] = {"setup_ms": setup_s * 1e3, "vcycle_ms": vc_s * 1e3,
+                                        "solve_ms": (time.perf_counter() - t0) * 1e3, "iterations": its,
+                                        "rel_res": res / max(res0, 1e-300), "n_active": int(act.sum()),
+                                        "threads": 1}
+
+
 def oracle_rows_check(pending: list):
     """Error of the GPU's multi-crack solutions against the FP64 oracle: the oracle's own rows (element by
     element, full Gauss quadrature) of the eliminated Jacobian applied to each solution on its seeded rows,
@@ -230,12 +317,13 @@ def oracle_rows_check(pending: list):
     one GPU), after the GPU sections."""
     from oracle import fem
     for p in pending:
+        if "rows" not in p:
+            continue
         w = p["w"]
         m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
         ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
         Gx = fem.apply_rows(m, ph, p["U"], p["pt"], p["mask"], p["x"], p["rows"])
         p["out"]["oracle_rows_rel_residual"] = float(np.abs(p["b_rows"] - Gx).max() / p["b_max"])
-    pending.clear()
 
 
 def bench_batch(count: int, dev):
@@ -615,6 +703,7 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="cells per edge of the 3D penny workload")
     ap.add_argument("--levels", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small-solve", type=int, default=1, help="GPU vs oracle solve on the 32^3 penny (0: off)")
     ap.add_argument("--batch", type=int, default=256, help="instances in the batching measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving measurement (0: skip)")
     ap.add_argument("--multi", type=int, default=256, help="cells per edge of the multi-crack measurement (0: skip)")
@@ -835,6 +924,8 @@ def main():
     if args.serve > 0:
         line["serve"] = bench_serve(args.serve)
     pending = []
+    if args.small_solve:
+        line["solve_small"] = bench_small_solve(dev, pending)
     if args.multi > 0:
         line["multi_crack"] = bench_multi(args.multi, dev, pending)
     if args.variants > 0:
@@ -847,6 +938,7 @@ def main():
         # the CPU leg: the oracle on the host cores, timed (cpu_baseline), and its rows of the multi-crack
         # systems applied to the GPU's solutions
         oracle_rows_check(pending)
+        oracle_solve_times(pending)
         line["cpu_baseline"] = cpu_baseline()
     pending.clear()
     if rank == 0:
