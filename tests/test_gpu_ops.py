@@ -8,6 +8,8 @@ Tolerances: FP64 operators 1e-12 relative (normwise, the required parity); FP32 
 pieces built on the FP64 operators 1e-9 (eigenvalue estimates enter through Chebyshev
 coefficients; 10 CG steps amplify rounding).
 """
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -87,6 +89,14 @@ class Case:
         pff.destroy_hierarchy(self.h)
 
 
+def _aniso(dim, deg, cells, levels):
+    """Cells with a different edge length per axis (0.25, 1/6, 0.3125 at the finest level), an
+    off-centre box and a crack inside it."""
+    w = W.Workload("aniso", dim, deg, tuple(cells[:dim]), levels, (-2.0, -1.0, -0.5)[:dim], (3.0, 1.0, 2.0)[:dim])
+    w.cracks = [W.Crack((0.5, 0.0, 0.5)[:dim], (0.0, 0.0, 1.0)[:dim] if dim == 3 else (0.0, 1.0), 0.8)]
+    return w.finalize()
+
+
 # (workload, kernel variant): 0 = Q1 fast path (df64 / FP32 with stored linearisation data),
 # 1 = generic kernels, 2 = one thread per Gauss point, 3 = one thread per cell, 5 = Gauss-point
 # lanes adding to y with global atomics, 6 = FP64 per cell with shared-memory derivatives, 7 = the
@@ -127,6 +137,22 @@ CASES = {
     "3d_q2_fast": (lambda: W.small(W.config_3d_penny(deg=2), 12, 3), 0),
     "3d_q2_fast_modulus": (lambda: W.small(W.config_3d_penny(deg=2), 8, 2), 0, True),
     "3d_q2_fast_lshape": (lambda: W.small(W.config_3d_lshape(deg=2), (8, 8, 4), 2), 0),
+    # anisotropic cells (a per-axis length taken from the wrong axis fails these)
+    "3d_q1_aniso": (lambda: _aniso(3, 1, (20, 12, 8), 2), 0),
+    "3d_q1_cell64_aniso": (lambda: _aniso(3, 1, (20, 12, 8), 2), 6),
+    "3d_q1_cell32_aniso": (lambda: _aniso(3, 1, (20, 12, 8), 2), 7),
+    "3d_q1_generic_aniso": (lambda: _aniso(3, 1, (8, 4, 4), 2), 1),
+    "3d_q1_lanes_aniso": (lambda: _aniso(3, 1, (8, 4, 4), 2), 2),
+    "3d_q2_aniso": (lambda: _aniso(3, 2, (8, 4, 4), 2), 0),
+    "2d_q1_aniso": (lambda: _aniso(2, 1, (20, 12), 2), 0),
+    "2d_q2_aniso": (lambda: _aniso(2, 2, (8, 4), 2), 1),
+    # degenerate cases: one level with odd cell counts, no Dirichlet face, every phi DoF active, none
+    "3d_q1_one_level": (lambda: W.small(W.config_3d_penny(), (5, 3, 7), 1), 0),
+    "3d_q1_cell64_one_level": (lambda: W.small(W.config_3d_penny(), (17, 5, 3), 1), 6),
+    "3d_q1_no_dirichlet": (lambda: replace(W.small(W.config_3d_penny(), 8, 2), dirichlet_faces=0), 0),
+    "3d_q1_all_active": (lambda: W.small(W.config_3d_penny(), 8, 2), 0, False, 0, 1.0),
+    "3d_q1_none_active": (lambda: W.small(W.config_3d_penny(), 8, 2), 6, False, 0, 0.0),
+    "3d_q2_all_active": (lambda: W.small(W.config_3d_penny(deg=2), 4, 2), 0, False, 0, 1.0),
     # SI units (steel in a 1 cm box): coefficients over ~30 decades, inside the float exponent range
     # that the double-float operators inherit
     "3d_q1_si_units": (lambda: W.config_3d_penny_si(12, 1, 2), 0),
@@ -139,7 +165,8 @@ CASES = {
 @pytest.fixture(scope="module", params=sorted(CASES))
 def case(request):
     make_w, variant, *rest = CASES[request.param]
-    c = Case(make_w(), variant=variant, modulus=bool(rest and rest[0]), split=rest[1] if len(rest) > 1 else 0)
+    c = Case(make_w(), variant=variant, modulus=bool(rest and rest[0]), split=rest[1] if len(rest) > 1 else 0,
+             active_fraction=rest[2] if len(rest) > 2 else 0.1)
     yield c
     c.close()
 

@@ -153,6 +153,50 @@ def test_jacobian_is_residual_derivative(dim, deg, f):
         assert np.linalg.norm(fd - Gv) <= 1e-7 * np.linalg.norm(Gv)
 
 
+def _aniso_mesh(dim, deg):
+    """Cells of three different edge lengths (0.6, 2/3, 0.35) on an off-centre box."""
+    return fem.Mesh(dim, deg, (2, 3, 2)[:dim], (-0.5, 0.0, 0.2)[:dim], (0.7, 2.0, 0.9)[:dim])
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_anisotropic_cells(dim, deg):
+    """On cells with a different edge length per axis: the energy of an affine u with phi = 1 is
+    (E_s + p tr e)|D|, the residual is the energy's gradient and the Jacobian the residual's derivative
+    (central differences), and the u-rows of an affine field vanish at interior nodes.  A per-axis
+    length taken from the wrong axis (in a derivative, a Gauss weight or a lumped mass) breaks one of
+    them."""
+    m = _aniso_mesh(dim, deg)
+    vol = np.prod([(0.7, 2.0, 0.9)[a] - (-0.5, 0.0, 0.2)[a] for a in range(dim)])
+    ph = fem.Phys(E=1.5, nu=0.2, p=0.3, eps=0.4, Gc=2.0, kappa=1e-3)
+    mu, lam = fem.lame(1.5, 0.2)
+    rng = np.random.default_rng(21)
+    A = 0.01 * rng.normal(size=(dim, dim))
+    U = np.concatenate([_affine_u(m, A, rng.normal(size=dim)), np.ones(m.n_nodes)])
+    e = 0.5 * (A + A.T)
+    Es = 0.5 * lam * np.trace(e) ** 2 + mu * np.sum(e * e)
+    assert fem.energy(m, ph, U) == pytest.approx((Es + ph.p * np.trace(A)) * vol, rel=1e-12)
+    Ares = fem.residual_A(m, ph, U, np.ones(m.n_nodes))
+    interior = fem.dirichlet_face_mask(m, 0x3F) == 0
+    if interior.any():
+        for c in range(dim):
+            assert np.abs(Ares[c * m.n_nodes:(c + 1) * m.n_nodes][interior]).max() < 1e-12
+    assert fem.lumped_mass(m).sum() == pytest.approx(vol, rel=1e-14)
+    U = _rand_state(m, 22)
+    phi = U[dim * m.n_nodes:]
+    R = fem.residual_A(m, ph, U, phi)
+    for _ in range(2):
+        v = rng.standard_normal(U.size)
+        fd = (fem.energy(m, ph, U + 1e-5 * v) - fem.energy(m, ph, U - 1e-5 * v)) / 2e-5
+        assert fd == pytest.approx(R @ v, rel=1e-7)
+    ptil = rng.uniform(0, 1, m.n_nodes)
+    G = fem.assemble(m, ph, U, ptil, np.zeros(m.n_nodes, np.uint8))
+    for _ in range(2):
+        v = rng.standard_normal(U.size)
+        fd = (fem.residual_A(m, ph, U + 1e-6 * v, ptil) - fem.residual_A(m, ph, U - 1e-6 * v, ptil)) / 2e-6
+        Gv = G @ v
+        assert np.linalg.norm(fd - Gv) <= 1e-7 * np.linalg.norm(Gv)
+
+
 @pytest.mark.parametrize("dim,deg", [(2, 1), (3, 1), (3, 2)])
 def test_block_structure(dim, deg):
     """G_uphi = 0 exactly (phi~ frozen in the u-equation, Sec. 3.3) and G_uu symmetric."""
