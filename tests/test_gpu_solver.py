@@ -42,12 +42,21 @@ def oracle_system(w, U, po, pt):
     return m, ph, act, Rt, lv
 
 
+def _aniso():
+    """Cells of edge lengths 0.3125, 0.25 and 0.1875 (16 x 8 x 8 cells, 3 levels) around a crack."""
+    w = W.Workload("aniso", 3, 1, (16, 8, 8), 3, (-2.0, -1.0, -0.5), (3.0, 1.0, 1.0))
+    w.cracks = [W.Crack((0.5, 0.0, 0.25), (0.0, 0.0, 1.0), 0.8)]
+    return w.finalize()
+
+
 SOLVE_CASES = {
     "2d_q1_64": lambda: W.config_2d_single_crack(),            # the 2D config itself (3 levels)
     "3d_q1_16": lambda: W.small(W.config_3d_penny(), 16, 3),
     "3d_q2_8": lambda: W.small(W.config_3d_penny(deg=2), 8, 2),
     "3d_q2_12": lambda: W.small(W.config_3d_penny(deg=2), 12, 3),
     "3d_lshape_32": lambda: W.config_3d_lshape(32, 3),
+    "3d_q1_aniso": lambda: _aniso(),
+    "3d_q1_one_level": lambda: W.small(W.config_3d_penny(), 8, 1),
 }
 
 

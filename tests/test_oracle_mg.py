@@ -224,6 +224,53 @@ def test_sneddon_crack_volume_2d():
     assert vol_pf > 0
 
 
+def test_sneddon_crack_volume_3d():
+    """Loose physics pin in 3D: a pressurised penny crack of radius a in an unbounded solid opens by
+    Sneddon's volume V = 16 (1 - nu^2) p a^3 / (3 E).  One octant of [-4,4]^3 on 32^3 Q1 cells with the
+    symmetry planes x = 0, y = 0, z = 0 (u_x, u_y, u_z fixed there, the crack lying in z = 0) and the far
+    faces clamped; phi fixed at the initial crack.  Phase-field volume = int u . grad(phi^2) over the
+    octant, times 8; a from the discrete phase field as in 2D.  O(eps) and finite-domain bias remain
+    (4 % here, 2.4 % on 48^3 cells of [-6,6]^3), so 8 % is asked."""
+    n, L = 32, 4.0
+    w = W.Workload("penny_octant", 3, 1, (n, n, n), 3, (0.0, 0.0, 0.0), (L, L, L), pressure=1e-3)
+    w.cracks = [W.Crack((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), 1.0)]
+    w = w.finalize()
+    m = fem.Mesh(3, 1, w.n_cells, w.lo, w.hi)
+    ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+    U, po, pt = W.initial_state(w)
+    X = m.node_coords()
+    nn = m.n_nodes
+    mask = np.zeros(nn, np.uint8)
+    for a in range(3):
+        mask |= np.where(np.abs(X[:, a]) < 1e-12, 1 << a, 0).astype(np.uint8)
+    far = np.zeros(nn, bool)
+    for a in range(3):
+        far |= np.abs(X[:, a] - L) < 1e-12
+    mask |= np.where(far, 7, 0).astype(np.uint8)
+    mask |= np.uint8(fem.BIT_PHI_DIR)
+    R = -fem.residual_A(m, ph, U, pt)
+    R[fem.constrained_dofs(m, mask)] = 0.0
+    lv = mg.build_levels(m, 3, ph, U, pt, mask)
+    mg.estimate_levels(lv, 12345, 10)
+    G = lv[-1].G
+    dU, its, res, res0, _ = krylov.fgmres(lambda v: G @ v, R, lambda v: mg.precondition(lv, v, mg.MGParams()),
+                                          rtol=1e-10, restart=30, maxit=200)
+    assert res <= 1e-10 * res0 * 1.0001
+    U1 = U + dU
+    # the u-rows of A at u = 0, p = 1, phi~ = phi are (phi^2, div Phi_i): V_pf = -sum_i u_i A_i
+    ph1 = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=1.0)
+    Ub = U.copy()
+    Ub[: 3 * nn] = 0.0
+    Au = fem.residual_A(m, ph1, Ub, U[3 * nn:])[: 3 * nn]
+    vol_pf = -8.0 * float(Au @ U1[: 3 * nn])
+    phi = U[3 * nn:]
+    on_plane = np.abs(X[:, 2]) < 1e-12
+    a_eff = np.hypot(X[:, 0], X[:, 1])[on_plane & (phi == 0.0)].max() + 0.5 * w.edge
+    vol = 16 * (1 - w.nu ** 2) * w.pressure * a_eff ** 3 / (3 * w.E)
+    assert vol_pf > 0
+    assert vol_pf == pytest.approx(vol, rel=0.08)
+
+
 @pytest.mark.parametrize("tie_scale", [0, 1])
 def test_active_set_complementarity_at_convergence(tie_scale):
     """At PDAS convergence: phi <= phi_old, phi = phi_old on the active set, the multiplier
