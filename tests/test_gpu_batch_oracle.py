@@ -1,7 +1,7 @@
 """Batched and served paths against the oracle (not against the single-instance GPU path).
 
-An uneven mix of five 3D instances (8^3 .. 24^3 cells, 1 to 3 levels, eps = 2h or 4h, seeded
-pressures and crack layouts) runs through the batch ABI; per instance:
+An uneven mix of six 3D instances (8^3 .. 24^3 cells and one of 16 x 8 x 12 cells with three
+different edge lengths, 1 to 3 levels, eps = 2h or 4h, seeded pressures and crack layouts) runs through the batch ABI; per instance:
   - the batched level operators on every level, in both kernel families (small-level kernels and
     per-cell kernels), against the oracle's assembled G_l x: FP64-accurate to 1e-12 and FP32 to 2e-5
     per block (displacement, phase field), elementwise against the block's largest entry too;
@@ -12,6 +12,7 @@ pressures and crack layouts) runs through the batch ABI; per instance:
 And two served requests (a crack instance and the displacement-driven L-shaped panel), two load steps
 each in one mix, against the oracle's load steps (Algorithm 1 to its stop test) to 1e-6."""
 import math
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -24,8 +25,10 @@ from paper_1902_08112_gb300 import pff, serve, workloads as W  # noqa: E402
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
-# (cells per edge, levels, eps factor)
-MIX = [(8, 1, 2.0), (12, 2, 4.0), (16, 3, 2.0), (20, 2, 4.0), (24, 3, 2.0)]
+# (cells per edge, levels, eps factor); the last instance has cells of three edge lengths on a
+# non-cubic box
+MIX = [(8, 1, 2.0), (12, 2, 4.0), (16, 3, 2.0), (20, 2, 4.0), (24, 3, 2.0), ((16, 8, 12), 2, 2.0)]
+ANISO_BOX = ((-10.0, -6.0, -8.0), (10.0, 6.0, 4.0))
 
 
 def t(a):
@@ -49,6 +52,8 @@ def mix_workloads(seed=0):
         base = W.config_3d_penny()
         base.eps_factor = ef
         w = W.small(base, n, L)
+        if not isinstance(n, int):
+            w = replace(w, lo=ANISO_BOX[0], hi=ANISO_BOX[1], eps=0.0).finalize()
         w.pressure = float(rng.uniform(5e-3, 2e-2))
         w.cracks = [W.Crack(tuple(rng.uniform(-4, 4, 3)), (0.0, 0.0, 1.0), float(rng.uniform(1.5, 3.5)))]
         out.append(w)
