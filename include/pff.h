@@ -201,7 +201,10 @@ pff_status pff_set_kernel_variant(pff_hierarchy* h, int variant);
 /* Set the linearisation point.  U: FP64 [u | phi] (n_dofs), phi_old: FP64 (n_nodes) = the
  * irreversibility bound, phi_tilde: FP64 (n_nodes) = the extrapolation used in the
  * displacement equation (Eq. (semilinear)).  The library copies them, restricts U and
- * phi_tilde to every coarser level by coincident nodes (Sec. 4.2), and keeps FP32 copies.
+ * phi_tilde to every coarser level by coincident nodes (Sec. 4.2), and keeps FP32 copies.  On
+ * Q2 levels (an extension of the paper) phi_tilde of a coarse node is instead the maximum of the
+ * fine phi_tilde over the fine nodes at most one lattice step from the coincident node along
+ * every axis, so that a coarse cell is not weaker than the fine cells it covers.
  * The current active set is kept.
  * u_dirichlet (nullable): device FP64 of at least dim * n_nodes entries in the layout of U's
  * displacement blocks: prescribed displacement values on the Dirichlet DoFs (the faces of

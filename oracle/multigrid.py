@@ -6,7 +6,11 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
    function (the canonical prolongation of Sec. 3.2), restriction of residuals R = P^T.
  - Level state, extrapolation and active set carried to the coarse levels by restriction
    onto coincident nodes (Sec. 4.2): every coarse node is also a fine node, so the active
-   indicator stays in {0,1}.
+   indicator stays in {0,1}.  Q2 levels (an extension; the paper uses Q1) take the extrapolated
+   phase field phi~ of a coarse node as the maximum of the fine phi~ over the fine nodes at most one
+   fine node spacing away from it (the 3^d block around the coincident node, cut at the boundary):
+   a Q2 field carries values at edge, face and cell-centre nodes that injection drops, and a coarse
+   cell that loses them becomes kappa-weak where the fine cells are stiff.
  - Level operators G_l(U_l) at the restricted state (Sec. 4.2), assembled by the C oracle.
  - Chebyshev-Jacobi smoother on each diagonal block (Sec. 3.2.1, block-diagonal S_full of
    Sec. 3.3), range [1.2 l/5, 1.2 l] with l from 10 Jacobi-preconditioned CG steps.  The
@@ -98,6 +102,24 @@ class Level:
     P: sp.csr_matrix | None = None   # prolongation from the next coarser level
 
 
+def neighbourhood_max(mesh_c: fem.Mesh, mesh_f: fem.Mesh, pf: np.ndarray) -> np.ndarray:
+    """For every coarse node, the maximum of the fine nodal field pf over the fine nodes whose lattice
+    index differs from the coincident node's by at most 1 along every axis (cut at the boundary)."""
+    npf = mesh_f.nodes_per_axis()
+    a = np.asarray(pf, dtype=np.float64).reshape(tuple(npf[::-1]))
+    out = a.copy()
+    for ax in range(mesh_f.dim):
+        axis = mesh_f.dim - 1 - ax              # array axis of mesh axis 'ax' (x is the last)
+        cur = out.copy()
+        lo = [slice(None)] * mesh_f.dim
+        hi = [slice(None)] * mesh_f.dim
+        lo[axis], hi[axis] = slice(0, -1), slice(1, None)
+        np.maximum(cur[tuple(lo)], out[tuple(hi)], out=cur[tuple(lo)])      # neighbour at +1
+        np.maximum(cur[tuple(hi)], out[tuple(lo)], out=cur[tuple(hi)])      # neighbour at -1
+        out = cur
+    return out.ravel()[injection_index(mesh_c, mesh_f)]
+
+
 def coarsen_cell_field(mesh: fem.Mesh, s: np.ndarray) -> np.ndarray:
     """Per-cell field on the next coarser mesh: the mean over the 2^d fine cells of each coarse
     cell (how a varying modulus enters the rediscretised coarse operators of Sec. 4.2)."""
@@ -131,7 +153,8 @@ def build_levels(mesh: fem.Mesh, n_levels: int, phys: fem.Phys, U, ptil, mask) -
         Uf, pf, mf = states[l + 1]
         nnf = meshes[l + 1].n_nodes
         Uc = np.concatenate([Uf[c * nnf + inj] for c in range(mesh.ncomp)])
-        states[l] = (Uc, pf[inj], mf[inj])
+        pc = neighbourhood_max(meshes[l], meshes[l + 1], pf) if mesh.deg == 2 else pf[inj]
+        states[l] = (Uc, pc, mf[inj])
     levels = []
     for l in range(n_levels):
         m = meshes[l]

@@ -37,16 +37,30 @@ __device__ __forceinline__ int64_t node_id(const Geom& g, int i, int j, int k) {
 }
 
 // ---------------------------------------------------------------- state restriction
+// Coincident-node injection of U, phi~ and the masks (Sec. 4.2).  On Q2 levels phi~ of a coarse node
+// is the maximum of the fine phi~ over the fine nodes at most one lattice step away along every axis
+// (the 3^d block around the coincident node, cut at the boundary): the Q2 field's values at edge, face
+// and cell-centre nodes, which injection drops, keep the coarse cells as stiff as the fine ones.
 __global__ void k_restrict_state(Geom gc, Geom gf, const double* __restrict__ Uf, const double* __restrict__ ptf,
                                  const uint8_t* __restrict__ maskf, double* __restrict__ Uc,
                                  double* __restrict__ ptc, uint8_t* __restrict__ maskc) {
     GRID_STRIDE(n, gc.n_nodes) {
         int i, j, k;
         node_ijk(gc, n, i, j, k);
-        const int64_t f = node_id(gf, 2 * i, 2 * j, gc.dim == 3 ? 2 * k : 0);
+        const int fk0 = gc.dim == 3 ? 2 * k : 0;
+        const int64_t f = node_id(gf, 2 * i, 2 * j, fk0);
         for (int c = 0; c <= gc.dim; ++c) Uc[c * gc.n_nodes + n] = Uf[c * gf.n_nodes + f];
-        ptc[n] = ptf[f];
         maskc[n] = maskf[f];
+        double p = ptf[f];
+        if (gc.deg == 2) {
+            const int k0 = gc.dim == 3 ? max(fk0 - 1, 0) : 0, k1 = gc.dim == 3 ? min(fk0 + 1, gf.nn[2] - 1) : 0;
+            const int j0 = max(2 * j - 1, 0), j1 = min(2 * j + 1, gf.nn[1] - 1);
+            const int i0 = max(2 * i - 1, 0), i1 = min(2 * i + 1, gf.nn[0] - 1);
+            for (int kk = k0; kk <= k1; ++kk)
+                for (int jj = j0; jj <= j1; ++jj)
+                    for (int ii = i0; ii <= i1; ++ii) p = fmax(p, ptf[node_id(gf, ii, jj, kk)]);
+        }
+        ptc[n] = p;
     }
 }
 

@@ -55,6 +55,7 @@ SOLVE_CASES = {
     "3d_q2_8": lambda: W.small(W.config_3d_penny(deg=2), 8, 2),
     "3d_q2_12": lambda: W.small(W.config_3d_penny(deg=2), 12, 3),
     "3d_lshape_32": lambda: W.config_3d_lshape(32, 3),
+    "3d_q2_multi_8": lambda: W.config_3d_multi(n=8, deg=2, n_levels=3),   # 8 cracks, Q2 coarse phi~ rule
     "3d_q1_aniso": lambda: _aniso(),
     "3d_q1_one_level": lambda: W.small(W.config_3d_penny(), 8, 1),
 }
