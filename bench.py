@@ -338,12 +338,12 @@ def bench_batch(count: int, dev):
     ws = W.batch_instances(count)
     stream = torch.cuda.Stream(device=dev)
 
-    def build(mgp):
+    def build(mgp, phi_max=0):
         hs, Us = [], []
         for w in ws:
             U, po, pt = W.initial_state(w, displacement="smooth")
             prm = pff.default_params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, pressure=w.pressure,
-                                     mg_precision=mgp, seed=w.seed)
+                                     mg_precision=mgp, seed=w.seed, coarse_phi_max=phi_max)
             h = pff.create_hierarchy(pff.make_mesh(3, 1, w.n_cells, w.n_levels, w.lo, w.hi), prm, stream)
             Ud = torch.from_numpy(U).to(dev)
             pff.set_state(h, Ud, torch.from_numpy(po).to(dev), torch.from_numpy(pt).to(dev))
@@ -405,6 +405,11 @@ def bench_batch(count: int, dev):
     ts64, its_s64 = single(hs, Us, U0)
     for h in hs:
         pff.destroy_hierarchy(h)
+    # the option beyond the paper: phi~ on the coarse levels as the neighbourhood maximum
+    hs, _ = build(32, phi_max=1)
+    tbx, infosx, precsx, _ = batched(hs, Us, U0)
+    for h in hs:
+        pff.destroy_hierarchy(h)
     out.update({
         "batched_fp32mg_solves_per_s": count / tb32,
         "batched_fp64mg_solves_per_s": count / tb64,
@@ -415,7 +420,11 @@ def bench_batch(count: int, dev):
         "switched_to_fp64mg": int(sum(p == 64 for p in precs32)),
         "gmres_its_batched_fp64mg": [i.solve.iterations for i in infos64],
         "gmres_its_single_fp32mg": its_s32, "gmres_its_single_fp64mg": its_s64,
-        "all_converged": all(i.solve.converged for i in infos32 + infos64),
+        "all_converged": all(i.solve.converged for i in infos32 + infos64 + infosx),
+        "coarse_phi_max": {"batched_fp32mg_solves_per_s": count / tbx,
+                           "batched_fp32mg_vs_single_fp64mg": ts64 / tbx,
+                           "gmres_its_batched_fp32mg": [i.solve.iterations for i in infosx],
+                           "switched_to_fp64mg": int(sum(p == 64 for p in precsx))},
         "autotuner_fp32mg": tune32, "autotuner_fp64mg": tune64})
     return out
 

@@ -110,6 +110,11 @@ typedef struct {
  *                 residual entry R_i, whose rounding noise does not shrink with the lumped mass
  *                 (M_ii ~ h^d) when the mesh is refined.
  *  newton_rtol    relative tolerance of the linear solve of each pff_newton_step (1e-8).
+ *  coarse_phi_max 0 (default): phi_tilde reaches the coarse Q1 levels by coincident-node injection
+ *                 (Sec. 4.2); 1: on Q1 levels too, a coarse node takes the maximum of the fine
+ *                 phi_tilde over the fine nodes at most one lattice step away along every axis (Q2
+ *                 levels always do, see pff_set_state).  A robustness option beyond the paper: it keeps
+ *                 coarse cells from turning kappa-weak where the fine cells they cover are stiff.
  *  preconditioner 0: P_full = MG(G~), the monolithic V-cycle (Sec. 3.3, default);
  *                 1: P_diag = blockdiag(MG(U~), MG(P~)) (Sec. 3.3): the coupling G_phiu is
  *                 left out of every V-cycle residual and of the coarse solve.  Batches
@@ -130,6 +135,7 @@ typedef struct {
     int split;
     int tie_scale;
     double newton_rtol;
+    int coarse_phi_max;
 } pff_params;
 
 typedef struct {

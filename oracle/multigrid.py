@@ -134,8 +134,9 @@ def coarsen_cell_field(mesh: fem.Mesh, s: np.ndarray) -> np.ndarray:
     return a.ravel()
 
 
-def build_levels(mesh: fem.Mesh, n_levels: int, phys: fem.Phys, U, ptil, mask) -> list:
-    """Level 0 = coarsest, n_levels-1 = finest (the given state and mask)."""
+def build_levels(mesh: fem.Mesh, n_levels: int, phys: fem.Phys, U, ptil, mask, coarse_phi_max: bool = False) -> list:
+    """Level 0 = coarsest, n_levels-1 = finest (the given state and mask).  coarse_phi_max: Q1 levels
+    take phi~ as the neighbourhood maximum too (an option beyond the paper; Q2 levels always do)."""
     meshes = [mesh]
     for _ in range(n_levels - 1):
         meshes.append(meshes[-1].coarsen())
@@ -153,7 +154,7 @@ def build_levels(mesh: fem.Mesh, n_levels: int, phys: fem.Phys, U, ptil, mask) -
         Uf, pf, mf = states[l + 1]
         nnf = meshes[l + 1].n_nodes
         Uc = np.concatenate([Uf[c * nnf + inj] for c in range(mesh.ncomp)])
-        pc = neighbourhood_max(meshes[l], meshes[l + 1], pf) if mesh.deg == 2 else pf[inj]
+        pc = neighbourhood_max(meshes[l], meshes[l + 1], pf) if (mesh.deg == 2 or coarse_phi_max) else pf[inj]
         states[l] = (Uc, pc, mf[inj])
     levels = []
     for l in range(n_levels):
@@ -276,6 +277,7 @@ class MGParams:
     coarse_rtol: float = 1e-6
     coarse_maxit: int = 200
     block_diagonal: bool = False   # P_diag = blockdiag(MG(U~), MG(P~)) of Sec. 3.3 instead of P_full
+    coarse_phi_max: bool = False   # phi~ on coarse Q1 levels: neighbourhood maximum (else injection)
 
 
 def level_operator(lev: Level, prm: MGParams):

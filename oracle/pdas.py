@@ -97,7 +97,7 @@ def newton_step(mesh, phys, n_levels, U, phi_old, ptil, dir_mask, prev_active, c
     act = active_set(mesh, R, M, U, phi_old, c_as, tol_as, fixed=(dir_mask & fem.BIT_PHI_DIR) != 0,
                      tie_scale=tie_scale)
     Rt, mask = eliminated_rhs(mesh, phys, U, ptil, phi_old, dir_mask, act, R)
-    levels = multigrid.build_levels(mesh, n_levels, phys, U, ptil, mask)
+    levels = multigrid.build_levels(mesh, n_levels, phys, U, ptil, mask, coarse_phi_max=prm.coarse_phi_max)
     multigrid.estimate_levels(levels, seed, cg_steps)
     G = levels[-1].G
     dU, its, lin_res, lin_res0, _ = krylov.fgmres(lambda v: G @ v, Rt,

@@ -49,6 +49,7 @@ extern "C" void pff_default_params(pff_params* p) {
     p->split = 0;
     p->tie_scale = 0;
     p->newton_rtol = 1e-8;
+    p->coarse_phi_max = 0;
 }
 
 // Gauss-Legendre rule with deg+1 points mapped to [0,1] and the Lagrange basis on the
@@ -115,6 +116,7 @@ static const char* check_params(const pff_params* p) {
     if (p->split != 0 && p->split != 1) return "split must be 0 (none) or 1 (Miehe)";
     if (p->tie_scale != 0 && p->tie_scale != 1) return "tie_scale must be 0 (lambda) or 1 (residual)";
     if (!(p->newton_rtol > 0 && p->newton_rtol < 1)) return "need 0 < newton_rtol < 1";
+    if (p->coarse_phi_max != 0 && p->coarse_phi_max != 1) return "coarse_phi_max must be 0 or 1";
     return nullptr;
 }
 

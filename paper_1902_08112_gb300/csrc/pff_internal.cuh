@@ -104,7 +104,7 @@ cudaError_t launch_init_masked_nodes(const Geom& g, const uint8_t* mask, int u_b
 // ---------------------------------------------------------------- vector kernels (pff_vec.cu)
 cudaError_t launch_restrict_state(const Geom& gc, const Geom& gf, const double* Uf, const double* ptf,
                                   const uint8_t* maskf, double* Uc, double* ptc, uint8_t* maskc,
-                                  cudaStream_t s);
+                                  bool phi_max_q1, cudaStream_t s);
 cudaError_t launch_cast_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 cudaError_t launch_cast_f32_f64(const float* a, double* b, int64_t n, cudaStream_t s);
 cudaError_t launch_face_mask(const Geom& g, unsigned faces, const uint8_t* extra, uint8_t* mask,

@@ -162,7 +162,8 @@ cudaError_t propagate_state(pff_hierarchy* h, bool values) {
     for (int l = h->L - 2; l >= 0; --l) {
         Level& C = h->lv[l];
         Level& F = h->lv[l + 1];
-        CK(launch_restrict_state(C.g, F.g, F.U64, F.pt64, F.mask, C.U64, C.pt64, C.mask, h->stream));
+        CK(launch_restrict_state(C.g, F.g, F.U64, F.pt64, F.mask, C.U64, C.pt64, C.mask, h->prm.coarse_phi_max != 0,
+                                 h->stream));
     }
     for (auto& L : h->lv) {
         if (!values) break;     // only the masks changed: FP32 copies and Gauss-point data stay valid

@@ -40,10 +40,11 @@ __device__ __forceinline__ int64_t node_id(const Geom& g, int i, int j, int k) {
 // Coincident-node injection of U, phi~ and the masks (Sec. 4.2).  On Q2 levels phi~ of a coarse node
 // is the maximum of the fine phi~ over the fine nodes at most one lattice step away along every axis
 // (the 3^d block around the coincident node, cut at the boundary): the Q2 field's values at edge, face
-// and cell-centre nodes, which injection drops, keep the coarse cells as stiff as the fine ones.
+// and cell-centre nodes, which injection drops, keep the coarse cells as stiff as the fine ones.  Q1
+// levels take the same maximum when phi_max_q1 is set (an option beyond the paper).
 __global__ void k_restrict_state(Geom gc, Geom gf, const double* __restrict__ Uf, const double* __restrict__ ptf,
                                  const uint8_t* __restrict__ maskf, double* __restrict__ Uc,
-                                 double* __restrict__ ptc, uint8_t* __restrict__ maskc) {
+                                 double* __restrict__ ptc, uint8_t* __restrict__ maskc, bool phi_max_q1) {
     GRID_STRIDE(n, gc.n_nodes) {
         int i, j, k;
         node_ijk(gc, n, i, j, k);
@@ -52,7 +53,7 @@ __global__ void k_restrict_state(Geom gc, Geom gf, const double* __restrict__ Uf
         for (int c = 0; c <= gc.dim; ++c) Uc[c * gc.n_nodes + n] = Uf[c * gf.n_nodes + f];
         maskc[n] = maskf[f];
         double p = ptf[f];
-        if (gc.deg == 2) {
+        if (gc.deg == 2 || phi_max_q1) {
             const int k0 = gc.dim == 3 ? max(fk0 - 1, 0) : 0, k1 = gc.dim == 3 ? min(fk0 + 1, gf.nn[2] - 1) : 0;
             const int j0 = max(2 * j - 1, 0), j1 = min(2 * j + 1, gf.nn[1] - 1);
             const int i0 = max(2 * i - 1, 0), i1 = min(2 * i + 1, gf.nn[0] - 1);
@@ -65,8 +66,8 @@ __global__ void k_restrict_state(Geom gc, Geom gf, const double* __restrict__ Uf
 }
 
 cudaError_t launch_restrict_state(const Geom& gc, const Geom& gf, const double* Uf, const double* ptf,
-                                  const uint8_t* maskf, double* Uc, double* ptc, uint8_t* maskc, cudaStream_t s) {
-    k_restrict_state<<<grid_for(gc.n_nodes), kThreads, 0, s>>>(gc, gf, Uf, ptf, maskf, Uc, ptc, maskc);
+                                  const uint8_t* maskf, double* Uc, double* ptc, uint8_t* maskc, bool phi_max_q1, cudaStream_t s) {
+    k_restrict_state<<<grid_for(gc.n_nodes), kThreads, 0, s>>>(gc, gf, Uf, ptf, maskf, Uc, ptc, maskc, phi_max_q1);
     return count_launch(cudaGetLastError());
 }
 

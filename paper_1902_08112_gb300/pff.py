@@ -33,7 +33,8 @@ class Params(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("cg_steps", ctypes.c_int), ("cheb_safety", ctypes.c_double),
                 ("cheb_ratio", ctypes.c_double), ("coarse_rtol", ctypes.c_double),
                 ("coarse_maxit", ctypes.c_int), ("seed", ctypes.c_uint64), ("preconditioner", ctypes.c_int),
-                ("split", ctypes.c_int), ("tie_scale", ctypes.c_int), ("newton_rtol", ctypes.c_double)]
+                ("split", ctypes.c_int), ("tie_scale", ctypes.c_int), ("newton_rtol", ctypes.c_double),
+                ("coarse_phi_max", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -37,6 +37,7 @@ def test_default_params(lib):
     p = pff.default_params()
     assert (p.E, p.nu, p.Gc, p.kappa, p.c_as, p.tol_as) == (1.0, 0.2, 1.0, 1e-10, 100.0, 1e-10)
     assert (p.mg_precision, p.cheb_degree, p.cg_steps, p.coarse_maxit, p.seed) == (32, 4, 10, 200, 12345)
+    assert (p.tie_scale, p.newton_rtol, p.coarse_phi_max, p.split, p.preconditioner) == (0, 1e-8, 0, 0, 0)
 
 
 @pytest.mark.parametrize("field,value", [("dim", 4), ("degree", 3), ("n_levels", 0)])
@@ -58,7 +59,8 @@ def test_create_rejects_indivisible_levels(lib):
 def test_create_rejects_bad_params(lib):
     m = pff.make_mesh(2, 1, (8, 8), 2, (-1, -1), (1, 1))
     h = ctypes.c_void_p()
-    for kw in ({"mg_precision": 16}, {"eps": 0.0}, {"nu": 0.5}, {"cg_steps": 0}):
+    for kw in ({"mg_precision": 16}, {"eps": 0.0}, {"nu": 0.5}, {"cg_steps": 0}, {"tie_scale": 2},
+               {"newton_rtol": 0.0}, {"coarse_phi_max": 2}):
         st = lib.pff_create_hierarchy(ctypes.byref(m), ctypes.byref(pff.default_params(**kw)), None,
                                       ctypes.byref(h))
         assert st == pff.EINVAL

@@ -60,7 +60,7 @@ class Case:
     """A hierarchy on the GPU and the oracle's levels for the same inputs."""
 
     def __init__(self, w, active_fraction=0.1, mg_precision=64, state="random", f=1.0, variant=0, modulus=False,
-                 split=0):
+                 split=0, coarse_phi_max=0):
         self.w = w
         if state == "random":
             U, po, pt = W.random_state(w)
@@ -68,7 +68,8 @@ class Case:
             U, po, pt = W.initial_state(w, displacement="smooth")
         self.U, self.po, self.pt = U, po, pt
         self.prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu,
-                                      Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f, split=split)
+                                      Gc=w.Gc, mg_precision=mg_precision, phi_elastic_factor=f, split=split,
+                                      coarse_phi_max=coarse_phi_max)
         cm = w.cell_mask()
         self.h = pff.create_hierarchy(pff.make_mesh(w.dim, w.deg, w.n_cells, w.n_levels, w.lo, w.hi,
                                                     dirichlet_faces=w.dirichlet_faces, cell_mask=cm), self.prm)
@@ -83,7 +84,8 @@ class Case:
         self.phys = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure, f=f, escale=es,
                              split=split)
         self.mask = fem.dirichlet_face_mask(self.mesh, w.dirichlet_faces) | (act * fem.BIT_ACTIVE).astype(np.uint8)
-        self.levels = mg.build_levels(self.mesh, w.n_levels, self.phys, U, pt, self.mask)
+        self.levels = mg.build_levels(self.mesh, w.n_levels, self.phys, U, pt, self.mask,
+                                      coarse_phi_max=bool(coarse_phi_max))
 
     def close(self):
         pff.destroy_hierarchy(self.h)
@@ -153,6 +155,9 @@ CASES = {
     "3d_q1_all_active": (lambda: W.small(W.config_3d_penny(), 8, 2), 0, False, 0, 1.0),
     "3d_q1_none_active": (lambda: W.small(W.config_3d_penny(), 8, 2), 6, False, 0, 0.0),
     "3d_q2_all_active": (lambda: W.small(W.config_3d_penny(deg=2), 4, 2), 0, False, 0, 1.0),
+    # phi~ on the coarse Q1 levels as the neighbourhood maximum (option coarse_phi_max)
+    "3d_q1_phi_max": (lambda: W.small(W.config_3d_penny(), 12, 3), 0, False, 0, 0.1, 1),
+    "2d_q1_phi_max": (lambda: W.small(W.config_2d_single_crack(), 24, 3), 0, False, 0, 0.1, 1),
     # SI units (steel in a 1 cm box): coefficients over ~30 decades, inside the float exponent range
     # that the double-float operators inherit
     "3d_q1_si_units": (lambda: W.config_3d_penny_si(12, 1, 2), 0),
@@ -166,7 +171,7 @@ CASES = {
 def case(request):
     make_w, variant, *rest = CASES[request.param]
     c = Case(make_w(), variant=variant, modulus=bool(rest and rest[0]), split=rest[1] if len(rest) > 1 else 0,
-             active_fraction=rest[2] if len(rest) > 2 else 0.1)
+             active_fraction=rest[2] if len(rest) > 2 else 0.1, coarse_phi_max=rest[3] if len(rest) > 3 else 0)
     yield c
     c.close()
 

@@ -228,7 +228,8 @@ def test_sneddon_crack_volume_2d():
 def test_q2_coarse_phi_tilde_is_neighbourhood_max(dim):
     """Coarse Q2 levels take phi~ at a node as the maximum of the fine phi~ over the fine nodes at most
     one lattice step away along every axis (brute force over the 3^d block here); Q1 levels keep the
-    coincident-node injection of Sec. 4.2; U and the masks are injected on both."""
+    coincident-node injection of Sec. 4.2 unless coarse_phi_max is set; U and the masks are injected on
+    all levels."""
     import itertools
     for deg in (1, 2):
         mf = fem.Mesh(dim, deg, (4, 6, 2)[:dim], (0.0,) * dim, (1.0, 1.5, 0.5)[:dim])
@@ -243,7 +244,9 @@ def test_q2_coarse_phi_tilde_is_neighbourhood_max(dim):
         np.testing.assert_array_equal(lv[0].U, np.concatenate([U[c * mf.n_nodes + inj] for c in range(dim + 1)]))
         if deg == 1:
             np.testing.assert_array_equal(lv[0].ptil, pt[inj])
-            continue
+            # the option takes the maximum on Q1 levels too
+            lv = mg.build_levels(mf, 2, fem.Phys(), U, pt, mask, coarse_phi_max=True)
+            np.testing.assert_array_equal(lv[0].mask, mask[inj])
         npf, npc = mf.nodes_per_axis(), mc.nodes_per_axis()
         ref = np.empty(mc.n_nodes)
         for cidx, I in enumerate(itertools.product(*[range(n) for n in npc[::-1]])):
