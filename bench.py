@@ -352,7 +352,7 @@ def bench_batch(count: int, dev):
         torch.cuda.synchronize()
         return hs, Us
 
-    def batched(hs, Us, U0):
+    def batched(hs, Us, U0, label):
         b = pff.batch_create(hs)
         for u, u0 in zip(Us, U0):
             u.copy_(u0)
@@ -361,10 +361,12 @@ def bench_batch(count: int, dev):
         for u, u0 in zip(Us, U0):
             u.copy_(u0)
         torch.cuda.synchronize()
+        _nvtx(f"batched_step_{label}", True)
         t0 = time.perf_counter()
         infos = pff.batch_newton_step(b, Us, allow_noconv=True)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        _nvtx("", False)
         precs = pff.batch_mg_precisions(b, len(hs))
         Lmax = max(w.n_levels for w in ws)
         tune = {}
@@ -396,18 +398,18 @@ def bench_batch(count: int, dev):
            "stream": "non-default (captured Arnoldi step replayed)"}
     hs, Us = build(32)
     U0 = [u.clone() for u in Us]
-    tb32, infos32, precs32, tune32 = batched(hs, Us, U0)
+    tb32, infos32, precs32, tune32 = batched(hs, Us, U0, "fp32mg")
     ts32, its_s32 = single(hs, Us, U0)
     for h in hs:
         pff.destroy_hierarchy(h)
     hs, _ = build(64)
-    tb64, infos64, _, tune64 = batched(hs, Us, U0)
+    tb64, infos64, _, tune64 = batched(hs, Us, U0, "fp64mg")
     ts64, its_s64 = single(hs, Us, U0)
     for h in hs:
         pff.destroy_hierarchy(h)
     # the option beyond the paper: phi~ on the coarse levels as the neighbourhood maximum
     hs, _ = build(32, phi_max=1)
-    tbx, infosx, precsx, _ = batched(hs, Us, U0)
+    tbx, infosx, precsx, _ = batched(hs, Us, U0, "fp32mg_phimax")
     for h in hs:
         pff.destroy_hierarchy(h)
     out.update({
