@@ -172,6 +172,40 @@ def test_newton_step_matches_oracle(mgp):
 
 
 @pytest.mark.parametrize("mgp", [64, 32])
+def test_newton_steps_q2_match_oracle(mgp):
+    """Algorithm 1 on Q2 elements (3D penny crack, 8^3 Q2 cells, 2 levels, 20x the recipe's pressure
+    so that the active set moves): residual, Gauss-Lobatto lumped mass (1/6, 2/3, 1/6), active set,
+    the Q2 coarse phi~ rule and the solve, step by step against the oracle."""
+    w = W.small(W.config_3d_penny(deg=2), 8, 2)
+    w.pressure = 20 * w.pressure
+    U, po, pt = W.initial_state(w)
+    prm = pff.default_params(eps=w.eps, pressure=w.pressure, kappa=w.kappa, E=w.E, nu=w.nu, Gc=w.Gc,
+                             mg_precision=mgp)
+    h = pff.create_hierarchy(pff.make_mesh(3, 2, w.n_cells, w.n_levels, w.lo, w.hi), prm)
+    try:
+        pff.set_state(h, t(U), t(po), t(pt))
+        m = fem.Mesh(3, 2, w.n_cells, w.lo, w.hi)
+        ph = fem.Phys(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressure)
+        dmask = fem.dirichlet_face_mask(m, 0x3F)
+        Ud, Uo, prev = t(U), U.copy(), None
+        for k in range(4):
+            info = pff.newton_step(h, Ud, allow_noconv=True)
+            Uo_new, oi = pdas.newton_step(m, ph, w.n_levels, Uo, po, pt, dmask, prev)
+            assert info.n_active == int(oi.active.sum()), k
+            assert info.n_changed == oi.n_changed, k
+            assert info.res_norm == pytest.approx(oi.res_norm, rel=1e-6, abs=1e-12), k
+            slack = 1 if mgp == 32 else 0
+            assert abs(info.solve.iterations - oi.gmres_its) <= max(slack, math.floor(0.1 * oi.gmres_its)), k
+            assert np.linalg.norm(Ud.cpu().numpy() - Uo_new) <= 1e-6 * np.linalg.norm(Uo_new), k
+            Uo, prev = Uo_new, oi.active
+            Ud = t(Uo)
+            if oi.converged:
+                break
+    finally:
+        pff.destroy_hierarchy(h)
+
+
+@pytest.mark.parametrize("mgp", [64, 32])
 def test_newton_steps_in_si_units(mgp):
     """Algorithm 1 on the penny crack in SI units (steel in a 1 cm box, p = 1e9 Pa so that the active set
     moves over five steps) with the tie band on the residual scale (tie_scale 1): where the exact value is
