@@ -51,6 +51,17 @@ TRAFFIC_DF64_PER_CELL = 157.498368e6 / 262144
 DF64_ADDS_PER_CELL, DF64_MULS_PER_CELL = 572, 223
 
 
+def vcycle_bytes_per_node(prec: int) -> float:
+    """Algorithmic bytes of one V-cycle per fine node: on every level nine operator applies (degree-4
+    Chebyshev pre- and post-smoothing from and to the level's vectors, 2 x 4 + 1 applies with the
+    residual) at 53 B/node in FP32 or 105 B/node FP64-accurate, five vector passes per Chebyshev step
+    over eight steps and two for the transfers (4 components of 4 or 8 bytes), summed over the levels
+    of a 3D hierarchy (factor 8/7)."""
+    s = 4 if prec == 32 else 8
+    b_apply = 53.0 if prec == 32 else 105.0
+    return (9 * b_apply + 8 * 5 * 4 * s + 2 * 4 * s) * 8.0 / 7.0
+
+
 def _nvtx(name: str, push: bool):
     """NVTX range around the timed region, so that a profiler can select exactly its launches."""
     try:
@@ -851,8 +862,12 @@ def main():
         info = pff.gmres_solve(h, R, xs, rtol=1e-8, restart=30, maxit=200, allow_noconv=True)
         stream.synchronize()
         solve_ms = (time.perf_counter() - t0) * 1e3
+        vc_gbs = vcycle_bytes_per_node(mgp) * nn / (vc_ms * 1e-3) / 1e9
         res[f"fp{mgp}_mg"] = {"vcycle_ms": vc_ms, "solve_ms": solve_ms, "iterations": info.iterations,
-                              "rel_res": info.res_final / max(info.res0, 1e-300)}
+                              "rel_res": info.res_final / max(info.res0, 1e-300),
+                              "vcycle_gdofs": nd / (vc_ms * 1e-3) / 1e9,
+                              "vcycle_hbm_frac": vc_gbs / _peaks().get("hbm_gbs", 6800.0),
+                              "vcycle_bytes_per_node": vcycle_bytes_per_node(mgp)}
 
     # ---- end to end through the C ABI with host buffers: pff_apply_jacobian_host copies x from
     # pinned host memory, applies and copies y back (slab-pipelined on three streams) and returns
